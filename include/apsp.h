@@ -1,0 +1,203 @@
+/*
+ * apsp.h -- C ABI of the GB300 blocked Floyd-Warshall all-pairs shortest-path
+ * library (libapsp.so).
+ *
+ * Problem (the paper, Sec. 3): an undirected weighted graph G = (V, E, w) with
+ * n vertices and no negative cycles is given by its adjacency matrix A with
+ * A_ij = A_ji = w_ij; the library returns the length of the shortest path
+ * between every pair of vertices (no paths).  Conventions of this ABI:
+ *   - A_ii = 0; a missing edge is INF (APSP_INF_I32, APSP_INF_U16, or +inf for
+ *     fp32); weights are >= 0 (an undirected negative edge is a negative
+ *     cycle).
+ *   - Output entry D_ij = shortest-path length, INF exactly when i and j are in
+ *     different components.
+ * Method (Sec. 4.4 and 4.5, Alg. 3 and 4; Fig. 1 phases): the n x n matrix is
+ * split into Bk x Bk blocks; for each round k = 0..q-1 (q = ceil(n/Bk)):
+ *   Phase 1  closes the diagonal block D_kk by Floyd-Warshall (Table 1
+ *            "FloydWarshall");
+ *   Phase 2  updates the row panel D_kJ = min(D_kJ, D_kk (x) D_kJ) and the
+ *            column panel D_Ik = min(D_Ik, D_Ik (x) D_kk) (Table 1 "MinPlus");
+ *   Phase 3  updates every remaining block D_IJ = min(D_IJ, D_Ik (x) D_kJ)
+ *            (Table 1 "MatProd" + "MatMin").
+ * (x) is the min-plus product (X (x) Y)_ij = min_t X_it + Y_tj.  Directed
+ * inputs are also solved exactly (the paper notes the method applies to them
+ * once symmetry is not exploited; the library never assumes symmetry).
+ *
+ * Memory: every matrix argument is a caller-owned pointer to DEVICE memory
+ * (unless a function says otherwise), row-major, n rows of `ld` elements
+ * (ld >= n); only the first n elements of each row are read or written.
+ * Calls that take a stream are asynchronous on it (a cudaStream_t passed as
+ * void*, NULL = the legacy default stream) unless stated otherwise.  No C++
+ * exception crosses this ABI; every call returns an apsp_status, 0 = success.
+ */
+#ifndef APSP_H_
+#define APSP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- sentinels ---------------------------------------------------------- */
+/* int32 INF = INT32_MAX / 2: any sum of two stored values stays <= INT32_MAX,
+ * so the add-min never overflows and a pair in different components keeps
+ * exactly INF (INF + x > INF >= the current value). */
+#define APSP_INF_I32 1073741823
+/* Packed unsigned 16-bit INF: stored values are <= 0x7FFF, so the sum of two
+ * never exceeds 0xFFFE and the 16-bit add never wraps. */
+#define APSP_INF_U16 0x7FFF
+
+typedef enum {
+  APSP_OK = 0,
+  APSP_E_INVALID = 1,   /* bad argument (null, n < 0, ld < n, negative weight, non-zero diagonal) */
+  APSP_E_CUDA = 2,      /* a CUDA runtime call failed; apsp_last_error() has the text */
+  APSP_E_NOMEM = 3,     /* workspace or request does not fit the memory budget */
+  APSP_E_RANGE = 4,     /* a finite weight >= INF, or the 16-bit bound does not hold */
+  APSP_E_BUSY = 5,      /* request queue full */
+  APSP_E_NOTFOUND = 6,  /* unknown ticket */
+  APSP_E_TIMEOUT = 7,   /* a bounded device wait gave up */
+  APSP_E_CANCELLED = 8, /* request cancelled, or the handle was destroyed */
+  APSP_E_NOTREADY = 9,  /* poll: the request has not finished */
+  APSP_E_UNSUPPORTED = 10
+} apsp_status;
+
+typedef enum {
+  APSP_I32 = 0,  /* int32 distances, INF = APSP_INF_I32 */
+  APSP_U16 = 1,  /* packed unsigned 16-bit distances, INF = APSP_INF_U16 */
+  APSP_F32 = 2,  /* fp32 distances, INF = +inf */
+  APSP_AUTO = 3  /* int32 in/out; solved in packed 16-bit when the bound allows */
+} apsp_dtype;
+
+typedef struct apsp_handle apsp_handle;
+
+typedef struct {
+  int device;            /* CUDA device ordinal (the handle makes it current in every call) */
+  int dtype;             /* apsp_dtype used by apsp_solve (default APSP_I32) */
+  int block_k;           /* round width Bk; 0 = the built-in choice (64) */
+  int max_batch;         /* serving: graphs per persistent launch (default 64) */
+  int queue_depth;       /* serving: pending requests before APSP_E_BUSY (default 4096) */
+  int64_t memory_budget; /* serving: bytes of device memory for admitted requests (0 = free HBM - reserve) */
+  int64_t spin_limit;    /* bounded device waits: iterations before APSP_E_TIMEOUT (0 = default) */
+} apsp_config;
+
+/* Fills *cfg with the defaults. */
+void apsp_config_default(apsp_config *cfg);
+
+/* Creates a handle on cfg->device (cfg == NULL: defaults).  The library owns
+ * the handle, its device workspace and its serving thread (started on the
+ * first apsp_submit).  Errors: APSP_E_INVALID, APSP_E_CUDA. */
+apsp_status apsp_create(apsp_handle **h, const apsp_config *cfg);
+
+/* Frees everything the handle owns; pending requests end as
+ * APSP_E_CANCELLED.  Safe on NULL. */
+apsp_status apsp_destroy(apsp_handle *h);
+
+/* ---- one-shot solve (Alg. 3/4 rounds on the caller's stream) ------------ */
+/* Solves APSP for the n x n matrix W into D, element type = the handle's
+ * dtype.  W and D are device pointers with the same leading dimension ld;
+ * W == D (in place) is allowed.  Asynchronous on `stream`, except that
+ * APSP_AUTO synchronizes the stream once to read the 16-bit bound.
+ * Input checks that need the data (negative weight, non-zero diagonal,
+ * finite weight >= INF) run on the device; read their result with
+ * apsp_last_status().  Errors returned directly: APSP_E_INVALID (null pointer,
+ * n < 0, ld < n), APSP_E_NOMEM (workspace), APSP_E_CUDA. */
+apsp_status apsp_solve(apsp_handle *h, const void *W, int64_t n, int64_t ld, void *D, void *stream);
+
+/* Same with an explicit element type. */
+apsp_status apsp_solve_t(apsp_handle *h, int dtype, const void *W, int64_t n, int64_t ld, void *D,
+                         void *stream);
+
+/* Builds D from an edge list on the device and solves it in place: D_ii = 0,
+ * D_uv = D_vu = min over duplicate edges of w, INF elsewhere (a-1 "densify").
+ * src/dst are int32 device arrays of m vertex ids, w holds m weights of the
+ * element type (int32 for APSP_I32/APSP_AUTO, uint16 for APSP_U16, float for
+ * APSP_F32).  For APSP_U16 and APSP_AUTO the 16-bit bound is computed from the
+ * edge list first (this synchronizes `stream`); APSP_U16 returns APSP_E_RANGE
+ * when it fails, APSP_AUTO then falls back to int32 (D must then be int32).
+ * This is the path for sizes where a dense int32 W does not fit next to D. */
+apsp_status apsp_solve_edges(apsp_handle *h, int dtype, const int32_t *src, const int32_t *dst, const void *w,
+                             int64_t m, int64_t n, void *D, int64_t ld, void *stream);
+
+/* Waits for `stream` and returns the device-side input check of the last
+ * solve on this handle: APSP_OK, APSP_E_INVALID (negative weight or non-zero
+ * diagonal) or APSP_E_RANGE (a finite weight >= INF). */
+apsp_status apsp_last_status(apsp_handle *h, void *stream);
+
+/* The 16-bit enable test by itself (north-star "precision selection"): for
+ * every connected component c of the graph given by the int32 matrix W, the
+ * single-source distances from the smallest vertex r_c of c give
+ * ecc(r_c); every finite distance in c is <= 2 ecc(r_c) (triangle inequality
+ * through r_c).  *bound = max_c 2 ecc(r_c) (saturated at INT64_MAX / 4), *ok =
+ * (*bound < APSP_INF_U16).  Synchronizes `stream`. */
+apsp_status apsp_int16_bound(apsp_handle *h, const int32_t *W, int64_t n, int64_t ld, int64_t *bound, int *ok,
+                             void *stream);
+
+/* ---- building blocks (Table 1) ------------------------------------------ */
+/* C = min(C, A (x) B): the min-plus product ("MatProd") followed by the
+ * element-wise minimum ("MatMin").  A is m x k (lda), B is k x n (ldb), C is
+ * m x n (ldc), all device, row-major, of the given dtype (APSP_I32, APSP_U16 or
+ * APSP_F32).  C must not overlap A or B.  Errors: APSP_E_INVALID. */
+apsp_status apsp_minplus(apsp_handle *h, int dtype, const void *A, int64_t lda, const void *B, int64_t ldb,
+                         void *C, int64_t ldc, int64_t m, int64_t k, int64_t n, void *stream);
+
+/* int32 -> packed u16 (INF32 -> INF16) and back, n x n with separate leading
+ * dimensions; the caller guarantees every finite entry is < APSP_INF_U16. */
+apsp_status apsp_pack_u16(const int32_t *src, int64_t lds, uint16_t *dst, int64_t ldd, int64_t n, void *stream);
+apsp_status apsp_unpack_u16(const uint16_t *src, int64_t lds, int32_t *dst, int64_t ldd, int64_t n, void *stream);
+
+/* ---- request loop (north-star "serving") -------------------------------- */
+typedef enum {
+  APSP_QUEUED = 0,   /* accepted, waiting for memory or a batch slot */
+  APSP_ADMITTED = 1, /* device matrix allocated and W copied; caller may reuse W */
+  APSP_RUNNING = 2,  /* rounds in progress in the persistent batched kernel */
+  APSP_DONE = 3,
+  APSP_ERROR = 4
+} apsp_state;
+
+typedef struct {
+  const void *W;   /* int32 adjacency matrix, n rows of ld elements */
+  int is_host;     /* 1: W is host memory (copied at admission), 0: device memory */
+  int64_t n;
+  int64_t ld;
+} apsp_request;
+
+/* Queues a request; non-blocking.  The library copies W into a device matrix
+ * it owns when the request is admitted (its n^2 * 4-byte footprint fits the
+ * memory budget); the caller may reuse W once apsp_poll reports
+ * APSP_ADMITTED or later.  Errors: APSP_E_INVALID, APSP_E_BUSY (queue full),
+ * APSP_E_NOMEM (n^2 * 4 bytes exceeds the whole budget). */
+apsp_status apsp_submit(apsp_handle *h, const apsp_request *r, uint64_t *ticket);
+
+/* Non-blocking state query.  On APSP_DONE, *D_dev (if non-NULL) points at the
+ * library-owned int32 n x n result (leading dimension n), valid until
+ * apsp_release.  Returns APSP_OK, or the request's error (APSP_E_TIMEOUT,
+ * APSP_E_CANCELLED, ...) with *st = APSP_ERROR, or APSP_E_NOTFOUND. */
+apsp_status apsp_poll(apsp_handle *h, uint64_t ticket, apsp_state *st, const void **D_dev);
+
+/* Blocks until the request is DONE or ERROR, or timeout_ms passes
+ * (APSP_E_NOTREADY). */
+apsp_status apsp_wait(apsp_handle *h, uint64_t ticket, int64_t timeout_ms);
+
+/* Copies a finished result to dst (device or host, leading dimension ldd) on
+ * `stream`. */
+apsp_status apsp_fetch(apsp_handle *h, uint64_t ticket, void *dst, int64_t ldd, void *stream);
+
+/* Frees a finished request's device matrix and forgets the ticket. */
+apsp_status apsp_release(apsp_handle *h, uint64_t ticket);
+
+/* Cancels a request that has not started running; running requests finish. */
+apsp_status apsp_cancel(apsp_handle *h, uint64_t ticket);
+
+/* ---- diagnostics -------------------------------------------------------- */
+const char *apsp_strerror(apsp_status s);
+/* Text of the last failure on this handle (thread-local per handle); never NULL. */
+const char *apsp_last_error(apsp_handle *h);
+/* Number of kernel launches this handle has issued (for launch accounting). */
+int64_t apsp_launch_count(apsp_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* APSP_H_ */

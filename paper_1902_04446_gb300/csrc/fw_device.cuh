@@ -1,0 +1,243 @@
+// Device-side building blocks of the blocked Floyd-Warshall kernels (sm_103a).
+//
+// Three storage modes share one code path through a "word" abstraction: every
+// kernel moves and computes 32-bit words.
+//   OpI32  one int32 distance per word, add-min = __viaddmin_s32
+//   OpU16  two unsigned 16-bit distances per word (element 2w in the low half),
+//          add-min = __viaddmin_u16x2 (two relaxations per lane-op)
+//   OpF32  one fp32 distance per word, add-min = fminf(a + b, c)
+// The relaxation is the min-plus step of the paper's Table 1 (MatProd followed
+// by MatMin): c = min(c, a + b).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace apsp {
+
+struct OpI32 {
+  using elem = int32_t;
+  static constexpr int EPW = 1;                 // elements per 32-bit word
+  static constexpr uint32_t INF_WORD = 1073741823u;
+  static constexpr int DTYPE = 0;
+  __device__ __forceinline__ static uint32_t addmin(uint32_t a, uint32_t b, uint32_t c) {
+    return (uint32_t)__viaddmin_s32((int)a, (int)b, (int)c);
+  }
+  // A-operand word for one element (same value in every lane of the word)
+  __device__ __forceinline__ static uint32_t dup(elem e) { return (uint32_t)e; }
+  __device__ __forceinline__ static elem inf_elem() { return (elem)1073741823; }
+  // scalar arithmetic for the diagonal closure
+  using scalar = int32_t;
+  __device__ __forceinline__ static scalar to_s(elem e) { return e; }
+  __device__ __forceinline__ static elem from_s(scalar s) { return s; }
+  __device__ __forceinline__ static scalar s_addmin(scalar a, scalar b, scalar c) { return __viaddmin_s32(a, b, c); }
+};
+
+struct OpU16 {
+  using elem = uint16_t;
+  static constexpr int EPW = 2;
+  static constexpr uint32_t INF_WORD = 0x7FFF7FFFu;
+  static constexpr int DTYPE = 1;
+  __device__ __forceinline__ static uint32_t addmin(uint32_t a, uint32_t b, uint32_t c) {
+    return __viaddmin_u16x2(a, b, c);
+  }
+  __device__ __forceinline__ static uint32_t dup(elem e) { return (uint32_t)e | ((uint32_t)e << 16); }
+  __device__ __forceinline__ static elem inf_elem() { return (elem)0x7FFF; }
+  using scalar = int32_t;
+  __device__ __forceinline__ static scalar to_s(elem e) { return (scalar)e; }
+  __device__ __forceinline__ static elem from_s(scalar s) { return (elem)s; }
+  // stored values are <= 0x7FFF, so a + b <= 0xFFFE and min() keeps <= 0x7FFF
+  __device__ __forceinline__ static scalar s_addmin(scalar a, scalar b, scalar c) { return __viaddmin_s32(a, b, c); }
+};
+
+struct OpF32 {
+  using elem = float;
+  static constexpr int EPW = 1;
+  static constexpr uint32_t INF_WORD = 0x7F800000u;
+  static constexpr int DTYPE = 2;
+  __device__ __forceinline__ static uint32_t addmin(uint32_t a, uint32_t b, uint32_t c) {
+    return __float_as_uint(fminf(__uint_as_float(a) + __uint_as_float(b), __uint_as_float(c)));
+  }
+  __device__ __forceinline__ static uint32_t dup(elem e) { return __float_as_uint(e); }
+  __device__ __forceinline__ static elem inf_elem() { return __int_as_float(0x7F800000); }
+  using scalar = float;
+  __device__ __forceinline__ static scalar to_s(elem e) { return e; }
+  __device__ __forceinline__ static elem from_s(scalar s) { return s; }
+  __device__ __forceinline__ static scalar s_addmin(scalar a, scalar b, scalar c) { return fminf(a + b, c); }
+};
+
+// ---------------------------------------------------------------------------
+// element <-> word helpers
+template <class Op>
+__device__ __forceinline__ uint32_t elem_bits(typename Op::elem e) {
+  if constexpr (Op::EPW == 2) return (uint32_t)e;
+  else if constexpr (Op::DTYPE == 2) return __float_as_uint(e);
+  else return (uint32_t)e;
+}
+template <class Op>
+__device__ __forceinline__ typename Op::elem bits_elem(uint32_t b) {
+  if constexpr (Op::EPW == 2) return (typename Op::elem)(b & 0xFFFFu);
+  else if constexpr (Op::DTYPE == 2) return __uint_as_float(b);
+  else return (typename Op::elem)b;
+}
+
+// Element e (0 .. 4*EPW-1) of a 4-word chunk.
+template <class Op>
+__device__ __forceinline__ uint32_t chunk_get(const uint4 &v, int e) {
+  uint32_t w = (e / Op::EPW == 0) ? v.x : (e / Op::EPW == 1) ? v.y : (e / Op::EPW == 2) ? v.z : v.w;
+  if constexpr (Op::EPW == 2) return (e & 1) ? (w >> 16) : (w & 0xFFFFu);
+  else return w;
+}
+template <class Op>
+__device__ __forceinline__ void chunk_set(uint4 &v, int e, uint32_t bits) {
+  uint32_t *w = (e / Op::EPW == 0) ? &v.x : (e / Op::EPW == 1) ? &v.y : (e / Op::EPW == 2) ? &v.z : &v.w;
+  if constexpr (Op::EPW == 2) {
+    if (e & 1) *w = (*w & 0x0000FFFFu) | (bits << 16);
+    else *w = (*w & 0xFFFF0000u) | (bits & 0xFFFFu);
+  } else {
+    *w = bits;
+  }
+}
+
+// Loads 4 words (4*EPW elements) of row r starting at element column c0 of a
+// row-major matrix with leading dimension ld.  Elements outside
+// [0, nrows) x [0, ncols) read as INF.  `vec` says that the matrix base is
+// 16-byte aligned and ld * sizeof(elem) is a multiple of 16, so that a chunk
+// starting at a multiple of 4*EPW is one aligned 16-byte access inside row r
+// (the row holds ld >= ncols elements).
+template <class Op>
+__device__ __forceinline__ uint4 load_chunk(const typename Op::elem *M, int64_t ld, int64_t nrows, int64_t ncols,
+                                            int64_t r, int64_t c0, bool vec) {
+  constexpr int E = 4 * Op::EPW;
+  uint4 v = make_uint4(Op::INF_WORD, Op::INF_WORD, Op::INF_WORD, Op::INF_WORD);
+  if (r < 0 || r >= nrows || c0 >= ncols) return v;
+  const typename Op::elem *p = M + r * ld + c0;
+  if (vec && c0 + E <= ld) {
+    v = __ldg(reinterpret_cast<const uint4 *>(p));
+    if (c0 + E > ncols) {
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (c0 + e >= ncols) chunk_set<Op>(v, e, elem_bits<Op>(Op::inf_elem()));
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (c0 + e < ncols) chunk_set<Op>(v, e, elem_bits<Op>(p[e]));
+  }
+  return v;
+}
+
+// Stores the elements of a 4-word chunk whose mask bit is set (bit e for
+// element e).  A full mask with `vec` is one 16-byte store.
+template <class Op>
+__device__ __forceinline__ void store_chunk(typename Op::elem *M, int64_t ld, int64_t r, int64_t c0, uint4 v,
+                                            uint32_t mask, bool vec) {
+  constexpr int E = 4 * Op::EPW;
+  constexpr uint32_t FULL = (1u << E) - 1u;
+  if (mask == 0) return;
+  typename Op::elem *p = M + r * ld + c0;
+  if (vec && mask == FULL) {
+    *reinterpret_cast<uint4 *>(p) = v;
+  } else {
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (mask & (1u << e)) p[e] = bits_elem<Op>(chunk_get<Op>(v, e));
+  }
+}
+
+// Mask of the elements c0 .. c0+E-1 that lie in [0, ncols) and outside the
+// excluded column range [x0, x1).
+template <class Op>
+__device__ __forceinline__ uint32_t col_mask(int64_t c0, int64_t ncols, int64_t x0, int64_t x1) {
+  constexpr int E = 4 * Op::EPW;
+  uint32_t m = 0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    int64_t c = c0 + e;
+    if (c < ncols && (c < x0 || c >= x1)) m |= 1u << e;
+  }
+  return m;
+}
+
+// ---------------------------------------------------------------------------
+// Register-blocked min-plus tile.
+//
+// A CTA of (BM/8) x (BNW/8) threads owns a BM x BNW-word output tile; thread
+// (ty, tx) holds an 8 x 8 word block: rows {ty*4 + 0..3} and
+// {BM/2 + ty*4 + 0..3}, word columns {tx*4 + 0..3} and {BNW/2 + tx*4 + 0..3},
+// so that every operand fetch is one 16-byte shared-memory load and a warp's
+// B fetch covers 256 contiguous bytes (no bank conflicts).
+//   As[t][i]  (BK x BM words)  A operand, transposed, each element duplicated
+//                              over the lanes of its word
+//   Bs[t][w]  (BK x BNW words) B operand
+//   acc[r][c] += min-plus over t:  acc = min(acc, As[t][row r] + Bs[t][col c])
+template <int BM, int BNW>
+struct TileMap {
+  static constexpr int TX = BNW / 8;
+  static constexpr int TY = BM / 8;
+  static constexpr int THREADS = TX * TY;
+  __device__ __forceinline__ static int row(int ty, int r) { return (r < 4) ? (ty * 4 + r) : (BM / 2 + ty * 4 + r - 4); }
+  __device__ __forceinline__ static int wcol(int tx, int h) { return h == 0 ? tx * 4 : BNW / 2 + tx * 4; }
+};
+
+template <class Op, int BM, int BNW, int BK>
+__device__ __forceinline__ void tile_minplus(const uint32_t *__restrict__ As, const uint32_t *__restrict__ Bs,
+                                             uint32_t (&acc)[8][8], int ty, int tx) {
+#pragma unroll 4
+  for (int t = 0; t < BK; ++t) {
+    const uint4 a0 = *reinterpret_cast<const uint4 *>(As + t * BM + ty * 4);
+    const uint4 a1 = *reinterpret_cast<const uint4 *>(As + t * BM + BM / 2 + ty * 4);
+    const uint4 b0 = *reinterpret_cast<const uint4 *>(Bs + t * BNW + tx * 4);
+    const uint4 b1 = *reinterpret_cast<const uint4 *>(Bs + t * BNW + BNW / 2 + tx * 4);
+    const uint32_t a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const uint32_t b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) acc[r][c] = Op::addmin(a[r], b[c], acc[r][c]);
+  }
+}
+
+// Loads the thread's 8 x 8 word block of the output tile whose top-left
+// element is (row0, col0) from M (INF outside [0,nrows) x [0,ncols)).
+template <class Op, int BM, int BNW>
+__device__ __forceinline__ void load_acc(const typename Op::elem *M, int64_t ld, int64_t nrows, int64_t ncols,
+                                         int64_t row0, int64_t col0, bool vec, uint32_t (&acc)[8][8], int ty,
+                                         int tx) {
+  using Map = TileMap<BM, BNW>;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint4 v = load_chunk<Op>(M, ld, nrows, ncols, row0 + Map::row(ty, r),
+                                     col0 + (int64_t)Map::wcol(tx, h) * Op::EPW, vec);
+      acc[r][4 * h + 0] = v.x;
+      acc[r][4 * h + 1] = v.y;
+      acc[r][4 * h + 2] = v.z;
+      acc[r][4 * h + 3] = v.w;
+    }
+  }
+}
+
+// Stores the thread's block: row r is written when it lies in [0, nrows) and
+// outside [xr0, xr1); an element column when it lies in [0, ncols) and outside
+// [xc0, xc1).
+template <class Op, int BM, int BNW>
+__device__ __forceinline__ void store_acc(typename Op::elem *M, int64_t ld, int64_t nrows, int64_t ncols,
+                                          int64_t row0, int64_t col0, int64_t xr0, int64_t xr1, int64_t xc0,
+                                          int64_t xc1, bool vec, const uint32_t (&acc)[8][8], int ty, int tx) {
+  using Map = TileMap<BM, BNW>;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int64_t c0 = col0 + (int64_t)Map::wcol(tx, h) * Op::EPW;
+    const uint32_t cm = col_mask<Op>(c0, ncols, xc0, xc1);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int64_t row = row0 + Map::row(ty, r);
+      if (row >= nrows || (row >= xr0 && row < xr1)) continue;
+      const uint4 v = make_uint4(acc[r][4 * h + 0], acc[r][4 * h + 1], acc[r][4 * h + 2], acc[r][4 * h + 3]);
+      store_chunk<Op>(M, ld, row, c0, v, cm, vec);
+    }
+  }
+}
+
+}  // namespace apsp

@@ -1,0 +1,40 @@
+// Internal launchers shared by the C-ABI layer (not part of the public ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace apsp {
+
+// Round width Bk used by launch_rounds for a dtype.
+int64_t round_width(int dtype);
+
+// q rounds of Phase 1 -> Phase 2 -> Phase 3 on D (n x n, leading dimension ld).
+// colT is a Bk x ldT panel buffer, ldT a multiple of 256 elements and >= n.
+cudaError_t launch_rounds(int dtype, void *D, int64_t ld, int64_t n, void *colT, int64_t ldT, cudaStream_t s,
+                          int64_t *launches);
+// Copies W to D when they differ and checks the input (status |= 1 invalid, 2 range).
+cudaError_t launch_ingest(int dtype, const void *W, void *D, int64_t n, int64_t ld, int *status, cudaStream_t s,
+                          int64_t *launches);
+cudaError_t launch_pack(const int32_t *src, int64_t lds, uint16_t *dst, int64_t ldd, int64_t n, cudaStream_t s,
+                        int64_t *launches);
+cudaError_t launch_unpack(const uint16_t *src, int64_t lds, int32_t *dst, int64_t ldd, int64_t n, cudaStream_t s,
+                          int64_t *launches);
+cudaError_t launch_densify(int dtype, const int32_t *src, const int32_t *dst, const void *w, int64_t m, void *D,
+                           int64_t n, int64_t ld, int *status, cudaStream_t s, int64_t *launches);
+cudaError_t launch_minplus(int dtype, const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc,
+                           int64_t m, int64_t k, int64_t nn, cudaStream_t s, int64_t *launches);
+
+// 16-bit enable test.  *bound = max over components of 2 * ecc(smallest vertex);
+// *ok = bound < 0x7FFF.  Both synchronize `s`.
+// Edge list: undirected edges (src[e], dst[e]) with weights of type wtype
+// (0 int32, 1 uint16); entries with a bad id, a self loop or an INF weight are
+// skipped.
+cudaError_t bound_from_edges(const int32_t *src, const int32_t *dst, const void *w, int wtype, int64_t m, int64_t n,
+                             cudaStream_t s, int64_t *bound, int *ok, int64_t *launches);
+// Dense int32 matrix: the finite off-diagonal entries become the edge list;
+// an asymmetric matrix (W_ij != W_ji) or more than `max_edges` finite entries
+// gives *ok = 0.
+cudaError_t bound_from_dense(const int32_t *W, int64_t n, int64_t ld, int64_t max_edges, cudaStream_t s,
+                             int64_t *bound, int *ok, int64_t *launches);
+
+}  // namespace apsp

@@ -1,0 +1,213 @@
+"""Handle: one C-ABI handle plus argument marshalling for torch CUDA tensors."""
+from __future__ import annotations
+
+import ctypes
+
+from ._lib import APSP_AUTO, APSP_F32, APSP_I32, APSP_U16, ApspError, apsp_config, apsp_request, lib
+
+_DT_NAMES = {"int32": APSP_I32, "i32": APSP_I32, "u16": APSP_U16, "uint16": APSP_U16, "u16x2": APSP_U16,
+             "int16": APSP_U16, "fp32": APSP_F32, "f32": APSP_F32, "float32": APSP_F32, "auto": APSP_AUTO}
+
+
+def dtype_code(d) -> int:
+    """apsp_dtype code from a name, a code, or a torch dtype."""
+    if isinstance(d, int):
+        return d
+    if isinstance(d, str):
+        return _DT_NAMES[d.lower()]
+    import torch
+    if d == torch.int32:
+        return APSP_I32
+    if d in (torch.int16, getattr(torch, "uint16", torch.int16)):
+        return APSP_U16
+    if d == torch.float32:
+        return APSP_F32
+    raise ValueError(f"unsupported dtype {d}")
+
+
+def _elem_ok(t, code):
+    import torch
+    want = {APSP_I32: (torch.int32,), APSP_AUTO: (torch.int32,), APSP_F32: (torch.float32,),
+            APSP_U16: (torch.int16, getattr(torch, "uint16", torch.int16))}[code]
+    if t.dtype not in want:
+        raise TypeError(f"tensor dtype {t.dtype} does not match apsp dtype {code}")
+
+
+def _mat(t, name):
+    if t.dim() != 2 or t.stride(1) != 1 or t.shape[1] < t.shape[0]:
+        raise ValueError(f"{name} must be a row-major (n, >=n) matrix view with unit column stride")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    return t.shape[0], t.stride(0)
+
+
+def _stream(stream, device):
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream(device).cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Handle:
+    """Owns one ``apsp_handle`` (workspace, serving thread) on one device."""
+
+    def __init__(self, device: int = 0, dtype="int32", max_batch: int = 64, queue_depth: int = 4096,
+                 memory_budget: int = 0, spin_limit: int = 0, block_k: int = 0):
+        cfg = apsp_config()
+        lib.apsp_config_default(ctypes.byref(cfg))
+        cfg.device = device
+        cfg.dtype = dtype_code(dtype)
+        cfg.max_batch = max_batch
+        cfg.queue_depth = queue_depth
+        cfg.memory_budget = memory_budget
+        cfg.spin_limit = spin_limit
+        cfg.block_k = block_k
+        h = ctypes.c_void_p()
+        st = lib.apsp_create(ctypes.byref(h), ctypes.byref(cfg))
+        if st != 0:
+            raise ApspError(st, "apsp_create")
+        self._h = h
+        self.device = device
+        self.dtype = cfg.dtype
+        self._hold = {}  # tickets -> host/device buffers kept alive until admission
+
+    # ------------------------------------------------------------ lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.apsp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, st, where):
+        if st != 0:
+            detail = lib.apsp_last_error(self._h).decode() if self._h else ""
+            raise ApspError(st, where, detail)
+
+    @property
+    def launch_count(self) -> int:
+        return int(lib.apsp_launch_count(self._h))
+
+    # ------------------------------------------------------------ solves
+    def solve_t(self, dtype, W, D=None, stream=None):
+        """apsp_solve_t: D (allocated like W when None) <- APSP of W; returns D."""
+        import torch
+        code = dtype_code(dtype)
+        n, ld = _mat(W, "W")
+        _elem_ok(W, code)
+        if D is None:
+            D = torch.empty_like(W)
+        nd, ldd = _mat(D, "D")
+        if nd != n or ldd != ld or D.dtype != W.dtype:
+            raise ValueError("D must have W's shape, leading dimension and dtype")
+        self._check(lib.apsp_solve_t(self._h, code, W.data_ptr(), n, ld, D.data_ptr(), _stream(stream, W.device)),
+                    "apsp_solve_t")
+        return D
+
+    def solve(self, W, D=None, stream=None):
+        """apsp_solve with the handle's dtype."""
+        return self.solve_t(self.dtype, W, D, stream)
+
+    def solve_edges(self, dtype, src, dst, w, n, D=None, stream=None):
+        """apsp_solve_edges: D (n x n, allocated when None) from an undirected edge list."""
+        import torch
+        code = dtype_code(dtype)
+        if D is None:
+            tdt = {APSP_I32: torch.int32, APSP_AUTO: torch.int32, APSP_F32: torch.float32,
+                   APSP_U16: torch.int16}[code]
+            D = torch.empty((n, n), dtype=tdt, device=src.device)
+        nd, ld = _mat(D, "D")
+        if nd != n:
+            raise ValueError("D must have n rows")
+        m = src.numel()
+        for t in (src, dst):
+            if t.dtype != torch.int32 or not t.is_cuda or not t.is_contiguous():
+                raise TypeError("src/dst must be contiguous int32 CUDA tensors")
+        if not w.is_contiguous() or not w.is_cuda or w.numel() != m:
+            raise TypeError("w must be a contiguous CUDA tensor of m weights")
+        self._check(lib.apsp_solve_edges(self._h, code, src.data_ptr(), dst.data_ptr(), w.data_ptr(), m, n,
+                                         D.data_ptr(), ld, _stream(stream, D.device)), "apsp_solve_edges")
+        return D
+
+    def last_status(self, stream=None) -> int:
+        """apsp_last_status: the device-side input check of the last solve (0 = OK)."""
+        import torch
+        return int(lib.apsp_last_status(self._h, _stream(stream, torch.device("cuda", self.device))))
+
+    def int16_bound(self, W, stream=None):
+        """apsp_int16_bound: (max_c 2 ecc(r_c), enabled) for an int32 adjacency matrix."""
+        n, ld = _mat(W, "W")
+        _elem_ok(W, APSP_I32)
+        b = ctypes.c_int64()
+        ok = ctypes.c_int()
+        self._check(lib.apsp_int16_bound(self._h, W.data_ptr(), n, ld, ctypes.byref(b), ctypes.byref(ok),
+                                         _stream(stream, W.device)), "apsp_int16_bound")
+        return int(b.value), bool(ok.value)
+
+    def minplus(self, A, B, C, stream=None):
+        """apsp_minplus: C <- min(C, A (x) B) in place; returns C."""
+        code = dtype_code(C.dtype)
+        for t, nm in ((A, "A"), (B, "B"), (C, "C")):
+            if t.dim() != 2 or t.stride(1) != 1 or not t.is_cuda:
+                raise ValueError(f"{nm} must be a row-major CUDA matrix")
+            _elem_ok(t, code)
+        m, k = A.shape
+        k2, n = B.shape
+        if k2 != k or tuple(C.shape) != (m, n):
+            raise ValueError("shape mismatch")
+        self._check(lib.apsp_minplus(self._h, code, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
+                                     C.data_ptr(), C.stride(0), m, k, n, _stream(stream, C.device)), "apsp_minplus")
+        return C
+
+    # ------------------------------------------------------------ request loop
+    def submit(self, W) -> int:
+        """apsp_submit: W is an int32 (n, >=n) tensor on the host (pinned or not) or the device."""
+        if W.dim() != 2 or W.stride(1) != 1 or W.shape[1] < W.shape[0]:
+            raise ValueError("W must be a row-major (n, >=n) matrix")
+        _elem_ok(W, APSP_I32)
+        r = apsp_request(W.data_ptr(), 0 if W.is_cuda else 1, W.shape[0], W.stride(0))
+        t = ctypes.c_uint64()
+        self._check(lib.apsp_submit(self._h, ctypes.byref(r), ctypes.byref(t)), "apsp_submit")
+        self._hold[int(t.value)] = W
+        return int(t.value)
+
+    def poll(self, ticket: int):
+        """apsp_poll: (state code, device pointer of the result or None, status)."""
+        st = ctypes.c_int()
+        p = ctypes.c_void_p()
+        rc = lib.apsp_poll(self._h, ticket, ctypes.byref(st), ctypes.byref(p))
+        if rc == 6:
+            raise ApspError(rc, "apsp_poll")
+        return int(st.value), p.value, int(rc)
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> int:
+        return int(lib.apsp_wait(self._h, ticket, timeout_ms))
+
+    def fetch(self, ticket: int, out, stream=None):
+        """apsp_fetch into a (n, >=n) int32 tensor (host or device)."""
+        import torch
+        dev = out.device if out.is_cuda else torch.device("cuda", self.device)
+        self._check(lib.apsp_fetch(self._h, ticket, out.data_ptr(), out.stride(0), _stream(stream, dev)),
+                    "apsp_fetch")
+        return out
+
+    def release(self, ticket: int) -> int:
+        rc = int(lib.apsp_release(self._h, ticket))
+        if rc == 0:
+            self._hold.pop(ticket, None)
+        return rc
+
+    def cancel(self, ticket: int) -> int:
+        return int(lib.apsp_cancel(self._h, ticket))

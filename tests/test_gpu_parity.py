@@ -1,0 +1,301 @@
+"""Parity of the CUDA path (through the C ABI) against the CPU oracle.
+
+Integer results must be bit-exact.  fp32 results must be within 1e-4
+relative of the float64 oracle, with exactly the same set of +inf entries.
+Inputs come from the seeded generators in ``gen``; expected values only from
+``oracle``.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+INF = oracle.INF32
+REL_TOL = 1e-4   # fp32 vs float64 oracle (spec tolerance)
+
+
+@pytest.fixture(scope="module")
+def H(lib):
+    h = lib.Handle(device=0)
+    yield h
+    h.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def er_edges(n, seed, deg=4.0, wmax=100, directed=False):
+    rng = np.random.default_rng(seed)
+    m = int(deg * n / (1 if directed else 2))
+    s = rng.integers(0, n, size=m)
+    d = rng.integers(0, n, size=m)
+    keep = s != d
+    s, d = s[keep], d[keep]
+    w = rng.integers(1, wmax + 1, size=s.shape[0])
+    return s, d, w
+
+
+def dense_directed(n, s, d, w, ld=None, dtype=np.int32, inf=INF):
+    return gen.dense_matrix(n, s, d, w, dtype=dtype, inf=inf, ld=ld, directed=True)
+
+
+def expect_fw(W):
+    return oracle.fw(np.asarray(W)[:, : W.shape[0]].astype(np.int64))
+
+
+# ------------------------------------------------------------------ min-plus product
+@pytest.mark.parametrize("m,k,n", [(1, 1, 1), (7, 3, 5), (128, 64, 128), (130, 65, 257), (300, 200, 140)])
+@pytest.mark.parametrize("dt", ["int32", "u16", "fp32"])
+def test_minplus_matches_oracle(H, m, k, n, dt):
+    rng = np.random.default_rng(m * 1000 + k * 10 + n)
+    if dt == "fp32":
+        A = rng.random((m, k), dtype=np.float32) * 50
+        B = rng.random((k, n), dtype=np.float32) * 50
+        C = rng.random((m, n), dtype=np.float32) * 120
+        A[rng.random(A.shape) < 0.2] = np.inf
+        B[rng.random(B.shape) < 0.2] = np.inf
+        got = H.minplus(dev(A), dev(B), dev(C)).cpu().numpy().astype(np.float64)
+        exp = oracle.minplus(A.astype(np.float64), B.astype(np.float64), C.astype(np.float64))
+        np.testing.assert_array_equal(np.isinf(got), np.isinf(exp))
+        f = np.isfinite(exp)
+        np.testing.assert_allclose(got[f], exp[f], rtol=REL_TOL, atol=0)
+        return
+    inf = INF if dt == "int32" else 0x7FFF
+    hi = 5000 if dt == "int32" else 16000
+    npdt = np.int32 if dt == "int32" else np.int16
+    A = rng.integers(0, hi, size=(m, k)); B = rng.integers(0, hi, size=(k, n)); C = rng.integers(0, 2 * hi, size=(m, n))
+    A[rng.random(A.shape) < 0.2] = inf
+    B[rng.random(B.shape) < 0.2] = inf
+    C[rng.random(C.shape) < 0.2] = inf
+    got = H.minplus(dev(A.astype(npdt)), dev(B.astype(npdt)), dev(C.astype(npdt))).cpu().numpy().astype(np.int64)
+    A64, B64, C64 = (np.where(x == inf, INF, x).astype(np.int64) for x in (A, B, C))
+    exp = oracle.minplus(A64, B64, C64)
+    if dt == "u16":
+        exp = np.where(exp >= 0x7FFF, 0x7FFF, exp)   # INF16 (and sums >= INF16 never win over C <= INF16)
+    np.testing.assert_array_equal(got, exp)
+
+
+# ------------------------------------------------------------------ int32 solves, odd sizes
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 33, 63, 64, 65, 127, 129, 200, 257, 513, 1000])
+def test_int32_solve_odd_sizes_bit_exact(H, n):
+    s, d, w = er_edges(n, seed=n, deg=3.0, wmax=1000)
+    W = gen.dense_matrix(n, s, d, w, dtype=np.int32)
+    D = H.solve_t("int32", dev(W)).cpu().numpy()
+    assert H.last_status() == 0
+    np.testing.assert_array_equal(D.astype(np.int64), expect_fw(W))
+
+
+@pytest.mark.parametrize("n,ld", [(100, 103), (129, 136), (250, 257)])
+def test_int32_padded_and_unaligned_leading_dimension(H, n, ld):
+    s, d, w = er_edges(n, seed=ld, deg=3.0)
+    W = gen.dense_matrix(n, s, d, w, dtype=np.int32, ld=ld)
+    Wd = dev(W)
+    guard = Wd[:, n:].clone()
+    D = H.solve_t("int32", Wd)
+    np.testing.assert_array_equal(D[:, :n].cpu().numpy().astype(np.int64), expect_fw(W))
+    # in place: the padding columns beyond n are never written
+    H.solve_t("int32", Wd, Wd)
+    np.testing.assert_array_equal(Wd[:, :n].cpu().numpy().astype(np.int64), expect_fw(W))
+    assert torch.equal(Wd[:, n:], guard)
+
+
+@pytest.mark.parametrize("n", [70, 300, 777])
+def test_directed_input_solved_exactly(H, n):
+    """Directed graphs: the row and column panels use both operand orders."""
+    s, d, w = er_edges(n, seed=n + 7, deg=4.0, directed=True)
+    W = dense_directed(n, s, d, w)
+    D = H.solve_t("int32", dev(W)).cpu().numpy()
+    np.testing.assert_array_equal(D.astype(np.int64), expect_fw(W))
+
+
+def test_disconnected_pairs_stay_exactly_inf(H):
+    n = 400
+    s, d, w = er_edges(n, seed=3, deg=0.7, wmax=1000)
+    W = gen.dense_matrix(n, s, d, w, dtype=np.int32)
+    D = H.solve_t("int32", dev(W)).cpu().numpy().astype(np.int64)
+    E = expect_fw(W)
+    assert (E == INF).any()
+    np.testing.assert_array_equal(D, E)
+    lab = oracle.components(n, s, d)
+    assert ((D == INF) == (lab[:, None] != lab[None, :])).all()
+
+
+def test_swiss_roll_512_int32(H):
+    g = gen.workload("roll512")
+    W = gen.dense_matrix(g.n, g.src, g.dst, g.w, dtype=np.int32)
+    D = H.solve_t("int32", dev(W)).cpu().numpy()
+    np.testing.assert_array_equal(D.astype(np.int64), expect_fw(W))
+
+
+def test_large_weights_near_inf_do_not_overflow(H):
+    n = 130
+    s = np.arange(n - 1); d = s + 1
+    w = np.full(n - 1, (INF - 1) // (n - 1))
+    W = gen.dense_matrix(n, s, d, w, dtype=np.int32)
+    D = H.solve_t("int32", dev(W)).cpu().numpy()
+    np.testing.assert_array_equal(D.astype(np.int64), expect_fw(W))
+
+
+# ------------------------------------------------------------------ packed 16-bit
+@pytest.mark.parametrize("n", [5, 64, 100, 257, 600])
+def test_u16_solve_bit_exact(H, n):
+    s, d, w = er_edges(n, seed=n + 1, deg=3.0, wmax=60)
+    W16 = gen.dense_matrix(n, s, d, w, dtype=np.int16, inf=0x7FFF)
+    D16 = H.solve_t("u16", dev(W16)).cpu().numpy()
+    E = expect_fw(gen.dense_matrix(n, s, d, w, dtype=np.int32))
+    assert E[E < INF].max() < 0x7FFF
+    np.testing.assert_array_equal(oracle.unpack_u16(D16.view(np.uint16)).astype(np.int64), E)
+
+
+def test_u16_odd_leading_dimension(H):
+    n, ld = 201, 203
+    s, d, w = er_edges(n, seed=11, deg=3.0, wmax=60)
+    W16 = gen.dense_matrix(n, s, d, w, dtype=np.int16, inf=0x7FFF, ld=ld)
+    D16 = H.solve_t("u16", dev(W16)).cpu().numpy()[:, :n]
+    E = expect_fw(gen.dense_matrix(n, s, d, w, dtype=np.int32))
+    np.testing.assert_array_equal(oracle.unpack_u16(D16.view(np.uint16)).astype(np.int64), E)
+
+
+def test_auto_uses_bound_and_matches_oracle(H):
+    g = gen.workload("roll512")
+    W = gen.dense_matrix(g.n, g.src, g.dst, g.w, dtype=np.int32)
+    bound, ok = H.int16_bound(dev(W))
+    eb, eok = oracle.int16_bound(g.n, g.src, g.dst, g.w)
+    assert (bound, ok) == (eb, eok) and ok
+    D = H.solve_t("auto", dev(W)).cpu().numpy()
+    np.testing.assert_array_equal(D.astype(np.int64), expect_fw(W))
+
+
+def test_auto_falls_back_to_int32_when_bound_fails(H):
+    n = 300
+    s = np.arange(n - 1); d = s + 1
+    w = np.full(n - 1, 200)   # path: 2 ecc(0) = 2 * 299 * 200 > 32767
+    W = gen.dense_matrix(n, s, d, w, dtype=np.int32)
+    bound, ok = H.int16_bound(dev(W))
+    assert bound == 2 * 299 * 200 and not ok
+    D = H.solve_t("auto", dev(W)).cpu().numpy()
+    np.testing.assert_array_equal(D.astype(np.int64), expect_fw(W))
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_int16_bound_matches_oracle_disconnected(H, seed):
+    n = 500
+    s, d, w = er_edges(n, seed=seed + 40, deg=1.2, wmax=300)
+    W = gen.dense_matrix(n, s, d, w, dtype=np.int32)
+    assert H.int16_bound(dev(W)) == oracle.int16_bound(n, s, d, w)
+
+
+def test_int16_bound_rejects_asymmetric(H):
+    n = 50
+    s, d, w = er_edges(n, seed=5, deg=3.0, directed=True)
+    W = dense_directed(n, s, d, w)
+    if (W == W.T).all():
+        pytest.skip("generator produced a symmetric matrix")
+    _, ok = H.int16_bound(dev(W))
+    assert not ok
+
+
+# ------------------------------------------------------------------ fp32
+@pytest.mark.parametrize("n", [65, 300, 1000])
+def test_fp32_within_tolerance(H, n):
+    pts = gen.gaussian_mixture(n, seed=n, dim=10, components=3)
+    s, d, dist = gen.knn_edges(pts, 6)
+    w32 = dist.astype(np.float32)
+    W = gen.dense_matrix(n, s, d, w32, dtype=np.float32)
+    D = H.solve_t("fp32", dev(W)).cpu().numpy().astype(np.float64)
+    E = oracle.fw(gen.dense_matrix(n, s, d, w32.astype(np.float64), dtype=np.float64))
+    np.testing.assert_array_equal(np.isinf(D), np.isinf(E))
+    f = np.isfinite(E) & (E > 0)
+    assert (np.abs(D[f] - E[f]) <= REL_TOL * E[f]).all()
+    assert (np.diag(D) == 0).all()
+
+
+# ------------------------------------------------------------------ edge-list path
+@pytest.mark.parametrize("dt", ["int32", "u16", "auto", "fp32"])
+def test_solve_edges(H, dt):
+    n = 333
+    s, d, w = er_edges(n, seed=9, deg=3.0, wmax=50)
+    # duplicates with larger weights and a self loop must not matter
+    s2 = np.concatenate([s, s[:10], [4]]); d2 = np.concatenate([d, d[:10], [4]]); w2 = np.concatenate([w, w[:10] + 5, [1]])
+    E = expect_fw(gen.dense_matrix(n, s, d, w, dtype=np.int32))
+    wt = {"int32": np.int32, "auto": np.int32, "u16": np.int16, "fp32": np.float32}[dt]
+    D = H.solve_edges(dt, dev(s2.astype(np.int32)), dev(d2.astype(np.int32)), dev(w2.astype(wt)), n).cpu().numpy()
+    assert H.last_status() == 0
+    if dt == "u16":
+        D = oracle.unpack_u16(D.view(np.uint16))
+    if dt == "fp32":
+        D = np.where(np.isinf(D), INF, D)
+    np.testing.assert_array_equal(D.astype(np.int64), E)
+
+
+def test_solve_edges_u16_refuses_when_bound_fails(H, lib):
+    n = 300
+    s = np.arange(n - 1); d = s + 1
+    w = np.full(n - 1, 200)
+    with pytest.raises(lib.ApspError) as ei:
+        H.solve_edges("u16", dev(s.astype(np.int32)), dev(d.astype(np.int32)), dev(w.astype(np.int16)), n)
+    assert ei.value.name == "APSP_E_RANGE"
+
+
+# ------------------------------------------------------------------ input checks
+def test_input_checks_reported(H, lib):
+    n = 40
+    s, d, w = er_edges(n, seed=1)
+    W = gen.dense_matrix(n, s, d, w, dtype=np.int32)
+    bad = W.copy(); bad[3, 5] = -2
+    H.solve_t("int32", dev(bad)); assert H.last_status() == 1
+    bad = W.copy(); bad[7, 7] = 3
+    H.solve_t("int32", dev(bad)); assert H.last_status() == 1
+    bad = W.copy(); bad[1, 2] = INF + 5
+    H.solve_t("int32", dev(bad)); assert H.last_status() == 4
+    H.solve_t("int32", dev(W)); assert H.last_status() == 0
+    with pytest.raises(lib.ApspError):
+        H.solve_t("int32", dev(W[:, :30]))   # ld < n is refused by the binding
+    Z = torch.zeros((0, 0), dtype=torch.int32, device="cuda")
+    H.solve_t("int32", Z)
+
+
+# ------------------------------------------------------------------ full-size workloads (sampled rows)
+def _sampled_rows_check(D_dev, g, nsample, seed, fp=False):
+    rng = np.random.default_rng(seed)
+    rows = np.sort(rng.choice(g.n, size=nsample, replace=False))
+    got = D_dev[torch.from_numpy(rows).cuda()].cpu().numpy()
+    if fp:
+        w = g.w.astype(np.float32).astype(np.float64)
+        exp = oracle.dijkstra(g.n, g.src, g.dst, w, rows)
+        got = got.astype(np.float64)
+        np.testing.assert_array_equal(np.isinf(got), np.isinf(exp))
+        f = np.isfinite(exp) & (exp > 0)
+        assert (np.abs(got[f] - exp[f]) <= REL_TOL * exp[f]).all()
+    else:
+        exp = oracle.dijkstra(g.n, g.src, g.dst, g.w, rows)
+        np.testing.assert_array_equal(got.astype(np.int64), exp)
+
+
+def test_gmm16k_int32_sampled(H):
+    g = gen.workload("gmm16k")
+    W = dev(gen.dense_matrix(g.n, g.src, g.dst, g.w, dtype=np.int32))
+    D = H.solve_t("int32", W)
+    _sampled_rows_check(D, g, 256, seed=1)
+    # symmetry and zero diagonal over the whole matrix (a property at any size)
+    assert torch.equal(D, D.T) and bool((torch.diagonal(D) == 0).all())
+
+
+def test_gmm16k_fp32_sampled(H):
+    g = gen.workload("gmm16k_f32")
+    W = dev(gen.dense_matrix(g.n, g.src, g.dst, g.w.astype(np.float32), dtype=np.float32))
+    D = H.solve_t("fp32", W)
+    _sampled_rows_check(D, g, 128, seed=2, fp=True)
+
+
+def test_gmm16k_auto_equals_int32(H):
+    g = gen.workload("gmm16k")
+    W = dev(gen.dense_matrix(g.n, g.src, g.dst, g.w, dtype=np.int32))
+    A = H.solve_t("auto", W)
+    B = H.solve_t("int32", W)
+    assert torch.equal(A, B)
