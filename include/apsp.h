@@ -197,6 +197,18 @@ const char *apsp_last_error(apsp_handle *h);
 /* Number of kernel launches this handle has issued (for launch accounting). */
 int64_t apsp_launch_count(apsp_handle *h);
 
+/* Per-phase device timing (measurement support; the paper has no counterpart
+ * beyond its wall-clock times of Sec. 5).  enable = 1: every later solve on
+ * this handle records a CUDA event pair around each Phase 1 / 2 / 3 launch on
+ * the solve's stream; enable = 0 stops recording.  apsp_profile_read waits for
+ * the recorded events and writes, for phases 0, 1, 2 (= Phase 1, 2, 3), the
+ * number of timed launches, their summed device time in ms, and their summed
+ * algorithmic relaxation counts (Phase 1: w^3, Phase 2: 2 (n-w) w^2, Phase 3:
+ * (n-w)^2 w for a round of width w); then it clears the record.  Any of the
+ * output arrays may be NULL. */
+apsp_status apsp_profile(apsp_handle *h, int enable);
+apsp_status apsp_profile_read(apsp_handle *h, int64_t launches[3], double ms[3], double relaxations[3]);
+
 #ifdef __cplusplus
 }
 #endif

@@ -12,9 +12,6 @@ CUDA tensors (device memory and streams are PyTorch's; nothing else is).
 """
 from __future__ import annotations
 
-import ctypes
-import os
-
 from ._lib import (  # noqa: F401
     APSP_AUTO,
     APSP_F32,
@@ -24,10 +21,17 @@ from ._lib import (  # noqa: F401
     INF_U16,
     ApspError,
     STATES,
-    lib,
+    get_lib,
     lib_path,
 )
 from .handle import Handle, dtype_code  # noqa: F401
 
-__all__ = ["Handle", "ApspError", "lib", "lib_path", "dtype_code", "INF_I32", "INF_U16",
+
+def __getattr__(name):
+    # ``paper_1902_04446_gb300.lib`` loads libapsp.so on first access
+    if name == "lib":
+        return get_lib()
+    raise AttributeError(name)
+
+__all__ = ["Handle", "ApspError", "get_lib", "lib_path", "dtype_code", "INF_I32", "INF_U16",
            "APSP_I32", "APSP_U16", "APSP_F32", "APSP_AUTO", "STATES"]

@@ -61,6 +61,9 @@ def _load():
         "apsp_strerror": (ctypes.c_char_p, [st]),
         "apsp_last_error": (ctypes.c_char_p, [H]),
         "apsp_launch_count": (i64, [H]),
+        "apsp_profile": (st, [H, i32]),
+        "apsp_profile_read": (st, [H, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -69,10 +72,19 @@ def _load():
     return L
 
 
-lib = _load()
+_L = None
+
+
+def get_lib():
+    """The loaded libapsp.so (loaded on first use; raises ImportError when it is not built)."""
+    global _L
+    if _L is None:
+        _L = _load()
+    return _L
 
 # every entry point of the header, for the export check
 ENTRY_POINTS = sorted(["apsp_config_default", "apsp_create", "apsp_destroy", "apsp_solve", "apsp_solve_t",
                        "apsp_solve_edges", "apsp_last_status", "apsp_int16_bound", "apsp_minplus", "apsp_pack_u16",
                        "apsp_unpack_u16", "apsp_submit", "apsp_poll", "apsp_wait", "apsp_fetch", "apsp_release",
-                       "apsp_cancel", "apsp_strerror", "apsp_last_error", "apsp_launch_count"])
+                       "apsp_cancel", "apsp_strerror", "apsp_last_error", "apsp_launch_count",
+                       "apsp_profile", "apsp_profile_read"])

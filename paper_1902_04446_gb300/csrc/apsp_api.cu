@@ -48,6 +48,63 @@ struct Request {
   cudaEvent_t done_ev = nullptr;
 };
 
+// Event pairs around phase launches (apsp_profile).
+struct Profiler : apsp::PhaseTimer {
+  struct Pair {
+    cudaEvent_t a, b;
+    int phase;
+    double relax;
+  };
+  std::vector<Pair> pairs;       // recorded, not yet read
+  std::vector<cudaEvent_t> pool; // free events
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  cudaEvent_t pending = nullptr;
+  void before(int, cudaStream_t s) override {
+    pending = get();
+    cudaEventRecord(pending, s);
+  }
+  void after(int phase, cudaStream_t s, double relax) override {
+    cudaEvent_t b = get();
+    cudaEventRecord(b, s);
+    pairs.push_back({pending, b, phase, relax});
+    pending = nullptr;
+  }
+  void read(int64_t *launches, double *ms, double *relax) {
+    for (int p = 0; p < 3; ++p) {
+      if (launches) launches[p] = 0;
+      if (ms) ms[p] = 0;
+      if (relax) relax[p] = 0;
+    }
+    for (Pair &q : pairs) {
+      cudaEventSynchronize(q.b);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, q.a, q.b);
+      if (launches) launches[q.phase] += 1;
+      if (ms) ms[q.phase] += t;
+      if (relax) relax[q.phase] += q.relax;
+      pool.push_back(q.a);
+      pool.push_back(q.b);
+    }
+    pairs.clear();
+  }
+  ~Profiler() {
+    for (Pair &q : pairs) {
+      cudaEventDestroy(q.a);
+      cudaEventDestroy(q.b);
+    }
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+};
+
 }  // namespace
 
 struct apsp_handle {
@@ -61,6 +118,7 @@ struct apsp_handle {
   int *h_status = nullptr;  // pinned
   std::string last_error;
   std::atomic<int64_t> launches{0};
+  std::unique_ptr<Profiler> prof;  // non-null while apsp_profile(h, 1) is on
 
   // ---- request loop
   std::mutex smu;
@@ -134,7 +192,7 @@ apsp_status run_rounds_locked(apsp_handle *h, int dtype, void *D, int64_t n, int
     return e == cudaErrorMemoryAllocation ? APSP_E_NOMEM : APSP_E_CUDA;
   }
   int64_t l = 0;
-  e = apsp::launch_rounds(dtype, D, ld, n, h->colT, ldT, s, &l);
+  e = apsp::launch_rounds(dtype, D, ld, n, h->colT, ldT, s, &l, h->prof.get());
   h->launches += l;
   if (e != cudaSuccess) {
     h->last_error = std::string("rounds: ") + cudaGetErrorString(e);
@@ -456,6 +514,34 @@ const char *apsp_last_error(apsp_handle *h) {
 }
 
 int64_t apsp_launch_count(apsp_handle *h) { return h ? h->launches.load() : 0; }
+
+apsp_status apsp_profile(apsp_handle *h, int enable) {
+  if (!h) return APSP_E_INVALID;
+  cudaSetDevice(h->cfg.device);
+  std::lock_guard<std::mutex> g(h->mu);
+  if (enable && !h->prof) h->prof.reset(new Profiler());
+  if (!enable && h->prof) {
+    cudaDeviceSynchronize();
+    h->prof.reset();
+  }
+  return APSP_OK;
+}
+
+apsp_status apsp_profile_read(apsp_handle *h, int64_t launches[3], double ms[3], double relaxations[3]) {
+  if (!h) return APSP_E_INVALID;
+  cudaSetDevice(h->cfg.device);
+  std::lock_guard<std::mutex> g(h->mu);
+  if (!h->prof) {
+    for (int p = 0; p < 3; ++p) {
+      if (launches) launches[p] = 0;
+      if (ms) ms[p] = 0;
+      if (relaxations) relaxations[p] = 0;
+    }
+    return APSP_OK;
+  }
+  h->prof->read(launches, ms, relaxations);
+  return APSP_OK;
+}
 
 }  // extern "C"
 

@@ -396,7 +396,7 @@ static inline unsigned grid_cols(int64_t n, int threads) {
 
 template <class Op, int BK>
 static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int64_t ldT, bool vec, cudaStream_t s,
-                               int64_t *launches) {
+                               int64_t *launches, PhaseTimer *tm) {
   using E = typename Op::elem;
   E *D = static_cast<E *>(Dv);
   E *colT = static_cast<E *>(colTv);
@@ -415,10 +415,19 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
   for (int64_t k = 0; k < q; ++k) {
     const int64_t p0 = k * BK;
     const int64_t p1 = (p0 + BK < n) ? p0 + BK : n;
+    const double w = (double)(p1 - p0), rest = (double)(n - (p1 - p0));
+    if (tm) tm->before(0, s);
     fw_phase1<Op, BK><<<1, P1_THREADS, 0, s>>>(D, ld, n, p0, colT, ldT);
-    fw_phase2<Op, BK><<<nrow + ncol, C2::THREADS, C2::SMEM, s>>>(D, ld, n, p0, p1, colT, ldT, nrow, vec ? 1 : 0);
-    if (q > 1) fw_phase3<Op, BK><<<g3, C3::THREADS, SMEM3, s>>>(D, ld, n, p0, p1, colT, ldT, vec ? 1 : 0);
-    if (launches) *launches += (q > 1) ? 3 : 2;
+    if (tm) tm->after(0, s, w * w * w);
+    if (q > 1) {
+      if (tm) tm->before(1, s);
+      fw_phase2<Op, BK><<<nrow + ncol, C2::THREADS, C2::SMEM, s>>>(D, ld, n, p0, p1, colT, ldT, nrow, vec ? 1 : 0);
+      if (tm) tm->after(1, s, 2.0 * rest * w * w);
+      if (tm) tm->before(2, s);
+      fw_phase3<Op, BK><<<g3, C3::THREADS, SMEM3, s>>>(D, ld, n, p0, p1, colT, ldT, vec ? 1 : 0);
+      if (tm) tm->after(2, s, rest * rest * w);
+    }
+    if (launches) *launches += (q > 1) ? 3 : 1;
   }
   return cudaGetLastError();
 }
@@ -428,12 +437,12 @@ static bool aligned16(const void *p, int64_t ld, size_t esz) {
 }
 
 cudaError_t launch_rounds(int dtype, void *D, int64_t ld, int64_t n, void *colT, int64_t ldT, cudaStream_t s,
-                          int64_t *launches) {
+                          int64_t *launches, PhaseTimer *tm) {
   if (n <= 0) return cudaSuccess;
   switch (dtype) {
-    case 0: return rounds_impl<OpI32, 64>(D, ld, n, colT, ldT, aligned16(D, ld, 4), s, launches);
-    case 1: return rounds_impl<OpU16, 64>(D, ld, n, colT, ldT, aligned16(D, ld, 2), s, launches);
-    case 2: return rounds_impl<OpF32, 64>(D, ld, n, colT, ldT, aligned16(D, ld, 4), s, launches);
+    case 0: return rounds_impl<OpI32, 64>(D, ld, n, colT, ldT, aligned16(D, ld, 4), s, launches, tm);
+    case 1: return rounds_impl<OpU16, 64>(D, ld, n, colT, ldT, aligned16(D, ld, 2), s, launches, tm);
+    case 2: return rounds_impl<OpF32, 64>(D, ld, n, colT, ldT, aligned16(D, ld, 4), s, launches, tm);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -5,13 +5,22 @@
 
 namespace apsp {
 
+// Optional per-phase timing hook: launch_rounds calls before()/after() around
+// every phase launch on the launch stream (phase 0, 1, 2 = Phase 1, 2, 3) and
+// passes the phase's algorithmic relaxation count.
+struct PhaseTimer {
+  virtual void before(int phase, cudaStream_t s) = 0;
+  virtual void after(int phase, cudaStream_t s, double relaxations) = 0;
+  virtual ~PhaseTimer() {}
+};
+
 // Round width Bk used by launch_rounds for a dtype.
 int64_t round_width(int dtype);
 
 // q rounds of Phase 1 -> Phase 2 -> Phase 3 on D (n x n, leading dimension ld).
 // colT is a Bk x ldT panel buffer, ldT a multiple of 256 elements and >= n.
 cudaError_t launch_rounds(int dtype, void *D, int64_t ld, int64_t n, void *colT, int64_t ldT, cudaStream_t s,
-                          int64_t *launches);
+                          int64_t *launches, PhaseTimer *timer = nullptr);
 // Copies W to D when they differ and checks the input (status |= 1 invalid, 2 range).
 cudaError_t launch_ingest(int dtype, const void *W, void *D, int64_t n, int64_t ld, int *status, cudaStream_t s,
                           int64_t *launches);

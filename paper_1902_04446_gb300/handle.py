@@ -3,7 +3,7 @@ from __future__ import annotations
 
 import ctypes
 
-from ._lib import APSP_AUTO, APSP_F32, APSP_I32, APSP_U16, ApspError, apsp_config, apsp_request, lib
+from ._lib import APSP_AUTO, APSP_F32, APSP_I32, APSP_U16, ApspError, apsp_config, apsp_request, get_lib
 
 _DT_NAMES = {"int32": APSP_I32, "i32": APSP_I32, "u16": APSP_U16, "uint16": APSP_U16, "u16x2": APSP_U16,
              "int16": APSP_U16, "fp32": APSP_F32, "f32": APSP_F32, "float32": APSP_F32, "auto": APSP_AUTO}
@@ -50,13 +50,17 @@ def _stream(stream, device):
     return stream.cuda_stream
 
 
+def _L():
+    return get_lib()
+
+
 class Handle:
     """Owns one ``apsp_handle`` (workspace, serving thread) on one device."""
 
     def __init__(self, device: int = 0, dtype="int32", max_batch: int = 64, queue_depth: int = 4096,
                  memory_budget: int = 0, spin_limit: int = 0, block_k: int = 0):
         cfg = apsp_config()
-        lib.apsp_config_default(ctypes.byref(cfg))
+        _L().apsp_config_default(ctypes.byref(cfg))
         cfg.device = device
         cfg.dtype = dtype_code(dtype)
         cfg.max_batch = max_batch
@@ -65,7 +69,7 @@ class Handle:
         cfg.spin_limit = spin_limit
         cfg.block_k = block_k
         h = ctypes.c_void_p()
-        st = lib.apsp_create(ctypes.byref(h), ctypes.byref(cfg))
+        st = _L().apsp_create(ctypes.byref(h), ctypes.byref(cfg))
         if st != 0:
             raise ApspError(st, "apsp_create")
         self._h = h
@@ -76,7 +80,7 @@ class Handle:
     # ------------------------------------------------------------ lifetime
     def close(self):
         if getattr(self, "_h", None):
-            lib.apsp_destroy(self._h)
+            _L().apsp_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -93,12 +97,24 @@ class Handle:
 
     def _check(self, st, where):
         if st != 0:
-            detail = lib.apsp_last_error(self._h).decode() if self._h else ""
+            detail = _L().apsp_last_error(self._h).decode() if self._h else ""
             raise ApspError(st, where, detail)
 
     @property
     def launch_count(self) -> int:
-        return int(lib.apsp_launch_count(self._h))
+        return int(_L().apsp_launch_count(self._h))
+
+    def profile(self, enable: bool = True):
+        """apsp_profile: record CUDA events around every phase launch of later solves."""
+        self._check(_L().apsp_profile(self._h, 1 if enable else 0), "apsp_profile")
+
+    def profile_read(self):
+        """apsp_profile_read: per phase (1, 2, 3) -> (launches, device ms, relaxations); clears the record."""
+        L = (ctypes.c_int64 * 3)()
+        M = (ctypes.c_double * 3)()
+        R = (ctypes.c_double * 3)()
+        self._check(_L().apsp_profile_read(self._h, L, M, R), "apsp_profile_read")
+        return {p + 1: (int(L[p]), float(M[p]), float(R[p])) for p in range(3)}
 
     # ------------------------------------------------------------ solves
     def solve_t(self, dtype, W, D=None, stream=None):
@@ -112,7 +128,7 @@ class Handle:
         nd, ldd = _mat(D, "D")
         if nd != n or ldd != ld or D.dtype != W.dtype:
             raise ValueError("D must have W's shape, leading dimension and dtype")
-        self._check(lib.apsp_solve_t(self._h, code, W.data_ptr(), n, ld, D.data_ptr(), _stream(stream, W.device)),
+        self._check(_L().apsp_solve_t(self._h, code, W.data_ptr(), n, ld, D.data_ptr(), _stream(stream, W.device)),
                     "apsp_solve_t")
         return D
 
@@ -137,14 +153,14 @@ class Handle:
                 raise TypeError("src/dst must be contiguous int32 CUDA tensors")
         if not w.is_contiguous() or not w.is_cuda or w.numel() != m:
             raise TypeError("w must be a contiguous CUDA tensor of m weights")
-        self._check(lib.apsp_solve_edges(self._h, code, src.data_ptr(), dst.data_ptr(), w.data_ptr(), m, n,
+        self._check(_L().apsp_solve_edges(self._h, code, src.data_ptr(), dst.data_ptr(), w.data_ptr(), m, n,
                                          D.data_ptr(), ld, _stream(stream, D.device)), "apsp_solve_edges")
         return D
 
     def last_status(self, stream=None) -> int:
         """apsp_last_status: the device-side input check of the last solve (0 = OK)."""
         import torch
-        return int(lib.apsp_last_status(self._h, _stream(stream, torch.device("cuda", self.device))))
+        return int(_L().apsp_last_status(self._h, _stream(stream, torch.device("cuda", self.device))))
 
     def int16_bound(self, W, stream=None):
         """apsp_int16_bound: (max_c 2 ecc(r_c), enabled) for an int32 adjacency matrix."""
@@ -152,7 +168,7 @@ class Handle:
         _elem_ok(W, APSP_I32)
         b = ctypes.c_int64()
         ok = ctypes.c_int()
-        self._check(lib.apsp_int16_bound(self._h, W.data_ptr(), n, ld, ctypes.byref(b), ctypes.byref(ok),
+        self._check(_L().apsp_int16_bound(self._h, W.data_ptr(), n, ld, ctypes.byref(b), ctypes.byref(ok),
                                          _stream(stream, W.device)), "apsp_int16_bound")
         return int(b.value), bool(ok.value)
 
@@ -167,7 +183,7 @@ class Handle:
         k2, n = B.shape
         if k2 != k or tuple(C.shape) != (m, n):
             raise ValueError("shape mismatch")
-        self._check(lib.apsp_minplus(self._h, code, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
+        self._check(_L().apsp_minplus(self._h, code, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
                                      C.data_ptr(), C.stride(0), m, k, n, _stream(stream, C.device)), "apsp_minplus")
         return C
 
@@ -179,7 +195,7 @@ class Handle:
         _elem_ok(W, APSP_I32)
         r = apsp_request(W.data_ptr(), 0 if W.is_cuda else 1, W.shape[0], W.stride(0))
         t = ctypes.c_uint64()
-        self._check(lib.apsp_submit(self._h, ctypes.byref(r), ctypes.byref(t)), "apsp_submit")
+        self._check(_L().apsp_submit(self._h, ctypes.byref(r), ctypes.byref(t)), "apsp_submit")
         self._hold[int(t.value)] = W
         return int(t.value)
 
@@ -187,27 +203,27 @@ class Handle:
         """apsp_poll: (state code, device pointer of the result or None, status)."""
         st = ctypes.c_int()
         p = ctypes.c_void_p()
-        rc = lib.apsp_poll(self._h, ticket, ctypes.byref(st), ctypes.byref(p))
+        rc = _L().apsp_poll(self._h, ticket, ctypes.byref(st), ctypes.byref(p))
         if rc == 6:
             raise ApspError(rc, "apsp_poll")
         return int(st.value), p.value, int(rc)
 
     def wait(self, ticket: int, timeout_ms: int = -1) -> int:
-        return int(lib.apsp_wait(self._h, ticket, timeout_ms))
+        return int(_L().apsp_wait(self._h, ticket, timeout_ms))
 
     def fetch(self, ticket: int, out, stream=None):
         """apsp_fetch into a (n, >=n) int32 tensor (host or device)."""
         import torch
         dev = out.device if out.is_cuda else torch.device("cuda", self.device)
-        self._check(lib.apsp_fetch(self._h, ticket, out.data_ptr(), out.stride(0), _stream(stream, dev)),
+        self._check(_L().apsp_fetch(self._h, ticket, out.data_ptr(), out.stride(0), _stream(stream, dev)),
                     "apsp_fetch")
         return out
 
     def release(self, ticket: int) -> int:
-        rc = int(lib.apsp_release(self._h, ticket))
+        rc = int(_L().apsp_release(self._h, ticket))
         if rc == 0:
             self._hold.pop(ticket, None)
         return rc
 
     def cancel(self, ticket: int) -> int:
-        return int(lib.apsp_cancel(self._h, ticket))
+        return int(_L().apsp_cancel(self._h, ticket))
