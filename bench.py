@@ -1,0 +1,472 @@
+#!/usr/bin/env python
+"""Benchmark of the blocked Floyd-Warshall APSP library on one GB300.
+
+Metric: APSP relaxations per second, n^3 / t (the paper's "ops" of Sec. 5.4),
+reported in GRelax/s.  One step = one apsp_solve of the whole workload matrix
+(ingest + q rounds of Phase 1 / 2 / 3), inputs resident in HBM; the matrix
+(1.07 GB at n = 16384) is larger than L2, so no extra flush is needed.
+
+Printed JSON line (rank 0): the headline int32 number, the packed-16-bit
+(automatic precision selection: bound + pack + u16x2 rounds + unpack) and fp32
+variants, the end-to-end number through host buffers, the live Phase-3
+roofline, the CPU-oracle baseline, clocks sampled during the timed region, and
+the serving replay (p50/p99 latency and solves/s against one-at-a-time solves).
+
+  python bench.py [--gpus N --steps K --warmup W] [--workload gmm16k]
+  python bench.py --impl reference ...   # the CPU oracle timed as the reference arm
+
+Multi-GPU (torchrun, N > 1): every rank solves its own replica of the workload
+(the solve is not sharded), timing is max over ranks, value = all ranks'
+relaxations / that time ("weak" scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import gen  # noqa: E402
+
+METRIC = "APSP GRelax/s (n³/s) int32 vs packed-int16; serving p50/p99 ms and solves/s"
+UNIT = "GRelax/s"
+ADDMIN_LANES_PER_CLK_PER_SM = 64  # measured add-min issue rate (profiles/addmin_issue_peak.md)
+WORKLOAD_TEXT = {
+    "gmm16k": "n=16384 symmetric k=10 kNN graph over a 10-D 8-component Gaussian mixture (seed 1), "
+              "int32 weights max(1, rint(50 d)), dense INF-padded adjacency matrix",
+    "roll64k": "n=65536 symmetric k=10 kNN Swiss-roll graph (seed 2), int32 weights max(1, rint(4 d))",
+    "roll512": "n=512 symmetric k=8 kNN Swiss-roll graph (seed 0), int32 weights max(1, rint(100 d))",
+}
+PAPER_CONTEXT = {
+    "source": "paper Table 3 (Blocked-CB, Spark, 64 Xeon Gold 6130 cores, n=16384 Erdos-Renyi): 2m50s",
+    "gops": 25.9,
+}
+
+
+# ----------------------------------------------------------------------------- helpers
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1902_04446_gb300", "csrc")
+    for f in ("fw_kernels.cu", "fw_device.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key: str):
+    """DRAM bytes per launch from a committed ncu summary, when it matches the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    cur = source_hash()
+    for line in open(p):
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == kernel_key and parts[1] == cur:
+            return float(parts[2])
+    return None
+
+
+def load_workload(name):
+    g = gen.workload(name)
+    W = gen.dense_matrix(g.n, g.src, g.dst, g.w, dtype=np.int32)
+    return g, W
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def timed_solves(torch, h, dtype, Wd, Dd, steps, warmup, dist=None, profile=False):
+    """Warm-up solves, then exactly `steps` solves bracketed by barrier + sync; returns (ms, launches, prof)."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        h.solve_t(dtype, Wd, Dd)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if profile:
+        h.profile(True)
+        h.profile_read()
+    l0 = h.launch_count
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        h.solve_t(dtype, Wd, Dd)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = h.launch_count - l0
+    prof = h.profile_read() if profile else None
+    if profile:
+        h.profile(False)
+    if h.last_status() != 0:
+        raise RuntimeError(f"input check failed during the {dtype} benchmark")
+    return ms, launches, prof
+
+
+def max_over_ranks(torch, dist, x):
+    if dist is None:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(torch, dist, x):
+    if dist is None:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def cpu_baseline(W, target_s=12.0):
+    """The oracle's Floyd-Warshall (single-threaded C) over a bounded slice of outer iterations."""
+    import oracle
+    n = W.shape[0]
+    D = W.astype(np.int64)
+    t0 = time.perf_counter()
+    D = oracle.fw(D, 0, 1)
+    t1 = time.perf_counter() - t0
+    kk = int(max(1, min(n - 1, target_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.fw(D, 1, 1 + kk)
+    dt = time.perf_counter() - t0
+    relax = kk * float(n) * n
+    return {"value": relax / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"outer iterations k=1..{kk} of the oracle's int64 Floyd-Warshall on the full "
+                      f"n={n} matrix ({kk}*n^2 relaxation steps, {dt:.1f} s on one host core)"}
+
+
+def serving_replay(torch, apsp, device, nreq, rate_scale=1.0):
+    """Replay the Poisson trace through apsp_submit/apsp_poll and through one-at-a-time solves."""
+    arrival, ns, seeds = gen.serving_trace(num=nreq)
+    arrival = arrival / rate_scale
+    mats = []
+    for s in seeds:
+        r = gen.graphs.serving_request(int(s))
+        n = r.n
+        W = torch.full((n, n), apsp.INF_I32, dtype=torch.int32, device=device)
+        src = torch.from_numpy(np.concatenate([r.src, r.dst])).to(device)
+        dst = torch.from_numpy(np.concatenate([r.dst, r.src])).to(device)
+        w = torch.from_numpy(np.concatenate([r.w, r.w]).astype(np.int32)).to(device)
+        W.view(-1).scatter_reduce_(0, src * n + dst, w, reduce="amin")
+        W.fill_diagonal_(0)
+        mats.append(W)
+    torch.cuda.synchronize()
+    relax = float(np.sum(ns.astype(np.float64) ** 3))
+
+    def pct(x, p):
+        return float(np.percentile(np.asarray(x), p))
+
+    # (a) continuous batching through the request loop
+    with apsp.Handle(device=device) as h:
+        # warm-up: one request per size class
+        for W in mats[:8]:
+            t = h.submit(W)
+            h.wait(t)
+            h.release(t)
+        lat = [None] * nreq
+        tickets = {}
+        pending = set()
+        t_start = time.perf_counter()
+        i = 0
+        while i < nreq or pending:
+            now = time.perf_counter() - t_start
+            while i < nreq and arrival[i] <= now:
+                tickets[i] = h.submit(mats[i])
+                pending.add(i)
+                i += 1
+            done = []
+            for j in pending:
+                st, _, rc = h.poll(tickets[j])
+                if st == 3:
+                    lat[j] = (time.perf_counter() - t_start) - arrival[j]
+                    done.append(j)
+                elif st == 4:
+                    raise RuntimeError(f"serving request {j} failed with status {rc}")
+            for j in done:
+                pending.discard(j)
+                h.release(tickets[j])
+            if not done and (i >= nreq or arrival[i] > now + 1e-4):
+                time.sleep(5e-5)
+        span = time.perf_counter() - t_start
+        batched = {"p50_ms": pct(lat, 50) * 1e3, "p99_ms": pct(lat, 99) * 1e3, "solves_per_s": nreq / span,
+                   "grelax_per_s": relax / span / 1e9}
+    # (b) one at a time, FIFO, each solve synchronized
+    with apsp.Handle(device=device) as h:
+        outs = [torch.empty_like(W) for W in mats[:8]]
+        for W, D in zip(mats[:8], outs):
+            h.solve_t("int32", W, D)
+        torch.cuda.synchronize()
+        lat = []
+        t_start = time.perf_counter()
+        for j in range(nreq):
+            now = time.perf_counter() - t_start
+            if arrival[j] > now:
+                time.sleep(arrival[j] - now)
+            D = torch.empty_like(mats[j])
+            h.solve_t("int32", mats[j], D)
+            torch.cuda.synchronize()
+            lat.append((time.perf_counter() - t_start) - arrival[j])
+        span = time.perf_counter() - t_start
+        single = {"p50_ms": pct(lat, 50) * 1e3, "p99_ms": pct(lat, 99) * 1e3, "solves_per_s": nreq / span,
+                  "grelax_per_s": relax / span / 1e9}
+    return {"requests": nreq, "offered_req_per_s": 200.0 * rate_scale,
+            "n": "log-uniform [128, 4096], ER avg degree 16 + spanning path, int32 weights U{1..1000}",
+            "batched": batched, "one_at_a_time": single}
+
+
+def run_gpu(args):
+    import torch
+
+    import paper_1902_04446_gb300 as apsp
+
+    ws, rank, local = dist_info()
+    dist = None
+    if ws > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    device = local
+    torch.cuda.set_device(device)
+    props = torch.cuda.get_device_properties(device)
+    g, W = load_workload(args.workload)
+    n = g.n
+    Wd = torch.from_numpy(W).to(device)
+    Dd = torch.empty_like(Wd)
+    h = apsp.Handle(device=device)
+
+    with ClockSampler(device) as clk:
+        ms, launches, prof = timed_solves(torch, h, "int32", Wd, Dd, args.steps, args.warmup, dist, profile=True)
+    clocks = clk.summary()
+    ms_max = max_over_ranks(torch, dist, ms)
+    relax_step = float(n) ** 3
+    value = sum_over_ranks(torch, dist, relax_step * args.steps) / (ms_max / 1e3) / 1e9
+
+    # roofline of the dominant kernel (Phase 3), from the live event timings
+    sms = props.multi_processor_count
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    n3, ms3, r3 = prof[3]
+    achieved = (r3 / n3) / (ms3 / n3 / 1e3) / 1e9 if n3 else None
+    peak = ADDMIN_LANES_PER_CLK_PER_SM * sms * sm_max_mhz * 1e6 / 1e9
+    phase_ms = {f"phase{p}": round(prof[p][1] / args.steps, 3) for p in (1, 2, 3)}
+    roofline = {"bound": "alu", "kernel": "fw_phase3<int32>", "achieved": achieved, "peak": peak, "unit": UNIT,
+                "frac": (achieved / peak) if achieved else None,
+                "peak_basis": f"{ADDMIN_LANES_PER_CLK_PER_SM} add-min lanes/clk/SM (measured) x {sms} SMs x "
+                              f"{sm_max_mhz:.0f} MHz (max SM clock)",
+                "traffic": ncu_traffic("fw_phase3_int32_gmm16k"),
+                "phase_ms_per_step": phase_ms,
+                "phase3_share_of_step": prof[3][1] / ms if ms else None}
+    if clocks and achieved:
+        roofline["frac_at_median_clock"] = achieved / (ADDMIN_LANES_PER_CLK_PER_SM * sms * clocks["sm_mhz"] / 1e3)
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "int32", "data": "synthetic",
+           "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT.get(args.workload, '')}", "n": n,
+                      "edges": int(g.src.shape[0]), "round_width": 64, "parallelism": f"replicas x{ws}",
+                      "l2": "input matrix larger than L2 (%.2f GB), no flush needed" % (n * n * 4 / 1e9)},
+           "roofline": roofline, "gpu_launches": int(launches), "clocks": clocks,
+           "paper_context": PAPER_CONTEXT}
+
+    # variants: automatic precision (bound + pack + packed u16x2 rounds + unpack) and fp32
+    if not args.no_variants:
+        ms16, l16, prof16 = timed_solves(torch, h, "auto", Wd, Dd, args.steps, args.warmup, dist, profile=True)
+        ms16 = max_over_ranks(torch, dist, ms16)
+        v16 = sum_over_ranks(torch, dist, relax_step * args.steps) / (ms16 / 1e3) / 1e9
+        n3, m3, r3 = prof16[3]
+        a16 = (r3 / n3) / (m3 / n3 / 1e3) / 1e9 if n3 else None
+        out["packed_u16"] = {"value": v16, "unit": UNIT, "ms_per_step": ms16 / args.steps,
+                             "speedup_vs_int32": v16 / value, "path": "apsp_solve(APSP_AUTO): bound pass, pack, "
+                             "u16x2 rounds, unpack (all inside the timed region)",
+                             "phase3_achieved": a16, "phase3_peak": 2 * peak,
+                             "phase3_frac": (a16 / (2 * peak)) if a16 else None, "gpu_launches": int(l16)}
+        Wf = torch.from_numpy(gen.dense_matrix(n, g.src, g.dst,
+                                               gen.workload("gmm16k_f32").w.astype(np.float32)
+                                               if args.workload == "gmm16k" else g.w.astype(np.float32),
+                                               dtype=np.float32)).to(device)
+        Df = torch.empty_like(Wf)
+        msf, lf, _ = timed_solves(torch, h, "fp32", Wf, Df, args.steps, args.warmup, dist)
+        msf = max_over_ranks(torch, dist, msf)
+        out["fp32"] = {"value": sum_over_ranks(torch, dist, relax_step * args.steps) / (msf / 1e3) / 1e9, "unit": UNIT,
+                       "ms_per_step": msf / args.steps,
+                       "weights": "raw Euclidean distances as fp32 (same points)", "gpu_launches": int(lf)}
+        del Wf, Df
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    Wh = torch.from_numpy(W).pin_memory()
+    Dh = torch.empty_like(Wh).pin_memory()
+    stream = torch.cuda.current_stream()
+    for _ in range(max(1, args.warmup)):
+        Wd.copy_(Wh, non_blocking=True)
+        h.solve_t("int32", Wd, Dd)
+        Dh.copy_(Dd, non_blocking=True)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        Wd.copy_(Wh, non_blocking=True)
+        h.solve_t("int32", Wd, Dd)
+        Dh.copy_(Dd, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if dist is not None:
+        dist.barrier()
+    mse = max_over_ranks(torch, dist, max(e0.elapsed_time(e1), wall * 1e3))
+    out["e2e"] = {"value": sum_over_ranks(torch, dist, relax_step * args.steps) / (mse / 1e3) / 1e9, "unit": UNIT,
+                  "h2d_bytes_per_step": int(Wh.numel() * 4), "d2h_bytes_per_step": int(Dh.numel() * 4),
+                  "ms_per_step": mse / args.steps}
+    del Wh, Dh
+    h.close()
+
+    if rank == 0 and not args.no_serving:
+        out["serving"] = serving_replay(torch, apsp, device, args.serving_requests)
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(W)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    """The CPU oracle as the reference arm: bounded slices of its Floyd-Warshall on the same matrix."""
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    import oracle
+    g, W = load_workload(args.workload)
+    n = g.n
+    D = W.astype(np.int64)
+    t0 = time.perf_counter()
+    D = oracle.fw(D, 0, 1)
+    per_k = time.perf_counter() - t0
+    kk = int(max(1, min(n // max(1, args.steps + args.warmup + 1), 2.0 / max(per_k, 1e-6))))
+    k = 1
+    for _ in range(args.warmup):
+        oracle.fw(D, k, k + kk)
+        k += kk
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        D = oracle.fw(D, k, min(n, k + kk))
+        k += kk
+    dt = time.perf_counter() - t0
+    value = args.steps * kk * float(n) * n / dt / 1e9
+    sample = (f"each step = {kk} outer iterations of the oracle's int64 Floyd-Warshall on the full n={n} "
+              f"matrix ({kk}*n^2 relaxation steps)")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+           "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT.get(args.workload, '')}", "n": n},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="gmm16k", choices=sorted(WORKLOAD_TEXT))
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=2000)
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

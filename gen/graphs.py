@@ -11,7 +11,8 @@ Readings of the workload recipes (recorded in DESIGN.md, "Input recipe"):
   lower vertex index, symmetrised by union (an edge if either endpoint lists
   the other).
 * Integer weights: max(1, rint(scale * distance)) with half-to-even rounding.
-* Erdos-Renyi: each unordered pair is an edge with p = deg / (n - 1); a
+* Erdos-Renyi: each unordered pair is an edge with p = deg / (n - 1) (drawn
+  as m ~ Binomial(N, p) distinct pairs out of the N pairs); a
   spanning path over a random permutation is added; weights U{1..wmax}; a
   duplicated pair keeps the smaller weight.
 * Serving trace: exponential inter-arrival gaps from seed 0; request i draws its
@@ -99,10 +100,20 @@ def er_graph(n: int, seed, avg_degree: float = 16.0, wmax: int = 1000):
     """
     rng = seed if isinstance(seed, np.random.Generator) else np.random.default_rng(seed)
     p = min(1.0, avg_degree / max(1, n - 1))
-    iu, ju = np.triu_indices(n, k=1)
-    mask = rng.random(iu.shape[0]) < p
-    s = iu[mask].astype(np.int64)
-    d = ju[mask].astype(np.int64)
+    # G(n, p): the number of edges is Binomial(N, p) over the N unordered
+    # pairs, and given that number the edge set is a uniform sample of pairs
+    N = n * (n - 1) // 2
+    m = int(rng.binomial(N, p)) if N > 0 else 0
+    idx = np.sort(rng.choice(N, size=m, replace=False)).astype(np.int64) if m else np.zeros(0, np.int64)
+    # pair index -> (i, j), i < j, in row-major order of the upper triangle
+    start = lambda i: i * (2 * n - i - 1) // 2  # noqa: E731
+    i = np.floor(((2 * n - 1) - np.sqrt((2.0 * n - 1) ** 2 - 8.0 * idx)) / 2).astype(np.int64)
+    i = np.clip(i, 0, max(0, n - 2))
+    for _ in range(3):
+        i = np.where(start(i + 1) <= idx, i + 1, i)
+        i = np.where(start(i) > idx, i - 1, i)
+    s = i
+    d = idx - start(i) + i + 1
     w = rng.integers(1, wmax + 1, size=s.shape[0]).astype(np.int64)
     perm = rng.permutation(n).astype(np.int64)
     ps, pd = perm[:-1], perm[1:]

@@ -229,7 +229,7 @@ def test_solve_edges(H, dt):
     if dt == "u16":
         D = oracle.unpack_u16(D.view(np.uint16))
     if dt == "fp32":
-        D = np.where(np.isinf(D), INF, D)
+        D = np.where(np.isinf(D), INF, D.astype(np.float64))
     np.testing.assert_array_equal(D.astype(np.int64), E)
 
 
