@@ -254,8 +254,13 @@ def test_input_checks_reported(H, lib):
     bad = W.copy(); bad[1, 2] = INF + 5
     H.solve_t("int32", dev(bad)); assert H.last_status() == 4
     H.solve_t("int32", dev(W)); assert H.last_status() == 0
-    with pytest.raises(lib.ApspError):
-        H.solve_t("int32", dev(W[:, :30]))   # ld < n is refused by the binding
+    with pytest.raises(ValueError):
+        H.solve_t("int32", dev(W[:, :30]))   # the binding refuses a matrix narrower than n
+    Wd = dev(W)
+    # the C ABI itself refuses ld < n and null pointers before touching the device
+    assert lib.lib.apsp_solve_t(H._h, 0, Wd.data_ptr(), n, n - 1, Wd.data_ptr(), None) == 1
+    assert lib.lib.apsp_solve_t(H._h, 0, None, n, n, Wd.data_ptr(), None) == 1
+    assert lib.lib.apsp_solve_t(H._h, 7, Wd.data_ptr(), n, n, Wd.data_ptr(), None) == 1
     Z = torch.zeros((0, 0), dtype=torch.int32, device="cuda")
     H.solve_t("int32", Z)
 
