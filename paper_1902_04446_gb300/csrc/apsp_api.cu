@@ -30,8 +30,6 @@ constexpr int64_t kDefaultMaxEdges = int64_t(1) << 26;
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
-size_t elem_size(int dtype) { return dtype == APSP_U16 ? 2 : 4; }
-
 struct Request {
   uint64_t ticket = 0;
   apsp_request req{};
@@ -185,7 +183,7 @@ int64_t panel_ld(int64_t n) { return round_up(n > 0 ? n : 1, 256); }
 apsp_status run_rounds_locked(apsp_handle *h, int dtype, void *D, int64_t n, int64_t ld, cudaStream_t s) {
   const int64_t bk = apsp::round_width(dtype);
   const int64_t ldT = panel_ld(n);
-  const size_t need = (size_t)bk * ldT * elem_size(dtype);
+  const size_t need = (size_t)bk * ldT * 4;  // panel buffer of 32-bit words
   cudaError_t e = ensure(&h->colT, &h->colT_bytes, need);
   if (e != cudaSuccess) {
     h->last_error = std::string("panel workspace: ") + cudaGetErrorString(e);

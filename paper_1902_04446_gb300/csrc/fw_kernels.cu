@@ -18,15 +18,22 @@
 // vertex t, and D_kk(i, t) already holds the best way to reach t.
 //
 // Layout: D is the caller's row-major matrix (n rows of ld elements).  colT is
-// a library-owned BK x ldT buffer (ldT a multiple of 256 elements, >= n):
-// colT[t][i] = D[i][p0 + t] after Phase 2.  Elements outside the matrix are
-// read as INF; INF never improves a finite value, so ragged edges need no
-// other handling.
+// a library-owned BK x ldT buffer of 32-bit words (ldT a multiple of 256,
+// >= n): after Phase 2, colT[t][i] holds D[i][p0 + t] as an A-operand word
+// (for packed 16-bit the value sits in both lanes).  Elements outside the
+// matrix are read as INF; INF never improves a finite value, so ragged edges
+// need no other handling.
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <mutex>
+
+#include <cudaTypedefs.h>
+
 #include "fw_device.cuh"
 #include "fw_launch.h"
+#include "tma.cuh"
 
 namespace apsp {
 
@@ -35,8 +42,7 @@ constexpr int P1_THREADS = 256;
 // ---------------------------------------------------------------- Phase 1
 template <class Op, int BK>
 __global__ void __launch_bounds__(P1_THREADS) fw_phase1(typename Op::elem *__restrict__ D, int64_t ld, int64_t n,
-                                                        int64_t p0, typename Op::elem *__restrict__ colT,
-                                                        int64_t ldT) {
+                                                        int64_t p0, uint32_t *__restrict__ colT, int64_t ldT) {
   using S = typename Op::scalar;
   constexpr int G = 16;        // 16 x 16 thread grid
   constexpr int PT = BK / G;   // each thread owns PT x PT entries
@@ -81,29 +87,20 @@ __global__ void __launch_bounds__(P1_THREADS) fw_phase1(typename Op::elem *__res
   }
   for (int idx = tid; idx < BK * BK; idx += P1_THREADS) {
     const int t = idx / BK, i = idx % BK;
-    colT[t * ldT + p0 + i] = Op::from_s(s[i][t]);
+    colT[t * ldT + p0 + i] = Op::dup(Op::from_s(s[i][t]));
   }
 }
 
 // ---------------------------------------------------------------- smem loaders
-// As[t][i] = dup(colT[t][i0 + i]) for t < BK, i < BM (colT rows are aligned).
-template <class Op, int BM, int BK, int NT>
-__device__ __forceinline__ void load_As_colT(uint32_t *As, const typename Op::elem *__restrict__ colT, int64_t ldT,
-                                             int64_t i0, int tid) {
+// As[t][i] = colT[t][i0 + i] for t < BK, i < BM (colT rows are aligned words).
+template <int BM, int BK, int NT>
+__device__ __forceinline__ void load_As_colT(uint32_t *As, const uint32_t *__restrict__ colT, int64_t ldT, int64_t i0,
+                                             int tid) {
   constexpr int CH = BK * BM / 4;
   for (int c = tid; c < CH; c += NT) {
     const int t = c / (BM / 4);
     const int i = (c % (BM / 4)) * 4;
-    const typename Op::elem *p = colT + t * ldT + i0 + i;
-    uint4 v;
-    if constexpr (Op::EPW == 1) {
-      v = __ldg(reinterpret_cast<const uint4 *>(p));
-    } else {
-      const uint2 u = __ldg(reinterpret_cast<const uint2 *>(p));
-      v = make_uint4(Op::dup((typename Op::elem)(u.x & 0xFFFFu)), Op::dup((typename Op::elem)(u.x >> 16)),
-                     Op::dup((typename Op::elem)(u.y & 0xFFFFu)), Op::dup((typename Op::elem)(u.y >> 16)));
-    }
-    *reinterpret_cast<uint4 *>(As + t * BM + i) = v;
+    *reinterpret_cast<uint4 *>(As + t * BM + i) = __ldg(reinterpret_cast<const uint4 *>(colT + t * ldT + i0 + i));
   }
 }
 
@@ -157,8 +154,8 @@ struct P2Cfg {
 
 template <class Op, int BK>
 __global__ void __launch_bounds__(128) fw_phase2(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
-                                                 int64_t p1, typename Op::elem *__restrict__ colT, int64_t ldT,
-                                                 int nrow_ctas, int vec) {
+                                                 int64_t p1, uint32_t *__restrict__ colT, int64_t ldT, int nrow_ctas,
+                                                 int vec) {
   using C = P2Cfg<Op, BK>;
   extern __shared__ __align__(16) uint32_t smem[];
   const int tid = threadIdx.x;
@@ -170,7 +167,7 @@ __global__ void __launch_bounds__(128) fw_phase2(typename Op::elem *__restrict__
     uint32_t *Bs = smem + BK * C::ROW_BM;
     const int tx = tid % Map::TX, ty = tid / Map::TX;
     const int64_t col0 = (int64_t)blockIdx.x * C::ROW_BNW * Op::EPW;
-    load_As_colT<Op, C::ROW_BM, BK, C::THREADS>(As, colT, ldT, p0, tid);
+    load_As_colT<C::ROW_BM, BK, C::THREADS>(As, colT, ldT, p0, tid);
     load_Bs_rows<Op, C::ROW_BNW, BK, C::THREADS>(Bs, D, ld, n, n, p0, col0, vec, tid);
     load_acc<Op, C::ROW_BM, C::ROW_BNW>(D, ld, n, n, p0, col0, vec, acc, ty, tx);
     __syncthreads();
@@ -189,7 +186,7 @@ __global__ void __launch_bounds__(128) fw_phase2(typename Op::elem *__restrict__
     __syncthreads();
     tile_minplus<Op, C::COL_BM, C::COL_BNW, BK>(As, Bs, acc, ty, tx);
     store_acc<Op, C::COL_BM, C::COL_BNW>(D, ld, n, n, row0, p0, p0, p1, 0, 0, vec, acc, ty, tx);
-    // transposed copy: colT[t][row0 + i] = D_Ik[i][t] for rows outside [p0, p1)
+    // transposed copy: colT[t][row0 + i] = word(D_Ik[i][t]) for rows outside [p0, p1)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
 #pragma unroll
@@ -203,26 +200,19 @@ __global__ void __launch_bounds__(128) fw_phase2(typename Op::elem *__restrict__
 #pragma unroll
           for (int lane = 0; lane < Op::EPW; ++lane) {
             const int t = w * Op::EPW + lane;
-            typename Op::elem e4[4];
+            uint32_t q4[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               const uint32_t word = acc[4 * g + q][4 * h + cw];
-              e4[q] = bits_elem<Op>(Op::EPW == 2 ? (lane ? (word >> 16) : (word & 0xFFFFu)) : word);
+              q4[q] = (Op::EPW == 2) ? Op::dup(bits_elem<Op>(lane ? (word >> 16) : (word & 0xFFFFu))) : word;
             }
-            typename Op::elem *dst = colT + (int64_t)t * ldT + rb;
+            uint32_t *dst = colT + (int64_t)t * ldT + rb;
             if (all_out) {
-              if constexpr (Op::EPW == 1) {
-                *reinterpret_cast<uint4 *>(dst) =
-                    make_uint4(elem_bits<Op>(e4[0]), elem_bits<Op>(e4[1]), elem_bits<Op>(e4[2]), elem_bits<Op>(e4[3]));
-              } else {
-                *reinterpret_cast<uint2 *>(dst) =
-                    make_uint2(elem_bits<Op>(e4[0]) | (elem_bits<Op>(e4[1]) << 16),
-                               elem_bits<Op>(e4[2]) | (elem_bits<Op>(e4[3]) << 16));
-              }
+              *reinterpret_cast<uint4 *>(dst) = make_uint4(q4[0], q4[1], q4[2], q4[3]);
             } else {
 #pragma unroll
               for (int q = 0; q < 4; ++q)
-                if (rb + q < p0 || rb + q >= p1) dst[q] = e4[q];
+                if (rb + q < p0 || rb + q >= p1) dst[q] = q4[q];
             }
           }
         }
@@ -240,9 +230,8 @@ struct P3Cfg {
 
 template <class Op, int BK>
 __global__ void __launch_bounds__(256, 2) fw_phase3(typename Op::elem *__restrict__ D, int64_t ld, int64_t n,
-                                                    int64_t p0, int64_t p1,
-                                                    const typename Op::elem *__restrict__ colT, int64_t ldT,
-                                                    int vec) {
+                                                    int64_t p0, int64_t p1, const uint32_t *__restrict__ colT,
+                                                    int64_t ldT, int vec) {
   using Cfg = P3Cfg<Op>;
   using Map = TileMap<Cfg::BM, Cfg::BNW>;
   extern __shared__ __align__(16) uint32_t smem[];
@@ -253,12 +242,131 @@ __global__ void __launch_bounds__(256, 2) fw_phase3(typename Op::elem *__restric
   const int64_t row0 = (int64_t)blockIdx.y * Cfg::BM;
   const int64_t col0 = (int64_t)blockIdx.x * Cfg::BNW * Op::EPW;
   uint32_t acc[8][8];
-  load_As_colT<Op, Cfg::BM, BK, Cfg::THREADS>(As, colT, ldT, row0, tid);
+  load_As_colT<Cfg::BM, BK, Cfg::THREADS>(As, colT, ldT, row0, tid);
   load_Bs_rows<Op, Cfg::BNW, BK, Cfg::THREADS>(Bs, D, ld, n, n, p0, col0, vec, tid);
   load_acc<Op, Cfg::BM, Cfg::BNW>(D, ld, n, n, row0, col0, vec, acc, ty, tx);
   __syncthreads();
   tile_minplus<Op, Cfg::BM, Cfg::BNW, BK>(As, Bs, acc, ty, tx);
   store_acc<Op, Cfg::BM, Cfg::BNW>(D, ld, n, n, row0, col0, p0, p1, p0, p1, vec, acc, ty, tx);
+}
+
+// ---------------------------------------------------------------- Phase 3, persistent + TMA
+// One CTA per SM walks a contiguous range of output tiles (row-major over the
+// tile grid).  Shared memory holds two stages of {A tile 64 x 128 words, B tile
+// 64 x 128 words} and one C tile (128 x 128 words): while the add-min loop
+// runs on tile i, TMA brings tile i+1's operands into the other stage and its
+// C block into the C buffer; results go back to D from registers.
+//   A = colT[0..64)[row0 .. row0+128)   (column panel, transposed, words)
+//   B = D[p0 .. p0+64)[col0 ..)         (row panel)
+//   C = D[row0 .. row0+128)[col0 ..)
+// TMA fills out-of-range elements with zeros.  That only reaches (a) C and B
+// columns >= n, which feed output columns that are never stored, (b) C rows
+// >= n, never stored, and (c) B rows >= n of the last, partial round, which
+// meet A words colT[t][.] that Phases 1 and 2 set to INF for those t, so the
+// sum is INF and never wins.
+constexpr int P3T_THREADS = 256;
+constexpr int P3T_STAGE_BYTES = 2 * 64 * 128 * 4;  // A + B, BK = 64
+constexpr int P3T_C_BYTES = 128 * 128 * 4;
+constexpr int P3T_SMEM = 2 * P3T_STAGE_BYTES + P3T_C_BYTES + 1024;
+constexpr uint32_t P3T_WAIT_LIMIT = 1u << 26;
+
+template <class Op>
+__global__ void __launch_bounds__(P3T_THREADS, 1)
+    fw_phase3_tma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                  const __grid_constant__ CUtensorMap mapC, typename Op::elem *__restrict__ D, int64_t ld, int64_t n,
+                  int64_t p0, int64_t p1, int tiles_x, int tiles_total, int *err) {
+  constexpr int BM = 128, BNW = 128, BK = 64;
+  using Map = TileMap<BM, BNW>;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t bar_ab[2];
+  __shared__ __align__(8) uint64_t bar_c;
+  __shared__ int abort_flag;
+  uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // stage s: A at base + s * STAGE, B right after it; C after both stages
+  auto stA = [&](int s) { return reinterpret_cast<uint32_t *>(base + s * P3T_STAGE_BYTES); };
+  auto stB = [&](int s) { return reinterpret_cast<uint32_t *>(base + s * P3T_STAGE_BYTES) + BK * BM; };
+  uint32_t *Cs = reinterpret_cast<uint32_t *>(base + 2 * P3T_STAGE_BYTES);
+
+  const int tid = threadIdx.x;
+  const int tx = tid % Map::TX, ty = tid / Map::TX;
+  const int per = tiles_total / (int)gridDim.x, extra = tiles_total % (int)gridDim.x;
+  const int t_begin = (int)blockIdx.x * per + min((int)blockIdx.x, extra);
+  const int t_end = t_begin + per + ((int)blockIdx.x < extra ? 1 : 0);
+  if (t_begin >= t_end) return;
+
+  if (tid == 0) {
+    mbar_init(&bar_ab[0], 1);
+    mbar_init(&bar_ab[1], 1);
+    mbar_init(&bar_c, 1);
+    fence_barrier_init();
+    prefetch_tensormap(&mapA);
+    prefetch_tensormap(&mapB);
+    prefetch_tensormap(&mapC);
+    abort_flag = 0;
+  }
+  __syncthreads();
+
+  auto tile_row0 = [&](int t) { return (t / tiles_x) * BM; };
+  auto tile_col0 = [&](int t) { return (t % tiles_x) * BNW * Op::EPW; };
+  auto issue_ab = [&](int t, int s) {
+    mbar_arrive_expect_tx(&bar_ab[s], P3T_STAGE_BYTES);
+    tma_load_2d(stA(s), &mapA, &bar_ab[s], tile_row0(t), 0);
+    tma_load_2d(stB(s), &mapB, &bar_ab[s], tile_col0(t), (int)p0);
+  };
+  auto issue_c = [&](int t) {
+    mbar_arrive_expect_tx(&bar_c, P3T_C_BYTES);
+    tma_load_2d(Cs, &mapC, &bar_c, tile_col0(t), tile_row0(t));
+  };
+  if (tid == 0) {
+    issue_ab(t_begin, 0);
+    issue_c(t_begin);
+  }
+  // parity of the next completion of bar_c (bit 0) and bar_ab[s] (bit 1 + s);
+  // `pend` has the same bits set while a copy on that barrier is in flight
+  uint32_t par = 0u, pend = 1u | 2u;
+  uint32_t acc[8][8];
+  for (int t = t_begin; t < t_end; ++t) {
+    const int s = (t - t_begin) & 1;
+    if (!mbar_wait_bounded(&bar_c, par & 1u, P3T_WAIT_LIMIT)) abort_flag = 1;
+    par ^= 1u;
+    pend &= ~1u;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(Cs + Map::row(ty, r) * BNW + Map::wcol(tx, h));
+        acc[r][4 * h + 0] = v.x;
+        acc[r][4 * h + 1] = v.y;
+        acc[r][4 * h + 2] = v.z;
+        acc[r][4 * h + 3] = v.w;
+      }
+    }
+    __syncthreads();  // C buffer read by all; stage s^1 no longer read (tile t-1 done)
+    if (abort_flag) break;
+    if (t + 1 < t_end) {
+      if (tid == 0) {
+        issue_c(t + 1);
+        issue_ab(t + 1, s ^ 1);
+      }
+      pend |= 1u | (2u << (s ^ 1));
+    }
+    const uint32_t bit = 2u << s;
+    if (!mbar_wait_bounded(&bar_ab[s], (par & bit) ? 1u : 0u, P3T_WAIT_LIMIT)) abort_flag = 1;
+    par ^= bit;
+    pend &= ~bit;
+    __syncwarp();
+    if (abort_flag) break;
+    tile_minplus<Op, BM, BNW, BK>(stA(s), stB(s), acc, ty, tx);
+    store_acc<Op, BM, BNW>(D, ld, n, n, tile_row0(t), tile_col0(t), p0, p1, p0, p1, true, acc, ty, tx);
+  }
+  if (abort_flag && tid == 0) {
+    // a wait gave up: wait (bounded) for this CTA's copies still in flight
+    // before the CTA's shared memory is released
+    if (pend & 1u) mbar_wait_bounded(&bar_c, par & 1u, P3T_WAIT_LIMIT);
+    for (int st = 0; st < 2; ++st)
+      if (pend & (2u << st)) mbar_wait_bounded(&bar_ab[st], (par & (2u << st)) ? 1u : 0u, P3T_WAIT_LIMIT);
+  }
+  if (abort_flag && tid == 0) atomicOr(err, 4);
 }
 
 // ---------------------------------------------------------------- general min-plus
@@ -388,6 +496,56 @@ __global__ void scatter_edges_kernel(const int32_t *__restrict__ src, const int3
 }
 
 // ---------------------------------------------------------------- host launchers
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 2-D row-major tensor map: dims {cols, rows}, row pitch in bytes, box {bx, by}.
+static bool make_map(CUtensorMap *m, CUtensorMapDataType dt, const void *base, uint64_t cols, uint64_t rows,
+                     uint64_t pitch, uint32_t bx, uint32_t by) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {pitch};
+  cuuint32_t box[2] = {bx, by};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(m, dt, 2, const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+static int sm_count() {
+  int dev = 0, c = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+  return c > 0 ? c : 1;
+}
+
+static int *error_word() {
+  // one device word per process and device for bounded-wait timeouts (rare)
+  static int *w[64] = {nullptr};
+  static std::mutex mu;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> g(mu);
+  if (dev < 0 || dev >= 64) return nullptr;
+  if (!w[dev]) {
+    if (cudaMalloc(&w[dev], sizeof(int)) != cudaSuccess) return nullptr;
+    cudaMemset(w[dev], 0, sizeof(int));
+  }
+  return w[dev];
+}
+
 static inline unsigned grid_rows(int64_t n) { return (unsigned)(n < 65535 ? (n > 0 ? n : 1) : 65535); }
 static inline unsigned grid_cols(int64_t n, int threads) {
   int64_t g = (n + threads - 1) / threads;
@@ -399,7 +557,7 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
                                int64_t *launches, PhaseTimer *tm) {
   using E = typename Op::elem;
   E *D = static_cast<E *>(Dv);
-  E *colT = static_cast<E *>(colTv);
+  uint32_t *colT = static_cast<uint32_t *>(colTv);
   using C2 = P2Cfg<Op, BK>;
   using C3 = P3Cfg<Op>;
   constexpr int SMEM3 = (BK * C3::BM + BK * C3::BNW) * 4;
@@ -408,6 +566,29 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(fw_phase3<Op, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM3);
   if (e != cudaSuccess) return e;
+  // persistent TMA Phase 3 when D is 16-byte addressable (otherwise the
+  // per-tile kernel with scalar edge handling)
+  CUtensorMap mA, mB, mC;
+  bool tma = vec && BK == 64;
+  int *err = nullptr;
+  if (tma) {
+    constexpr CUtensorMapDataType dt = Op::DTYPE == 1   ? CU_TENSOR_MAP_DATA_TYPE_UINT16
+                                       : Op::DTYPE == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                        : CU_TENSOR_MAP_DATA_TYPE_INT32;
+    tma = make_map(&mA, CU_TENSOR_MAP_DATA_TYPE_UINT32, colT, (uint64_t)ldT, (uint64_t)BK, (uint64_t)ldT * 4, 128,
+                   64) &&
+          make_map(&mB, dt, D, (uint64_t)n, (uint64_t)n, (uint64_t)ld * sizeof(E), 128 * Op::EPW, 64) &&
+          make_map(&mC, dt, D, (uint64_t)n, (uint64_t)n, (uint64_t)ld * sizeof(E), 128 * Op::EPW, 128);
+    err = tma ? error_word() : nullptr;
+    tma = tma && err != nullptr;
+    if (tma) {
+      e = cudaFuncSetAttribute(fw_phase3_tma<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, P3T_SMEM);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  const int tiles_x = (int)((n + 128 * Op::EPW - 1) / (128 * Op::EPW));
+  const int tiles_total = tiles_x * (int)((n + 127) / 128);
+  const int grid_tma = std::min(sm_count(), tiles_total);
   const int64_t q = (n + BK - 1) / BK;
   const int nrow = (int)((n + C2::ROW_BNW * Op::EPW - 1) / (C2::ROW_BNW * Op::EPW));
   const int ncol = (int)((n + C2::COL_BM - 1) / C2::COL_BM);
@@ -424,7 +605,11 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
       fw_phase2<Op, BK><<<nrow + ncol, C2::THREADS, C2::SMEM, s>>>(D, ld, n, p0, p1, colT, ldT, nrow, vec ? 1 : 0);
       if (tm) tm->after(1, s, 2.0 * rest * w * w);
       if (tm) tm->before(2, s);
-      fw_phase3<Op, BK><<<g3, C3::THREADS, SMEM3, s>>>(D, ld, n, p0, p1, colT, ldT, vec ? 1 : 0);
+      if (tma)
+        fw_phase3_tma<Op><<<grid_tma, P3T_THREADS, P3T_SMEM, s>>>(mA, mB, mC, D, ld, n, p0, p1, tiles_x, tiles_total,
+                                                                  err);
+      else
+        fw_phase3<Op, BK><<<g3, C3::THREADS, SMEM3, s>>>(D, ld, n, p0, p1, colT, ldT, vec ? 1 : 0);
       if (tm) tm->after(2, s, rest * rest * w);
     }
     if (launches) *launches += (q > 1) ? 3 : 1;

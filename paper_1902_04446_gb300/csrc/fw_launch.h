@@ -18,7 +18,7 @@ struct PhaseTimer {
 int64_t round_width(int dtype);
 
 // q rounds of Phase 1 -> Phase 2 -> Phase 3 on D (n x n, leading dimension ld).
-// colT is a Bk x ldT panel buffer, ldT a multiple of 256 elements and >= n.
+// colT is a Bk x ldT panel buffer of 32-bit words, ldT a multiple of 256 and >= n.
 cudaError_t launch_rounds(int dtype, void *D, int64_t ld, int64_t n, void *colT, int64_t ldT, cudaStream_t s,
                           int64_t *launches, PhaseTimer *timer = nullptr);
 // Copies W to D when they differ and checks the input (status |= 1 invalid, 2 range).
