@@ -200,36 +200,39 @@ def sum_over_ranks(torch, dist, x):
     return float(t.item())
 
 
-def _oracle_slices(W, target_s):
-    """Times the oracle's Floyd-Warshall on a bounded slice of outer iterations k.
+def sample_graph(workload: str, n_s: int):
+    """The workload's generator recipe at a smaller vertex count (for the CPU oracle)."""
+    if workload.startswith("gmm"):
+        s, d, dist = gen.knn_edges(gen.gaussian_mixture(n_s, 1), 10)
+        return s, d, gen.int_weights(dist, 50.0)
+    if workload.startswith("roll"):
+        k, scale, seed = {"roll512": (8, 100.0, 0), "roll64k": (10, 4.0, 2)}.get(workload, (10, 4.0, 2))
+        s, d, dist = gen.knn_edges(gen.swiss_roll(n_s, seed), k)
+        return s, d, gen.int_weights(dist, scale)
+    return gen.er_graph(n_s, 8)
 
-    The first call touches the matrix (page faults) and is not timed; the slice
-    length is then calibrated on 8 iterations so that the timed slice takes
-    about target_s seconds.
+
+def oracle_full_fw(workload: str, n_s: int):
+    """Times the oracle's complete Floyd-Warshall on the workload's recipe at n_s vertices.
+
+    A complete run is the honest sample: a slice of early outer iterations
+    would be much faster than the whole (the oracle skips rows whose d(i,k) is
+    still INF, and early in the run most are).
     """
     import oracle
-    n = W.shape[0]
-    D = oracle.fw(W.astype(np.int64), 0, 1)
+    s, d, w = sample_graph(workload, n_s)
+    W = gen.dense_matrix(n_s, s, d, w, dtype=np.int64)
     t0 = time.perf_counter()
-    D = oracle.fw(D, 1, 9)
-    per_k = (time.perf_counter() - t0) / 8
-    kk = int(max(1, min(n - 9, target_s / max(per_k, 1e-9))))
-    return D, kk, 9
+    oracle.fw(W)
+    return time.perf_counter() - t0
 
 
-def cpu_baseline(W, target_s=15.0):
-    """The oracle's Floyd-Warshall (single-threaded C) over a bounded slice of outer iterations."""
-    import oracle
-    n = W.shape[0]
-    D, kk, k0 = _oracle_slices(W, target_s)
-    t0 = time.perf_counter()
-    oracle.fw(D, k0, k0 + kk)
-    dt = time.perf_counter() - t0
-    relax = kk * float(n) * n
-    return {"value": relax / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"outer iterations k={k0}..{k0 + kk - 1} of the oracle's int64 Floyd-Warshall on the full "
-                      f"n={n} matrix ({kk}*n^2 relaxation steps, {dt:.1f} s on one host core); the oracle skips "
-                      f"rows whose d(i,k) is INF, so on this 8-component graph it does about 1/8 of them"}
+def cpu_baseline(workload: str, n_s: int = 4096):
+    """The oracle (single-threaded C Floyd-Warshall), complete run on a bounded sample of the workload."""
+    dt = oracle_full_fw(workload, n_s)
+    return {"value": float(n_s) ** 3 / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"the oracle's complete int64 Floyd-Warshall on the same generator recipe at n={n_s} "
+                      f"({dt:.1f} s on one host core); value = n^3 / t"}
 
 
 def serving_replay(torch, apsp, device, nreq, rate_scale=1.0):
@@ -428,7 +431,7 @@ def run_gpu(args):
     if rank == 0 and not args.no_serving:
         out["serving"] = serving_replay(torch, apsp, device, args.serving_requests)
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(W)
+        out["cpu_baseline"] = cpu_baseline(args.workload)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
@@ -437,31 +440,24 @@ def run_gpu(args):
 
 
 # ----------------------------------------------------------------------------- reference arm
-def run_reference(args):
-    """The CPU oracle as the reference arm: bounded slices of its Floyd-Warshall on the same matrix."""
+def run_reference(args, n_s: int = 2048):
+    """The CPU oracle as the reference arm: each step is its complete Floyd-Warshall on a bounded sample."""
     ws, rank, _ = dist_info()
     if rank != 0:
         return
-    import oracle
-    g, W = load_workload(args.workload)
-    n = g.n
-    D, kk, k = _oracle_slices(W, 3.0)
-    kk = max(1, min(kk, (n - k) // max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        oracle.fw(D, k, k + kk)
-        k += kk
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        D = oracle.fw(D, k, min(n, k + kk))
-        k += kk
-    dt = time.perf_counter() - t0
-    value = args.steps * kk * float(n) * n / dt / 1e9
-    sample = (f"each step = {kk} outer iterations of the oracle's int64 Floyd-Warshall on the full n={n} "
-              f"matrix ({kk}*n^2 relaxation steps)")
+        oracle_full_fw(args.workload, n_s)
+    times = [oracle_full_fw(args.workload, n_s) for _ in range(args.steps)]
+    dt = sum(times)
+    value = args.steps * float(n_s) ** 3 / dt / 1e9
+    sample = (f"each step = the oracle's complete int64 Floyd-Warshall on the workload's generator recipe at "
+              f"n={n_s} (one host core); value = n^3 / t")
+    n = {"gmm16k": 16384, "er8k": 8192, "er16k": 16384, "roll64k": 65536, "roll512": 512}.get(args.workload)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-           "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT.get(args.workload, '')}", "n": n},
+           "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT.get(args.workload, '')}", "n": n,
+                      "sample_n": n_s},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)

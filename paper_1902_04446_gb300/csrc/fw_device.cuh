@@ -104,7 +104,16 @@ __device__ __forceinline__ void chunk_set(uint4 &v, int e, uint32_t bits) {
 // 16-byte aligned and ld * sizeof(elem) is a multiple of 16, so that a chunk
 // starting at a multiple of 4*EPW is one aligned 16-byte access inside row r
 // (the row holds ld >= ncols elements).
-template <class Op>
+// CG = true reads through L2 only (ld.global.cg): required for data that other
+// CTAs of the same launch wrote (the batched persistent kernel); otherwise the
+// read-only path is used.
+template <bool CG>
+__device__ __forceinline__ uint4 ld16(const void *p) {
+  if constexpr (CG) return __ldcg(reinterpret_cast<const uint4 *>(p));
+  else return __ldg(reinterpret_cast<const uint4 *>(p));
+}
+
+template <class Op, bool CG = false>
 __device__ __forceinline__ uint4 load_chunk(const typename Op::elem *M, int64_t ld, int64_t nrows, int64_t ncols,
                                             int64_t r, int64_t c0, bool vec) {
   constexpr int E = 4 * Op::EPW;
@@ -112,7 +121,7 @@ __device__ __forceinline__ uint4 load_chunk(const typename Op::elem *M, int64_t 
   if (r < 0 || r >= nrows || c0 >= ncols) return v;
   const typename Op::elem *p = M + r * ld + c0;
   if (vec && c0 + E <= ld) {
-    v = __ldg(reinterpret_cast<const uint4 *>(p));
+    v = ld16<CG>(p);
     if (c0 + E > ncols) {
 #pragma unroll
       for (int e = 0; e < E; ++e)
@@ -121,7 +130,10 @@ __device__ __forceinline__ uint4 load_chunk(const typename Op::elem *M, int64_t 
   } else {
 #pragma unroll
     for (int e = 0; e < E; ++e)
-      if (c0 + e < ncols) chunk_set<Op>(v, e, elem_bits<Op>(p[e]));
+      if (c0 + e < ncols) {
+        if constexpr (CG) chunk_set<Op>(v, e, elem_bits<Op>(__ldcg(p + e)));
+        else chunk_set<Op>(v, e, elem_bits<Op>(p[e]));
+      }
   }
   return v;
 }
@@ -199,7 +211,7 @@ __device__ __forceinline__ void tile_minplus(const uint32_t *__restrict__ As, co
 
 // Loads the thread's 8 x 8 word block of the output tile whose top-left
 // element is (row0, col0) from M (INF outside [0,nrows) x [0,ncols)).
-template <class Op, int BM, int BNW>
+template <class Op, int BM, int BNW, bool CG = false>
 __device__ __forceinline__ void load_acc(const typename Op::elem *M, int64_t ld, int64_t nrows, int64_t ncols,
                                          int64_t row0, int64_t col0, bool vec, uint32_t (&acc)[8][8], int ty,
                                          int tx) {
@@ -208,8 +220,8 @@ __device__ __forceinline__ void load_acc(const typename Op::elem *M, int64_t ld,
   for (int r = 0; r < 8; ++r) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const uint4 v = load_chunk<Op>(M, ld, nrows, ncols, row0 + Map::row(ty, r),
-                                     col0 + (int64_t)Map::wcol(tx, h) * Op::EPW, vec);
+      const uint4 v = load_chunk<Op, CG>(M, ld, nrows, ncols, row0 + Map::row(ty, r),
+                                         col0 + (int64_t)Map::wcol(tx, h) * Op::EPW, vec);
       acc[r][4 * h + 0] = v.x;
       acc[r][4 * h + 1] = v.y;
       acc[r][4 * h + 2] = v.z;
@@ -237,6 +249,51 @@ __device__ __forceinline__ void store_acc(typename Op::elem *M, int64_t ld, int6
       const uint4 v = make_uint4(acc[r][4 * h + 0], acc[r][4 * h + 1], acc[r][4 * h + 2], acc[r][4 * h + 3]);
       store_chunk<Op>(M, ld, row, c0, v, cm, vec);
     }
+  }
+}
+
+// As[t][i] = colT[t][i0 + i] for t < BK, i < BM (colT rows are aligned words).
+template <int BM, int BK, int NT, bool CG = false>
+__device__ __forceinline__ void load_As_colT(uint32_t *As, const uint32_t *__restrict__ colT, int64_t ldT, int64_t i0,
+                                             int tid) {
+  constexpr int CH = BK * BM / 4;
+  for (int c = tid; c < CH; c += NT) {
+    const int t = c / (BM / 4);
+    const int i = (c % (BM / 4)) * 4;
+    *reinterpret_cast<uint4 *>(As + t * BM + i) = ld16<CG>(colT + t * ldT + i0 + i);
+  }
+}
+
+// Bs[t][w] = word w of row (r0 + t), element columns c0 .. c0 + BNW*EPW.
+template <class Op, int BNW, int BK, int NT, bool CG = false>
+__device__ __forceinline__ void load_Bs_rows(uint32_t *Bs, const typename Op::elem *__restrict__ M, int64_t ld,
+                                             int64_t nrows, int64_t ncols, int64_t r0, int64_t c0, bool vec,
+                                             int tid) {
+  constexpr int CH = BK * BNW / 4;
+  for (int c = tid; c < CH; c += NT) {
+    const int t = c / (BNW / 4);
+    const int w = (c % (BNW / 4)) * 4;
+    const uint4 v = load_chunk<Op, CG>(M, ld, nrows, ncols, r0 + t, c0 + (int64_t)w * Op::EPW, vec);
+    *reinterpret_cast<uint4 *>(Bs + t * BNW + w) = v;
+  }
+}
+
+// As[t][i] = dup(M[i0 + i][c0 + t]) for t < BK, i < BM: a transposing load of a
+// BM x BK block (consecutive threads take consecutive rows, so the scalar
+// shared-memory stores hit consecutive banks).
+template <class Op, int BM, int BK, int NT, bool CG = false>
+__device__ __forceinline__ void load_As_transposed(uint32_t *As, const typename Op::elem *__restrict__ M, int64_t ld,
+                                                   int64_t nrows, int64_t ncols, int64_t i0, int64_t c0, bool vec,
+                                                   int tid) {
+  constexpr int E = 4 * Op::EPW;
+  constexpr int CH = BM * (BK / E);
+  for (int c = tid; c < CH; c += NT) {
+    const int i = c % BM;
+    const int tq = (c / BM) * E;
+    const uint4 v = load_chunk<Op, CG>(M, ld, nrows, ncols, i0 + i, c0 + tq, vec);
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      As[(tq + e) * BM + i] = Op::dup(bits_elem<Op>(chunk_get<Op>(v, e)));
   }
 }
 

@@ -92,50 +92,7 @@ __global__ void __launch_bounds__(P1_THREADS) fw_phase1(typename Op::elem *__res
 }
 
 // ---------------------------------------------------------------- smem loaders
-// As[t][i] = colT[t][i0 + i] for t < BK, i < BM (colT rows are aligned words).
-template <int BM, int BK, int NT>
-__device__ __forceinline__ void load_As_colT(uint32_t *As, const uint32_t *__restrict__ colT, int64_t ldT, int64_t i0,
-                                             int tid) {
-  constexpr int CH = BK * BM / 4;
-  for (int c = tid; c < CH; c += NT) {
-    const int t = c / (BM / 4);
-    const int i = (c % (BM / 4)) * 4;
-    *reinterpret_cast<uint4 *>(As + t * BM + i) = __ldg(reinterpret_cast<const uint4 *>(colT + t * ldT + i0 + i));
-  }
-}
-
-// Bs[t][w] = word w of row (r0 + t), element columns c0 .. c0 + BNW*EPW.
-template <class Op, int BNW, int BK, int NT>
-__device__ __forceinline__ void load_Bs_rows(uint32_t *Bs, const typename Op::elem *__restrict__ M, int64_t ld,
-                                             int64_t nrows, int64_t ncols, int64_t r0, int64_t c0, bool vec,
-                                             int tid) {
-  constexpr int CH = BK * BNW / 4;
-  for (int c = tid; c < CH; c += NT) {
-    const int t = c / (BNW / 4);
-    const int w = (c % (BNW / 4)) * 4;
-    const uint4 v = load_chunk<Op>(M, ld, nrows, ncols, r0 + t, c0 + (int64_t)w * Op::EPW, vec);
-    *reinterpret_cast<uint4 *>(Bs + t * BNW + w) = v;
-  }
-}
-
-// As[t][i] = dup(M[i0 + i][c0 + t]) for t < BK, i < BM: a transposing load of a
-// BM x BK block (consecutive threads take consecutive rows, so the scalar
-// shared-memory stores hit consecutive banks).
-template <class Op, int BM, int BK, int NT>
-__device__ __forceinline__ void load_As_transposed(uint32_t *As, const typename Op::elem *__restrict__ M, int64_t ld,
-                                                   int64_t nrows, int64_t ncols, int64_t i0, int64_t c0, bool vec,
-                                                   int tid) {
-  constexpr int E = 4 * Op::EPW;
-  constexpr int CH = BM * (BK / E);
-  for (int c = tid; c < CH; c += NT) {
-    const int i = c % BM;
-    const int tq = (c / BM) * E;
-    const uint4 v = load_chunk<Op>(M, ld, nrows, ncols, i0 + i, c0 + tq, vec);
-#pragma unroll
-    for (int e = 0; e < E; ++e)
-      As[(tq + e) * BM + i] = Op::dup(bits_elem<Op>(chunk_get<Op>(v, e)));
-  }
-}
+// shared-memory loaders: load_As_colT, load_Bs_rows, load_As_transposed (fw_device.cuh)
 
 // ---------------------------------------------------------------- Phase 2
 // Row-panel CTAs: tile BK x 128 words; column-panel CTAs: tile
