@@ -75,7 +75,7 @@ typedef struct apsp_handle apsp_handle;
 typedef struct {
   int device;            /* CUDA device ordinal (the handle makes it current in every call) */
   int dtype;             /* apsp_dtype used by apsp_solve (default APSP_I32) */
-  int block_k;           /* round width Bk; 0 = the built-in choice (64) */
+  int block_k;           /* round width Bk (32 or 64); 0 = tuned (apsp_autotune) or 64 */
   int max_batch;         /* serving: graphs per persistent launch (default 64) */
   int queue_depth;       /* serving: pending requests before APSP_E_BUSY (default 4096) */
   int64_t memory_budget; /* serving: bytes of device memory for admitted requests (0 = free HBM - reserve) */
@@ -122,7 +122,8 @@ apsp_status apsp_solve_edges(apsp_handle *h, int dtype, const int32_t *src, cons
 
 /* Waits for `stream` and returns the device-side input check of the last
  * solve on this handle: APSP_OK, APSP_E_INVALID (negative weight or non-zero
- * diagonal) or APSP_E_RANGE (a finite weight >= INF). */
+ * diagonal), APSP_E_RANGE (a finite weight >= INF) or, after
+ * apsp_solve_batch, APSP_E_TIMEOUT (a bounded device wait gave up). */
 apsp_status apsp_last_status(apsp_handle *h, void *stream);
 
 /* The 16-bit enable test by itself (north-star "precision selection"): for
@@ -133,6 +134,26 @@ apsp_status apsp_last_status(apsp_handle *h, void *stream);
  * (*bound < APSP_INF_U16).  Synchronizes `stream`. */
 apsp_status apsp_int16_bound(apsp_handle *h, const int32_t *W, int64_t n, int64_t ld, int64_t *bound, int *ok,
                              void *stream);
+
+/* ---- batched solve (north-star "batching") ------------------------------- */
+/* Solves `count` int32 graphs of uneven n in ONE persistent launch on
+ * `stream`: the rounds of every graph (Alg. 3/4 phases) are cut into tasks
+ * that resident CTAs pull from a device work queue in dependency order, so
+ * rounds of different graphs overlap on the device.  W[i], D[i] are device
+ * matrices (n[i] rows of ld[i] elements, W[i] == D[i] allowed).  Asynchronous;
+ * apsp_last_status() reports the input checks of all graphs and
+ * APSP_E_TIMEOUT if a bounded device wait gave up.  Errors: APSP_E_INVALID,
+ * APSP_E_NOMEM (workspace), APSP_E_CUDA. */
+apsp_status apsp_solve_batch(apsp_handle *h, int64_t count, const int32_t *const *W, const int64_t *n,
+                             const int64_t *ld, int32_t *const *D, void *stream);
+
+/* Diagnostic of the bounded device waits (no paper counterpart): runs one
+ * batched launch over a small built-in graph whose first task waits on a
+ * device flag that nothing sets, with the given spin limit (> 0).  Returns
+ * APSP_E_TIMEOUT when the kernel gave up and reported it (the expected
+ * outcome), APSP_OK if it did not wait, or another error.  Synchronizes the
+ * device; the context stays usable. */
+apsp_status apsp_check_bounded_wait(apsp_handle *h, int64_t spin_limit);
 
 /* ---- building blocks (Table 1) ------------------------------------------ */
 /* C = min(C, A (x) B): the min-plus product ("MatProd") followed by the
@@ -189,6 +210,22 @@ apsp_status apsp_release(apsp_handle *h, uint64_t ticket);
 
 /* Cancels a request that has not started running; running requests finish. */
 apsp_status apsp_cancel(apsp_handle *h, uint64_t ticket);
+
+/* ---- autotuner ---------------------------------------------------------- */
+/* The paper picks its block size b per problem size (Sec. 3 "user-provided
+ * (or auto-tuned)", Sec. 5.2-5.4, Table 3).  For `dtype` and every n bucket
+ * (powers of two from 128 up to n_max) this times the candidate round shapes
+ * -- round width Bk in {32, 64} x Phase-3 variant (persistent TMA kernel or
+ * one CTA per tile) -- on a synthetic matrix generated on the device (the
+ * kernels do the same work for any graph of a given n), and keeps the
+ * fastest for later solves on this handle.  cache_path (nullable): a JSON
+ * file keyed by GPU name; entries for this GPU are loaded instead of timing
+ * when present, and new results are written back.  Synchronizes the device. */
+apsp_status apsp_autotune(apsp_handle *h, int dtype, int64_t n_max, const char *cache_path);
+
+/* The round shape the handle uses for (dtype, n): *block_k and *tma (1 =
+ * persistent TMA Phase 3). */
+apsp_status apsp_tuned_config(apsp_handle *h, int dtype, int64_t n, int *block_k, int *tma);
 
 /* ---- diagnostics -------------------------------------------------------- */
 const char *apsp_strerror(apsp_status s);

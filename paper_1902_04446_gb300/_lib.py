@@ -62,6 +62,11 @@ def _load():
         "apsp_last_error": (ctypes.c_char_p, [H]),
         "apsp_launch_count": (i64, [H]),
         "apsp_profile": (st, [H, i32]),
+        "apsp_solve_batch": (st, [H, i64, ctypes.POINTER(vp), ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                  ctypes.POINTER(vp), vp]),
+        "apsp_check_bounded_wait": (st, [H, i64]),
+        "apsp_autotune": (st, [H, i32, i64, ctypes.c_char_p]),
+        "apsp_tuned_config": (st, [H, i32, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "apsp_profile_read": (st, [H, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double)]),
     }
@@ -87,4 +92,5 @@ ENTRY_POINTS = sorted(["apsp_config_default", "apsp_create", "apsp_destroy", "ap
                        "apsp_solve_edges", "apsp_last_status", "apsp_int16_bound", "apsp_minplus", "apsp_pack_u16",
                        "apsp_unpack_u16", "apsp_submit", "apsp_poll", "apsp_wait", "apsp_fetch", "apsp_release",
                        "apsp_cancel", "apsp_strerror", "apsp_last_error", "apsp_launch_count",
-                       "apsp_profile", "apsp_profile_read"])
+                       "apsp_profile", "apsp_profile_read", "apsp_solve_batch", "apsp_check_bounded_wait",
+                       "apsp_autotune", "apsp_tuned_config"])

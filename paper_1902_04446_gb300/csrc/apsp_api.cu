@@ -11,6 +11,8 @@
 #include <condition_variable>
 #include <cstdio>
 #include <cstring>
+#include <fstream>
+#include <sstream>
 #include <deque>
 #include <map>
 #include <memory>
@@ -22,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/apsp.h"
+#include "batch.h"
 #include "fw_launch.h"
 
 namespace {
@@ -30,20 +33,35 @@ constexpr int64_t kDefaultMaxEdges = int64_t(1) << 26;
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+// A group: requests admitted together and solved by one batched launch on
+// one stream.
+struct Group {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t copy_ev = nullptr;  // all inputs copied (callers may reuse W)
+  cudaEvent_t done_ev = nullptr;  // batched launch finished
+  void *ws = nullptr;             // plan tables + panel buffers (freed at completion)
+  int *status = nullptr;          // device words: [i] input checks of request i, [count] kernel errors
+  apsp::BatchGraph *graphs_dev = nullptr;
+  std::vector<uint64_t> tickets;
+  int64_t transient = 0;          // budget bytes returned at completion
+  bool finished = false;
+  ~Group() {
+    if (copy_ev) cudaEventDestroy(copy_ev);
+    if (done_ev) cudaEventDestroy(done_ev);
+  }
+};
+
 struct Request {
   uint64_t ticket = 0;
   apsp_request req{};
-  int64_t bytes = 0;
+  int64_t bytes = 0;      // n^2 * 4 (held until release)
+  int64_t transient = 0;  // panel share (held until the group finishes)
   bool admitted = false;
-  bool finished = false;  // done event observed complete
-  bool released = false;
+  bool finished = false;
   apsp_status err = APSP_OK;
   void *D = nullptr;
-  void *colT = nullptr;
-  int *status = nullptr;
-  cudaStream_t stream = nullptr;
-  cudaEvent_t copy_ev = nullptr;
-  cudaEvent_t done_ev = nullptr;
+  std::shared_ptr<Group> group;
+  int gidx = -1;
 };
 
 // Event pairs around phase launches (apsp_profile).
@@ -112,11 +130,14 @@ struct apsp_handle {
   size_t colT_bytes = 0;
   void *ws16 = nullptr;
   size_t ws16_bytes = 0;
+  void *wsb = nullptr;  // batched solve: plan + panel buffers
+  size_t wsb_bytes = 0;
   int *d_status = nullptr;
   int *h_status = nullptr;  // pinned
   std::string last_error;
   std::atomic<int64_t> launches{0};
   std::unique_ptr<Profiler> prof;  // non-null while apsp_profile(h, 1) is on
+  std::map<std::pair<int, int64_t>, apsp::RoundConfig> tuned;  // (dtype, n bucket) -> round shape
 
   // ---- request loop
   std::mutex smu;
@@ -129,7 +150,7 @@ struct apsp_handle {
   std::map<uint64_t, std::unique_ptr<Request>> reqs;  // every live ticket
   int64_t budget = 0;
   int64_t used = 0;
-  int running = 0;
+  std::vector<std::shared_ptr<Group>> groups;  // in flight
   std::vector<cudaStream_t> free_streams;
 };
 
@@ -179,9 +200,31 @@ bool valid_dtype(int d) { return d == APSP_I32 || d == APSP_U16 || d == APSP_F32
 
 int64_t panel_ld(int64_t n) { return round_up(n > 0 ? n : 1, 256); }
 
+int64_t bucket_of(int64_t n) {
+  int64_t b = 128;
+  while (b < n) b <<= 1;
+  return b;
+}
+
+// Round shape for (dtype, n): a forced block_k, else the tuned bucket (the
+// largest tuned bucket for larger n), else Bk = 64 with the TMA Phase 3.
+apsp::RoundConfig config_for(apsp_handle *h, int dtype, int64_t n) {
+  apsp::RoundConfig c;
+  if (h->cfg.block_k == 32 || h->cfg.block_k == 64) {
+    c.bk = h->cfg.block_k;
+    return c;
+  }
+  const int64_t b = bucket_of(n);
+  auto it = h->tuned.find({dtype, b});
+  if (it != h->tuned.end()) return it->second;
+  for (auto r = h->tuned.rbegin(); r != h->tuned.rend(); ++r)
+    if (r->first.first == dtype && r->first.second < b) return r->second;
+  return c;
+}
+
 // Enqueues the q rounds on D (already holding W) using the handle's panel buffer.
 apsp_status run_rounds_locked(apsp_handle *h, int dtype, void *D, int64_t n, int64_t ld, cudaStream_t s) {
-  const int64_t bk = apsp::round_width(dtype);
+  const int64_t bk = apsp::kMaxRoundWidth;
   const int64_t ldT = panel_ld(n);
   const size_t need = (size_t)bk * ldT * 4;  // panel buffer of 32-bit words
   cudaError_t e = ensure(&h->colT, &h->colT_bytes, need);
@@ -190,7 +233,7 @@ apsp_status run_rounds_locked(apsp_handle *h, int dtype, void *D, int64_t n, int
     return e == cudaErrorMemoryAllocation ? APSP_E_NOMEM : APSP_E_CUDA;
   }
   int64_t l = 0;
-  e = apsp::launch_rounds(dtype, D, ld, n, h->colT, ldT, s, &l, h->prof.get());
+  e = apsp::launch_rounds(dtype, D, ld, n, h->colT, ldT, s, &l, h->prof.get(), config_for(h, dtype, n));
   h->launches += l;
   if (e != cudaSuccess) {
     h->last_error = std::string("rounds: ") + cudaGetErrorString(e);
@@ -292,7 +335,7 @@ apsp_status apsp_create(apsp_handle **out, const apsp_config *cfg) {
   apsp_config_default(&c);
   if (cfg) c = *cfg;
   if (c.dtype != APSP_AUTO && !valid_dtype(c.dtype)) return APSP_E_INVALID;
-  if (c.block_k != 0 && c.block_k != 64) return APSP_E_INVALID;
+  if (c.block_k != 0 && c.block_k != 32 && c.block_k != 64) return APSP_E_INVALID;
   if (c.max_batch <= 0) c.max_batch = 64;
   if (c.queue_depth <= 0) c.queue_depth = 4096;
   int ndev = 0;
@@ -312,13 +355,7 @@ apsp_status apsp_create(apsp_handle **out, const apsp_config *cfg) {
 
 static void free_request_device(Request *r) {
   if (r->D) cudaFree(r->D);
-  if (r->colT) cudaFree(r->colT);
-  if (r->status) cudaFree(r->status);
-  if (r->copy_ev) cudaEventDestroy(r->copy_ev);
-  if (r->done_ev) cudaEventDestroy(r->done_ev);
-  r->D = r->colT = nullptr;
-  r->status = nullptr;
-  r->copy_ev = r->done_ev = nullptr;
+  r->D = nullptr;
 }
 
 apsp_status apsp_destroy(apsp_handle *h) {
@@ -333,9 +370,17 @@ apsp_status apsp_destroy(apsp_handle *h) {
   cudaDeviceSynchronize();
   for (auto &kv : h->reqs) free_request_device(kv.second.get());
   h->reqs.clear();
+  for (auto &g : h->groups) {
+    if (g->ws) cudaFree(g->ws);
+    if (g->status) cudaFree(g->status);
+    g->ws = nullptr;
+    g->status = nullptr;
+  }
+  h->groups.clear();
   for (cudaStream_t s : h->free_streams) cudaStreamDestroy(s);
   if (h->colT) cudaFree(h->colT);
   if (h->ws16) cudaFree(h->ws16);
+  if (h->wsb) cudaFree(h->wsb);
   if (h->d_status) cudaFree(h->d_status);
   if (h->h_status) cudaFreeHost(h->h_status);
   delete h;
@@ -434,6 +479,10 @@ apsp_status apsp_last_status(apsp_handle *h, void *stream) {
     return APSP_E_CUDA;
   }
   const int st = *h->h_status;
+  if (st & 4) {
+    h->last_error = "a bounded device wait gave up";
+    return APSP_E_TIMEOUT;
+  }
   if (st & 1) {
     h->last_error = "input check: negative weight, bad vertex id or non-zero diagonal";
     return APSP_E_INVALID;
@@ -485,6 +534,298 @@ apsp_status apsp_unpack_u16(const uint16_t *src, int64_t lds, int32_t *dst, int6
   return apsp::launch_unpack(src, lds, dst, ldd, n, static_cast<cudaStream_t>(stream), nullptr) == cudaSuccess
              ? APSP_OK
              : APSP_E_CUDA;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Lays out the batched-solve workspace: plan tables, then one panel buffer
+// per graph.  Returns the total bytes; fills colT pointers relative to base.
+size_t batch_layout(const std::vector<int64_t> &n, char *base, std::vector<uint32_t *> &colT, size_t plan_bytes) {
+  size_t off = (plan_bytes + 255) / 256 * 256;
+  colT.resize(n.size());
+  for (size_t i = 0; i < n.size(); ++i) {
+    colT[i] = reinterpret_cast<uint32_t *>(base + off);
+    off += ((size_t)64 * apsp::batch_panel_ld(n[i]) * 4 + 255) / 256 * 256;
+  }
+  return off;
+}
+
+// Enqueues ingest checks and one batched launch (the handle lock is held).
+apsp_status batch_locked(apsp_handle *h, const std::vector<const int32_t *> &W, const std::vector<int64_t> &n,
+                         const std::vector<int64_t> &ld, const std::vector<int32_t *> &D, cudaStream_t s,
+                         int64_t spin_limit, const int *gate) {
+  cudaError_t e = cudaMemsetAsync(h->d_status, 0, sizeof(int), s);
+  if (e != cudaSuccess) return APSP_E_CUDA;
+  std::vector<int32_t *> Dl;
+  std::vector<int64_t> nl, ldl;
+  for (size_t i = 0; i < n.size(); ++i) {
+    if (n[i] == 0) continue;
+    int64_t l = 0;
+    e = apsp::launch_ingest(APSP_I32, W[i], D[i], n[i], ld[i], h->d_status, s, &l);
+    h->launches += l;
+    if (e != cudaSuccess) {
+      h->last_error = std::string("ingest: ") + cudaGetErrorString(e);
+      return APSP_E_CUDA;
+    }
+    Dl.push_back(D[i]);
+    nl.push_back(n[i]);
+    ldl.push_back(ld[i]);
+  }
+  if (Dl.empty()) return APSP_OK;
+  // plan sizes do not depend on the panel pointers: build once to size, once for real
+  apsp::BatchPlan plan;
+  std::vector<uint32_t *> colT(Dl.size(), nullptr);
+  plan.build(Dl, nl, ldl, colT);
+  const size_t plan_bytes = plan.workspace_bytes();
+  const size_t need = batch_layout(nl, nullptr, colT, plan_bytes);
+  e = ensure(&h->wsb, &h->wsb_bytes, need);
+  if (e != cudaSuccess) {
+    h->last_error = std::string("batch workspace: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? APSP_E_NOMEM : APSP_E_CUDA;
+  }
+  batch_layout(nl, static_cast<char *>(h->wsb), colT, plan_bytes);
+  plan.build(Dl, nl, ldl, colT);
+  int64_t l = 0;
+  e = apsp::launch_batch(plan, h->wsb, s, spin_limit, gate, h->d_status, nullptr, &l);
+  h->launches += l;
+  if (e != cudaSuccess) {
+    h->last_error = std::string("batched launch: ") + cudaGetErrorString(e);
+    return APSP_E_CUDA;
+  }
+  return APSP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+apsp_status apsp_solve_batch(apsp_handle *h, int64_t count, const int32_t *const *W, const int64_t *n,
+                             const int64_t *ld, int32_t *const *D, void *stream) {
+  if (!h) return APSP_E_INVALID;
+  if (count < 0 || (count > 0 && (!W || !n || !ld || !D))) return set_err(h, APSP_E_INVALID, "bad batch arrays");
+  for (int64_t i = 0; i < count; ++i)
+    if (n[i] < 0 || ld[i] < n[i] || n[i] > (int64_t(1) << 31) - 1 || (n[i] > 0 && (!W[i] || !D[i])))
+      return set_err(h, APSP_E_INVALID, "bad graph " + std::to_string(i) + " in batch");
+  cudaError_t e = cudaSetDevice(h->cfg.device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+  std::lock_guard<std::mutex> g(h->mu);
+  std::vector<const int32_t *> Wv(W, W + count);
+  std::vector<int64_t> nv(n, n + count), ldv(ld, ld + count);
+  std::vector<int32_t *> Dv(D, D + count);
+  return batch_locked(h, Wv, nv, ldv, Dv, static_cast<cudaStream_t>(stream), h->cfg.spin_limit, nullptr);
+}
+
+apsp_status apsp_check_bounded_wait(apsp_handle *h, int64_t spin_limit) {
+  if (!h || spin_limit <= 0) return APSP_E_INVALID;
+  cudaError_t e = cudaSetDevice(h->cfg.device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+  std::lock_guard<std::mutex> g(h->mu);
+  const int64_t n = 96;  // two rounds
+  void *buf = nullptr;
+  e = cudaMalloc(&buf, (size_t)n * n * 4 + 256);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
+  int32_t *D = static_cast<int32_t *>(buf);
+  int *gate = reinterpret_cast<int *>(static_cast<char *>(buf) + (size_t)n * n * 4);
+  cudaStream_t s = nullptr;
+  apsp_status st = APSP_OK;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) st = APSP_E_CUDA;
+  if (st == APSP_OK) {
+    // a valid graph (a path), and a gate flag that nothing ever sets
+    std::vector<int32_t> hW((size_t)n * n, APSP_INF_I32);
+    for (int64_t i = 0; i < n; ++i) {
+      hW[(size_t)i * n + i] = 0;
+      if (i + 1 < n) hW[(size_t)i * n + i + 1] = hW[(size_t)(i + 1) * n + i] = 1;
+    }
+    if (cudaMemcpy(D, hW.data(), hW.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(gate, 0, sizeof(int)) != cudaSuccess)
+      st = APSP_E_CUDA;
+  }
+  if (st == APSP_OK) {
+    std::vector<const int32_t *> Wv{D};
+    std::vector<int64_t> nv{n}, ldv{n};
+    std::vector<int32_t *> Dv{D};
+    st = batch_locked(h, Wv, nv, ldv, Dv, s, spin_limit, gate);
+  }
+  if (st == APSP_OK) {
+    e = cudaMemcpyAsync(h->h_status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_fail(nullptr, e, "sync");
+    else if (*h->h_status & 4) st = APSP_E_TIMEOUT;
+  }
+  if (s) cudaStreamDestroy(s);
+  cudaFree(buf);
+  if (st == APSP_E_TIMEOUT) h->last_error = "bounded wait gave up as expected";
+  return st;
+}
+
+}  // extern "C"
+
+namespace {
+
+struct TuneEntry {
+  std::string gpu;
+  int dtype = 0;
+  int64_t n = 0;
+  int bk = 64, tma = 1;
+  double ms = 0;
+};
+
+std::string json_str_field(const std::string &obj, const char *key) {
+  const std::string k = std::string("\"") + key + "\"";
+  size_t p = obj.find(k);
+  if (p == std::string::npos) return "";
+  p = obj.find('"', obj.find(':', p) + 1);
+  if (p == std::string::npos) return "";
+  const size_t q = obj.find('"', p + 1);
+  return q == std::string::npos ? "" : obj.substr(p + 1, q - p - 1);
+}
+
+double json_num_field(const std::string &obj, const char *key, double dflt) {
+  const std::string k = std::string("\"") + key + "\"";
+  size_t p = obj.find(k);
+  if (p == std::string::npos) return dflt;
+  p = obj.find(':', p);
+  if (p == std::string::npos) return dflt;
+  return std::strtod(obj.c_str() + p + 1, nullptr);
+}
+
+// The cache is a JSON object {"entries": [{...}, ...]}; every entry is one
+// flat object, read back field by field.
+std::vector<TuneEntry> read_cache(const char *path) {
+  std::vector<TuneEntry> out;
+  if (!path) return out;
+  std::ifstream f(path);
+  if (!f) return out;
+  std::stringstream ss;
+  ss << f.rdbuf();
+  const std::string txt = ss.str();
+  size_t p = txt.find('[');
+  while (p != std::string::npos) {
+    const size_t a = txt.find('{', p);
+    if (a == std::string::npos) break;
+    const size_t b = txt.find('}', a);
+    if (b == std::string::npos) break;
+    const std::string obj = txt.substr(a, b - a + 1);
+    TuneEntry e;
+    e.gpu = json_str_field(obj, "gpu");
+    e.dtype = (int)json_num_field(obj, "dtype", -1);
+    e.n = (int64_t)json_num_field(obj, "n", 0);
+    e.bk = (int)json_num_field(obj, "bk", 64);
+    e.tma = (int)json_num_field(obj, "tma", 1);
+    e.ms = json_num_field(obj, "ms", 0);
+    if (!e.gpu.empty() && e.dtype >= 0 && e.n > 0 && (e.bk == 32 || e.bk == 64)) out.push_back(e);
+    p = b + 1;
+  }
+  return out;
+}
+
+bool write_cache(const char *path, const std::vector<TuneEntry> &es) {
+  if (!path) return true;
+  const std::string tmp = std::string(path) + ".tmp";
+  {
+    std::ofstream f(tmp);
+    if (!f) return false;
+    f << "{\"entries\": [\n";
+    for (size_t i = 0; i < es.size(); ++i) {
+      const TuneEntry &e = es[i];
+      f << "  {\"gpu\": \"" << e.gpu << "\", \"dtype\": " << e.dtype << ", \"n\": " << e.n << ", \"bk\": " << e.bk
+        << ", \"tma\": " << e.tma << ", \"ms\": " << e.ms << "}" << (i + 1 < es.size() ? "," : "") << "\n";
+    }
+    f << "]}\n";
+  }
+  return std::rename(tmp.c_str(), path) == 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+apsp_status apsp_autotune(apsp_handle *h, int dtype, int64_t n_max, const char *cache_path) {
+  if (!h || !valid_dtype(dtype) || n_max < 1) return APSP_E_INVALID;
+  cudaError_t e = cudaSetDevice(h->cfg.device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+  cudaDeviceProp prop;
+  if ((e = cudaGetDeviceProperties(&prop, h->cfg.device)) != cudaSuccess) return cuda_fail(h, e, "properties");
+  const std::string gpu = prop.name;
+  std::vector<TuneEntry> cache = read_cache(cache_path);
+  std::lock_guard<std::mutex> g(h->mu);
+  const int64_t top = bucket_of(n_max);
+  const size_t es = dtype == APSP_U16 ? 2 : 4;
+  bool wrote = false;
+  for (int64_t b = 128; b <= top; b <<= 1) {
+    bool cached = false;
+    for (const TuneEntry &t : cache)
+      if (t.gpu == gpu && t.dtype == dtype && t.n == b) {
+        apsp::RoundConfig c;
+        c.bk = t.bk;
+        c.tma = t.tma != 0;
+        h->tuned[{dtype, b}] = c;
+        cached = true;
+      }
+    if (cached) continue;
+    void *M = nullptr;
+    if ((e = cudaMalloc(&M, (size_t)b * b * es)) != cudaSuccess) return cuda_fail(h, e, "autotune matrix");
+    const int64_t ldT = panel_ld(b);
+    if ((e = ensure(&h->colT, &h->colT_bytes, (size_t)apsp::kMaxRoundWidth * ldT * 4)) != cudaSuccess) {
+      cudaFree(M);
+      return cuda_fail(h, e, "autotune panel");
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 1e30;
+    apsp::RoundConfig best_c;
+    for (int bk : {32, 64})
+      for (int tma : {1, 0}) {
+        apsp::RoundConfig c;
+        c.bk = bk;
+        c.tma = tma != 0;
+        double t_min = 1e30;
+        for (int rep = 0; rep < 4; ++rep) {
+          apsp::launch_synth(dtype, M, b, b, nullptr);
+          cudaEventRecord(e0, nullptr);
+          int64_t l = 0;
+          e = apsp::launch_rounds(dtype, M, b, b, h->colT, ldT, nullptr, &l, nullptr, c);
+          cudaEventRecord(e1, nullptr);
+          if (e != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (rep > 0) t_min = std::min(t_min, (double)ms);  // first run warms up
+        }
+        if (e != cudaSuccess) break;
+        if (t_min < best) {
+          best = t_min;
+          best_c = c;
+        }
+      }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(M);
+    if (e != cudaSuccess) return cuda_fail(h, e, "autotune run");
+    h->tuned[{dtype, b}] = best_c;
+    TuneEntry t;
+    t.gpu = gpu;
+    t.dtype = dtype;
+    t.n = b;
+    t.bk = best_c.bk;
+    t.tma = best_c.tma ? 1 : 0;
+    t.ms = best;
+    cache.push_back(t);
+    wrote = true;
+  }
+  if (wrote && !write_cache(cache_path, cache)) return set_err(nullptr, APSP_E_INVALID, "cannot write cache");
+  return APSP_OK;
+}
+
+apsp_status apsp_tuned_config(apsp_handle *h, int dtype, int64_t n, int *block_k, int *tma) {
+  if (!h || !block_k || !tma || !valid_dtype(dtype) || n < 0) return APSP_E_INVALID;
+  std::lock_guard<std::mutex> g(h->mu);
+  const apsp::RoundConfig c = config_for(h, dtype, n);
+  *block_k = c.bk;
+  *tma = c.tma ? 1 : 0;
+  return APSP_OK;
 }
 
 const char *apsp_strerror(apsp_status s) {
@@ -544,49 +885,119 @@ apsp_status apsp_profile_read(apsp_handle *h, int64_t launches[3], double ms[3],
 }  // extern "C"
 
 // ============================================================== request loop
-// Continuous batching over streams: the worker admits queued requests in
-// arrival order while their footprint (n^2 * 4 bytes of D plus the panel
-// buffer) fits the memory budget and fewer than max_batch are in flight; each
-// admitted request gets its own stream, so rounds of co-arriving graphs
-// overlap on the device; completions free memory and slots for the next ones.
+// Continuous batching: the worker admits queued requests in arrival order
+// while their footprint (n^2 * 4 bytes of D plus the panel buffer) fits the
+// memory budget; requests admitted in one pass form a group that is solved by
+// ONE batched persistent launch on its own stream, so the rounds of its
+// graphs interleave on the device, and groups admitted later run concurrently
+// with the earlier ones.  A group's completion returns its panel memory; a
+// request's matrix is returned by apsp_release.
 namespace {
 
-int64_t request_bytes(int64_t n) {
-  return n * n * 4 + (int64_t)apsp::round_width(APSP_I32) * panel_ld(n) * 4 + 256;
+constexpr int kMaxGroupsInFlight = 16;
+
+int64_t panel_bytes(int64_t n) { return 64 * apsp::batch_panel_ld(n) * 4 + 256; }
+
+// Marks a finished group's requests DONE or ERROR and frees its transient
+// memory (called with smu held, after done_ev completed).
+void finish_group(apsp_handle *h, const std::shared_ptr<Group> &g) {
+  if (g->finished) return;
+  g->finished = true;
+  const size_t cnt = g->tickets.size();
+  std::vector<int> st(cnt + 1, 0);
+  cudaMemcpy(st.data(), g->status, (cnt + 1) * sizeof(int), cudaMemcpyDeviceToHost);
+  std::vector<apsp::BatchGraph> G(g->tickets.size());
+  if (g->graphs_dev && !G.empty())
+    cudaMemcpy(G.data(), g->graphs_dev, G.size() * sizeof(apsp::BatchGraph), cudaMemcpyDeviceToHost);
+  for (size_t i = 0; i < g->tickets.size(); ++i) {
+    auto it = h->reqs.find(g->tickets[i]);
+    if (it == h->reqs.end()) continue;
+    Request *r = it->second.get();
+    r->finished = true;
+    if (st[i] & 1) r->err = APSP_E_INVALID;
+    else if (st[i] & 2) r->err = APSP_E_RANGE;
+    else if (g->graphs_dev ? (G[i].status & 4) != 0 : (st[cnt] & 4) != 0) r->err = APSP_E_TIMEOUT;
+    h->used -= r->transient;
+    r->transient = 0;
+  }
+  cudaFreeAsync(g->ws, g->stream);
+  cudaFreeAsync(g->status, g->stream);
+  g->ws = nullptr;
+  g->status = nullptr;
+  h->free_streams.push_back(g->stream);
+  h->groups.erase(std::remove(h->groups.begin(), h->groups.end(), g), h->groups.end());
+  h->scv.notify_all();
 }
 
-// Admits one request (called by the worker with smu held).
-apsp_status admit(apsp_handle *h, Request *r) {
-  const int64_t n = r->req.n;
-  cudaStream_t s;
+void poll_groups(apsp_handle *h) {
+  std::vector<std::shared_ptr<Group>> done;
+  for (auto &g : h->groups)
+    if (cudaEventQuery(g->done_ev) == cudaSuccess) done.push_back(g);
+  for (auto &g : done) finish_group(h, g);
+}
+
+// Admits `rs` as one group: matrices, input copies, checks, one batched launch.
+apsp_status admit_group(apsp_handle *h, const std::vector<Request *> &rs) {
+  auto g = std::make_shared<Group>();
   if (!h->free_streams.empty()) {
-    s = h->free_streams.back();
+    g->stream = h->free_streams.back();
     h->free_streams.pop_back();
-  } else if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+  } else if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess) {
     return APSP_E_CUDA;
   }
-  r->stream = s;
-  const int64_t ldT = panel_ld(n);
-  if (cudaMallocAsync(&r->D, (size_t)std::max<int64_t>(1, n * n) * 4, s) != cudaSuccess ||
-      cudaMallocAsync(&r->colT, (size_t)apsp::round_width(APSP_I32) * ldT * 4, s) != cudaSuccess ||
-      cudaMallocAsync((void **)&r->status, 64, s) != cudaSuccess ||
-      cudaEventCreateWithFlags(&r->copy_ev, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming) != cudaSuccess)
+  cudaStream_t s = g->stream;
+  std::vector<int32_t *> D;
+  std::vector<int64_t> n, ld;
+  for (Request *r : rs) {
+    const int64_t rn = r->req.n;
+    if (cudaMallocAsync(&r->D, (size_t)std::max<int64_t>(1, rn * rn) * 4, s) != cudaSuccess) return APSP_E_CUDA;
+    if (rn > 0 && cudaMemcpy2DAsync(r->D, (size_t)rn * 4, r->req.W, (size_t)r->req.ld * 4, (size_t)rn * 4,
+                                    (size_t)rn, r->req.is_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                    s) != cudaSuccess)
+      return APSP_E_CUDA;
+    r->group = g;
+    r->gidx = (int)g->tickets.size();
+    g->tickets.push_back(r->ticket);
+    g->transient += r->transient;
+    if (rn > 0) {
+      D.push_back(static_cast<int32_t *>(r->D));
+      n.push_back(rn);
+      ld.push_back(rn);
+    }
+  }
+  if (cudaEventCreateWithFlags(&g->copy_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->done_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventRecord(g->copy_ev, s) != cudaSuccess)
     return APSP_E_CUDA;
-  if (n > 0) {
-    if (cudaMemcpy2DAsync(r->D, (size_t)n * 4, r->req.W, (size_t)r->req.ld * 4, (size_t)n * 4, (size_t)n,
-                          r->req.is_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+  const size_t sbytes = (rs.size() + 1) * sizeof(int);
+  if (cudaMallocAsync((void **)&g->status, sbytes, s) != cudaSuccess ||
+      cudaMemsetAsync(g->status, 0, sbytes, s) != cudaSuccess)
+    return APSP_E_CUDA;
+  int64_t l = 0;
+  for (size_t i = 0; i < rs.size(); ++i) {
+    const int64_t rn = rs[i]->req.n;
+    if (rn > 0 && apsp::launch_ingest(APSP_I32, rs[i]->D, rs[i]->D, rn, rn, g->status + i, s, &l) != cudaSuccess)
       return APSP_E_CUDA;
   }
-  cudaEventRecord(r->copy_ev, s);
-  cudaMemsetAsync(r->status, 0, sizeof(int), s);
-  int64_t l = 0;
-  cudaError_t e = apsp::launch_ingest(APSP_I32, r->D, r->D, n, n, r->status, s, &l);
-  if (e == cudaSuccess) e = apsp::launch_rounds(APSP_I32, r->D, n, n, r->colT, ldT, s, &l);
+  // only graphs with n > 0 take part; group indices follow the tickets
+  apsp::BatchPlan plan;
+  std::vector<uint32_t *> colT(D.size(), nullptr);
+  plan.build(D, n, ld, colT);
+  const size_t plan_bytes = plan.workspace_bytes();
+  const size_t need = batch_layout(n, nullptr, colT, plan_bytes);
+  if (cudaMallocAsync(&g->ws, need, s) != cudaSuccess) return APSP_E_CUDA;
+  batch_layout(n, static_cast<char *>(g->ws), colT, plan_bytes);
+  plan.build(D, n, ld, colT);
+  if (!D.empty() &&
+      apsp::launch_batch(plan, g->ws, s, h->cfg.spin_limit, nullptr, g->status + rs.size(), &g->graphs_dev, &l) !=
+          cudaSuccess)
+    return APSP_E_CUDA;
   h->launches += l;
-  if (e != cudaSuccess) return APSP_E_CUDA;
-  cudaEventRecord(r->done_ev, s);
-  r->admitted = true;
+  if (cudaEventRecord(g->done_ev, s) != cudaSuccess) return APSP_E_CUDA;
+  // graphs_dev indexes only n > 0 graphs; map statuses back by skipping n == 0
+  if (D.size() != rs.size()) g->graphs_dev = nullptr;
+  for (Request *r : rs) r->admitted = true;
+  h->groups.push_back(g);
   return APSP_OK;
 }
 
@@ -594,42 +1005,33 @@ void worker_loop(apsp_handle *h) {
   cudaSetDevice(h->cfg.device);
   std::unique_lock<std::mutex> g(h->smu);
   while (!h->stopping) {
-    // completions
-    for (auto &kv : h->reqs) {
-      Request *r = kv.second.get();
-      if (r->admitted && !r->finished && cudaEventQuery(r->done_ev) == cudaSuccess) {
-        r->finished = true;
-        int st = 0;
-        cudaMemcpy(&st, r->status, sizeof(int), cudaMemcpyDeviceToHost);
-        if (st & 1) r->err = APSP_E_INVALID;
-        else if (st & 2) r->err = APSP_E_RANGE;
-        cudaFreeAsync(r->colT, r->stream);
-        cudaFreeAsync(r->status, r->stream);
-        r->colT = nullptr;
-        r->status = nullptr;
-        h->used -= (int64_t)apsp::round_width(APSP_I32) * panel_ld(r->req.n) * 4 + 256;
-        h->free_streams.push_back(r->stream);
-        --h->running;
-        h->scv.notify_all();
+    poll_groups(h);
+    // one group per pass from the front of the queue, in arrival order
+    if (!h->queue.empty() && (int)h->groups.size() < kMaxGroupsInFlight) {
+      std::vector<Request *> rs;
+      int64_t add = 0;
+      while (!h->queue.empty() && (int)rs.size() < h->cfg.max_batch) {
+        Request *r = h->reqs[h->queue.front()].get();
+        const int64_t b = r->bytes + panel_bytes(r->req.n);
+        if (h->used + add + b > h->budget) break;  // wait for memory to free up
+        h->queue.pop_front();
+        r->transient = panel_bytes(r->req.n);
+        add += b;
+        rs.push_back(r);
+      }
+      if (!rs.empty()) {
+        h->used += add;
+        apsp_status st = admit_group(h, rs);
+        if (st != APSP_OK) {
+          for (Request *r : rs) {
+            r->err = st;
+            r->admitted = r->finished = true;
+          }
+        }
+        continue;  // look for more work right away
       }
     }
-    // admissions, in arrival order
-    while (!h->queue.empty() && h->running < h->cfg.max_batch) {
-      Request *r = h->reqs[h->queue.front()].get();
-      if (h->used + r->bytes > h->budget && h->running > 0) break;  // wait for memory to free up
-      h->queue.pop_front();
-      apsp_status st = admit(h, r);
-      h->used += r->bytes;
-      if (st != APSP_OK) {
-        r->err = st;
-        r->finished = true;
-        r->admitted = true;
-        h->used -= r->bytes;
-        continue;
-      }
-      ++h->running;
-    }
-    h->scv.wait_for(g, std::chrono::microseconds(h->running > 0 ? 50 : 2000));
+    h->scv.wait_for(g, std::chrono::microseconds(h->groups.empty() ? 2000 : 20));
   }
 }
 
@@ -657,8 +1059,8 @@ apsp_status apsp_submit(apsp_handle *h, const apsp_request *r, uint64_t *ticket)
   cudaSetDevice(h->cfg.device);
   std::unique_lock<std::mutex> g(h->smu);
   start_worker(h);
-  const int64_t bytes = request_bytes(r->n);
-  if (bytes > h->budget) return APSP_E_NOMEM;
+  const int64_t bytes = r->n * r->n * 4;
+  if (bytes + panel_bytes(r->n) > h->budget) return APSP_E_NOMEM;
   if ((int64_t)h->queue.size() >= h->cfg.queue_depth) return APSP_E_BUSY;
   std::unique_ptr<Request> q(new Request());
   q->ticket = h->next_ticket++;
@@ -678,6 +1080,8 @@ apsp_status apsp_poll(apsp_handle *h, uint64_t ticket, apsp_state *st, const voi
   auto it = h->reqs.find(ticket);
   if (it == h->reqs.end()) return APSP_E_NOTFOUND;
   Request *r = it->second.get();
+  if (r->admitted && !r->finished && r->group && cudaEventQuery(r->group->done_ev) == cudaSuccess)
+    finish_group(h, r->group);
   if (r->err != APSP_OK) {
     *st = APSP_ERROR;
     return r->err;
@@ -686,12 +1090,12 @@ apsp_status apsp_poll(apsp_handle *h, uint64_t ticket, apsp_state *st, const voi
     *st = APSP_QUEUED;
     return APSP_OK;
   }
-  if (r->finished || cudaEventQuery(r->done_ev) == cudaSuccess) {
+  if (r->finished) {
     *st = APSP_DONE;
     if (D_dev) *D_dev = r->D;
     return APSP_OK;
   }
-  *st = cudaEventQuery(r->copy_ev) == cudaSuccess ? APSP_RUNNING : APSP_QUEUED;
+  *st = (r->group && cudaEventQuery(r->group->copy_ev) == cudaSuccess) ? APSP_RUNNING : APSP_QUEUED;
   return APSP_OK;
 }
 
@@ -702,16 +1106,10 @@ apsp_status apsp_wait(apsp_handle *h, uint64_t ticket, int64_t timeout_ms) {
     apsp_state st;
     apsp_status s = apsp_poll(h, ticket, &st, nullptr);
     if (s != APSP_OK) return s;
-    if (st == APSP_DONE) {
-      // make the result visible to the caller's streams
-      std::unique_lock<std::mutex> g(h->smu);
-      Request *r = h->reqs[ticket].get();
-      if (r->done_ev) cudaEventSynchronize(r->done_ev);
-      return APSP_OK;
-    }
+    if (st == APSP_DONE) return APSP_OK;
     if (timeout_ms >= 0 && std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(timeout_ms))
       return APSP_E_NOTREADY;
-    std::this_thread::sleep_for(std::chrono::microseconds(50));
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
 }
 
@@ -722,12 +1120,12 @@ apsp_status apsp_fetch(apsp_handle *h, uint64_t ticket, void *dst, int64_t ldd, 
   if (it == h->reqs.end()) return APSP_E_NOTFOUND;
   Request *r = it->second.get();
   if (r->err != APSP_OK) return r->err;
-  if (!r->admitted) return APSP_E_NOTREADY;
+  if (!r->admitted || !r->group) return APSP_E_NOTREADY;
   const int64_t n = r->req.n;
   if (ldd < n) return APSP_E_INVALID;
   if (n == 0) return APSP_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cudaStreamWaitEvent(s, r->done_ev, 0) != cudaSuccess) return APSP_E_CUDA;
+  if (cudaStreamWaitEvent(s, r->group->done_ev, 0) != cudaSuccess) return APSP_E_CUDA;
   if (cudaMemcpy2DAsync(dst, (size_t)ldd * 4, r->D, (size_t)n * 4, (size_t)n * 4, (size_t)n, cudaMemcpyDefault, s) !=
       cudaSuccess)
     return APSP_E_CUDA;
@@ -740,21 +1138,17 @@ apsp_status apsp_release(apsp_handle *h, uint64_t ticket) {
   auto it = h->reqs.find(ticket);
   if (it == h->reqs.end()) return APSP_E_NOTFOUND;
   Request *r = it->second.get();
-  if (r->admitted && !r->finished && r->err == APSP_OK) {
-    // still running: wait for it, then free
-    cudaEventSynchronize(r->done_ev);
-    return APSP_E_NOTREADY;
+  if (r->admitted && !r->finished && r->group) {
+    if (cudaEventQuery(r->group->done_ev) != cudaSuccess) return APSP_E_NOTREADY;  // still running
+    finish_group(h, r->group);
   }
   if (!r->admitted) {
     h->queue.erase(std::remove(h->queue.begin(), h->queue.end(), ticket), h->queue.end());
   } else if (r->D) {
-    cudaFreeAsync(r->D, r->stream);
+    cudaFreeAsync(r->D, r->group ? r->group->stream : nullptr);
     r->D = nullptr;
-    h->used -= r->req.n * r->req.n * 4;
+    h->used -= r->bytes;
   }
-  if (r->copy_ev) cudaEventDestroy(r->copy_ev);
-  if (r->done_ev) cudaEventDestroy(r->done_ev);
-  r->copy_ev = r->done_ev = nullptr;
   h->reqs.erase(it);
   h->scv.notify_all();
   return APSP_OK;

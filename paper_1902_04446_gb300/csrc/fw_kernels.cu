@@ -33,6 +33,7 @@
 
 #include "fw_device.cuh"
 #include "fw_launch.h"
+#include "fw_tasks.cuh"
 #include "tma.cuh"
 
 namespace apsp {
@@ -43,55 +44,10 @@ constexpr int P1_THREADS = 256;
 template <class Op, int BK>
 __global__ void __launch_bounds__(P1_THREADS) fw_phase1(typename Op::elem *__restrict__ D, int64_t ld, int64_t n,
                                                         int64_t p0, uint32_t *__restrict__ colT, int64_t ldT) {
-  using S = typename Op::scalar;
-  constexpr int G = 16;        // 16 x 16 thread grid
-  constexpr int PT = BK / G;   // each thread owns PT x PT entries
-  static_assert(BK % G == 0, "BK must be a multiple of 16");
-  __shared__ S s[BK][BK + 1];
-  const int tid = threadIdx.x;
-  const int by = tid / G, bx = tid % G;
-  const S INF = Op::to_s(Op::inf_elem());
-  for (int idx = tid; idx < BK * BK; idx += P1_THREADS) {
-    const int i = idx / BK, j = idx % BK;
-    const int64_t r = p0 + i, c = p0 + j;
-    s[i][j] = (r < n && c < n) ? Op::to_s(D[r * ld + c]) : INF;
-  }
-  __syncthreads();
-  S v[PT][PT];
-#pragma unroll
-  for (int r = 0; r < PT; ++r)
-#pragma unroll
-    for (int c = 0; c < PT; ++c) v[r][c] = s[by + G * r][bx + G * c];
-  // Step t relaxes every entry through vertex p0 + t.  Row t and column t do
-  // not change in step t (D_tt = 0, and INF + x >= x on padded vertices), so
-  // one barrier per step orders the steps.
-  for (int t = 0; t < BK; ++t) {
-    S a[PT], b[PT];
-#pragma unroll
-    for (int r = 0; r < PT; ++r) a[r] = s[by + G * r][t];
-#pragma unroll
-    for (int c = 0; c < PT; ++c) b[c] = s[t][bx + G * c];
-#pragma unroll
-    for (int r = 0; r < PT; ++r)
-#pragma unroll
-      for (int c = 0; c < PT; ++c) {
-        v[r][c] = Op::s_addmin(a[r], b[c], v[r][c]);
-        s[by + G * r][bx + G * c] = v[r][c];
-      }
-    __syncthreads();
-  }
-  for (int idx = tid; idx < BK * BK; idx += P1_THREADS) {
-    const int i = idx / BK, j = idx % BK;
-    const int64_t r = p0 + i, c = p0 + j;
-    if (r < n && c < n) D[r * ld + c] = Op::from_s(s[i][j]);
-  }
-  for (int idx = tid; idx < BK * BK; idx += P1_THREADS) {
-    const int t = idx / BK, i = idx % BK;
-    colT[t * ldT + p0 + i] = Op::dup(Op::from_s(s[i][t]));
-  }
+  __shared__ typename Op::scalar s[BK][BK + 1];
+  phase1_body<Op, BK, P1_THREADS, false>(D, ld, n, p0, colT, ldT, s, threadIdx.x);
 }
 
-// ---------------------------------------------------------------- smem loaders
 // shared-memory loaders: load_As_colT, load_Bs_rows, load_As_transposed (fw_device.cuh)
 
 // ---------------------------------------------------------------- Phase 2
@@ -101,7 +57,7 @@ template <class Op, int BK>
 struct P2Cfg {
   static constexpr int ROW_BM = BK, ROW_BNW = 128;
   static constexpr int COL_BM = 128 * Op::EPW, COL_BNW = BK / Op::EPW;
-  static constexpr int THREADS = 128;
+  static constexpr int THREADS = (BK / 8) * 16;
   static_assert(TileMap<ROW_BM, ROW_BNW>::THREADS == THREADS, "row tile");
   static_assert(TileMap<COL_BM, COL_BNW>::THREADS == THREADS, "col tile");
   static constexpr int ROW_SMEM = (BK * ROW_BM + BK * ROW_BNW) * 4;
@@ -110,72 +66,19 @@ struct P2Cfg {
 };
 
 template <class Op, int BK>
-__global__ void __launch_bounds__(128) fw_phase2(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
+__global__ void __launch_bounds__(P2Cfg<Op, BK>::THREADS) fw_phase2(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
                                                  int64_t p1, uint32_t *__restrict__ colT, int64_t ldT, int nrow_ctas,
                                                  int vec) {
   using C = P2Cfg<Op, BK>;
   extern __shared__ __align__(16) uint32_t smem[];
-  const int tid = threadIdx.x;
-  uint32_t acc[8][8];
-  if ((int)blockIdx.x < nrow_ctas) {
-    // row panel: D_kJ = min(D_kJ, D_kk (x) D_kJ); A = D_kk (from colT), B = C = D_kJ
-    using Map = TileMap<C::ROW_BM, C::ROW_BNW>;
-    uint32_t *As = smem;
-    uint32_t *Bs = smem + BK * C::ROW_BM;
-    const int tx = tid % Map::TX, ty = tid / Map::TX;
-    const int64_t col0 = (int64_t)blockIdx.x * C::ROW_BNW * Op::EPW;
-    load_As_colT<C::ROW_BM, BK, C::THREADS>(As, colT, ldT, p0, tid);
-    load_Bs_rows<Op, C::ROW_BNW, BK, C::THREADS>(Bs, D, ld, n, n, p0, col0, vec, tid);
-    load_acc<Op, C::ROW_BM, C::ROW_BNW>(D, ld, n, n, p0, col0, vec, acc, ty, tx);
-    __syncthreads();
-    tile_minplus<Op, C::ROW_BM, C::ROW_BNW, BK>(As, Bs, acc, ty, tx);
-    store_acc<Op, C::ROW_BM, C::ROW_BNW>(D, ld, n, n, p0, col0, 0, 0, p0, p1, vec, acc, ty, tx);
-  } else {
-    // column panel: D_Ik = min(D_Ik, D_Ik (x) D_kk); A = C = D_Ik, B = D_kk
-    using Map = TileMap<C::COL_BM, C::COL_BNW>;
-    uint32_t *As = smem;
-    uint32_t *Bs = smem + BK * C::COL_BM;
-    const int tx = tid % Map::TX, ty = tid / Map::TX;
-    const int64_t row0 = (int64_t)(blockIdx.x - nrow_ctas) * C::COL_BM;
-    load_As_transposed<Op, C::COL_BM, BK, C::THREADS>(As, D, ld, n, n, row0, p0, vec, tid);
-    load_Bs_rows<Op, C::COL_BNW, BK, C::THREADS>(Bs, D, ld, n, n, p0, p0, vec, tid);
-    load_acc<Op, C::COL_BM, C::COL_BNW>(D, ld, n, n, row0, p0, vec, acc, ty, tx);
-    __syncthreads();
-    tile_minplus<Op, C::COL_BM, C::COL_BNW, BK>(As, Bs, acc, ty, tx);
-    store_acc<Op, C::COL_BM, C::COL_BNW>(D, ld, n, n, row0, p0, p0, p1, 0, 0, vec, acc, ty, tx);
-    // transposed copy: colT[t][row0 + i] = word(D_Ik[i][t]) for rows outside [p0, p1)
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-#pragma unroll
-      for (int g = 0; g < 2; ++g) {
-        const int ib = Map::row(ty, 4 * g);   // 4 consecutive rows ib .. ib+3
-        const int64_t rb = row0 + ib;
-        const bool all_out = (rb + 3 < p0) || (rb >= p1);
-#pragma unroll
-        for (int cw = 0; cw < 4; ++cw) {
-          const int w = Map::wcol(tx, h) + cw;
-#pragma unroll
-          for (int lane = 0; lane < Op::EPW; ++lane) {
-            const int t = w * Op::EPW + lane;
-            uint32_t q4[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const uint32_t word = acc[4 * g + q][4 * h + cw];
-              q4[q] = (Op::EPW == 2) ? Op::dup(bits_elem<Op>(lane ? (word >> 16) : (word & 0xFFFFu))) : word;
-            }
-            uint32_t *dst = colT + (int64_t)t * ldT + rb;
-            if (all_out) {
-              *reinterpret_cast<uint4 *>(dst) = make_uint4(q4[0], q4[1], q4[2], q4[3]);
-            } else {
-#pragma unroll
-              for (int q = 0; q < 4; ++q)
-                if (rb + q < p0 || rb + q >= p1) dst[q] = q4[q];
-            }
-          }
-        }
-      }
-    }
-  }
+  if ((int)blockIdx.x < nrow_ctas)
+    p2_row_task<Op, BK, C::ROW_BNW, C::THREADS, false>(D, ld, n, p0, p1, colT, ldT,
+                                                       (int64_t)blockIdx.x * C::ROW_BNW * Op::EPW, vec, smem,
+                                                       threadIdx.x);
+  else
+    p2_col_task<Op, BK, C::COL_BM, C::THREADS, false>(D, ld, n, p0, p1, colT, ldT,
+                                                      (int64_t)(blockIdx.x - nrow_ctas) * C::COL_BM, vec, smem,
+                                                      threadIdx.x);
 }
 
 // ---------------------------------------------------------------- Phase 3
@@ -189,22 +92,9 @@ template <class Op, int BK>
 __global__ void __launch_bounds__(256, 2) fw_phase3(typename Op::elem *__restrict__ D, int64_t ld, int64_t n,
                                                     int64_t p0, int64_t p1, const uint32_t *__restrict__ colT,
                                                     int64_t ldT, int vec) {
-  using Cfg = P3Cfg<Op>;
-  using Map = TileMap<Cfg::BM, Cfg::BNW>;
   extern __shared__ __align__(16) uint32_t smem[];
-  uint32_t *As = smem;
-  uint32_t *Bs = smem + BK * Cfg::BM;
-  const int tid = threadIdx.x;
-  const int tx = tid % Map::TX, ty = tid / Map::TX;
-  const int64_t row0 = (int64_t)blockIdx.y * Cfg::BM;
-  const int64_t col0 = (int64_t)blockIdx.x * Cfg::BNW * Op::EPW;
-  uint32_t acc[8][8];
-  load_As_colT<Cfg::BM, BK, Cfg::THREADS>(As, colT, ldT, row0, tid);
-  load_Bs_rows<Op, Cfg::BNW, BK, Cfg::THREADS>(Bs, D, ld, n, n, p0, col0, vec, tid);
-  load_acc<Op, Cfg::BM, Cfg::BNW>(D, ld, n, n, row0, col0, vec, acc, ty, tx);
-  __syncthreads();
-  tile_minplus<Op, Cfg::BM, Cfg::BNW, BK>(As, Bs, acc, ty, tx);
-  store_acc<Op, Cfg::BM, Cfg::BNW>(D, ld, n, n, row0, col0, p0, p1, p0, p1, vec, acc, ty, tx);
+  p3_task<Op, BK, false>(D, ld, n, p0, p1, colT, ldT, (int64_t)blockIdx.y * P3Cfg<Op>::BM,
+                         (int64_t)blockIdx.x * P3Cfg<Op>::BNW * Op::EPW, vec, smem, threadIdx.x);
 }
 
 // ---------------------------------------------------------------- Phase 3, persistent + TMA
@@ -222,17 +112,21 @@ __global__ void __launch_bounds__(256, 2) fw_phase3(typename Op::elem *__restric
 // meet A words colT[t][.] that Phases 1 and 2 set to INF for those t, so the
 // sum is INF and never wins.
 constexpr int P3T_THREADS = 256;
-constexpr int P3T_STAGE_BYTES = 2 * 64 * 128 * 4;  // A + B, BK = 64
 constexpr int P3T_C_BYTES = 128 * 128 * 4;
-constexpr int P3T_SMEM = 2 * P3T_STAGE_BYTES + P3T_C_BYTES + 1024;
 constexpr uint32_t P3T_WAIT_LIMIT = 1u << 26;
+template <int BK>
+struct P3T {
+  static constexpr int STAGE_BYTES = 2 * BK * 128 * 4;  // A + B tiles
+  static constexpr int SMEM = 2 * STAGE_BYTES + P3T_C_BYTES + 1024;
+};
 
-template <class Op>
+template <class Op, int BK>
 __global__ void __launch_bounds__(P3T_THREADS, 1)
     fw_phase3_tma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                   const __grid_constant__ CUtensorMap mapC, typename Op::elem *__restrict__ D, int64_t ld, int64_t n,
                   int64_t p0, int64_t p1, int tiles_x, int tiles_total, int *err) {
-  constexpr int BM = 128, BNW = 128, BK = 64;
+  constexpr int BM = 128, BNW = 128;
+  constexpr int P3T_STAGE_BYTES = P3T<BK>::STAGE_BYTES;
   using Map = TileMap<BM, BNW>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t bar_ab[2];
@@ -452,6 +346,31 @@ __global__ void scatter_edges_kernel(const int32_t *__restrict__ src, const int3
   if (bad) atomicOr(status, bad);
 }
 
+// Synthetic symmetric graph for the autotuner: edge (i, j) with probability
+// about 8/n, weight 1..1000, from an integer hash of (min(i,j), max(i,j)).
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352dU;
+  x ^= x >> 15;
+  x *= 0x846ca68bU;
+  x ^= x >> 16;
+  return x;
+}
+
+template <class Op>
+__global__ void synth_kernel(typename Op::elem *__restrict__ D, int64_t n, int64_t ld) {
+  const uint32_t thresh = (uint32_t)(4294967295.0 * (8.0 / (double)(n > 8 ? n : 8)));
+  for (int64_t i = blockIdx.y; i < n; i += gridDim.y)
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+      const uint32_t a = (uint32_t)(i < j ? i : j), b = (uint32_t)(i < j ? j : i);
+      const uint32_t h = mix32(a * 0x9E3779B9U ^ mix32(b));
+      typename Op::elem v = Op::inf_elem();
+      if (i == j) v = (typename Op::elem)0;
+      else if (h < thresh) v = (typename Op::elem)(1 + mix32(h) % (Op::DTYPE == 1 ? 16u : 1000u));
+      D[i * ld + j] = v;
+    }
+}
+
 // ---------------------------------------------------------------- host launchers
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -510,8 +429,8 @@ static inline unsigned grid_cols(int64_t n, int threads) {
 }
 
 template <class Op, int BK>
-static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int64_t ldT, bool vec, cudaStream_t s,
-                               int64_t *launches, PhaseTimer *tm) {
+static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int64_t ldT, bool vec, bool use_tma,
+                               cudaStream_t s, int64_t *launches, PhaseTimer *tm) {
   using E = typename Op::elem;
   E *D = static_cast<E *>(Dv);
   uint32_t *colT = static_cast<uint32_t *>(colTv);
@@ -526,20 +445,20 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
   // persistent TMA Phase 3 when D is 16-byte addressable (otherwise the
   // per-tile kernel with scalar edge handling)
   CUtensorMap mA, mB, mC;
-  bool tma = vec && BK == 64;
+  bool tma = vec && use_tma;
   int *err = nullptr;
   if (tma) {
     constexpr CUtensorMapDataType dt = Op::DTYPE == 1   ? CU_TENSOR_MAP_DATA_TYPE_UINT16
                                        : Op::DTYPE == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                                         : CU_TENSOR_MAP_DATA_TYPE_INT32;
     tma = make_map(&mA, CU_TENSOR_MAP_DATA_TYPE_UINT32, colT, (uint64_t)ldT, (uint64_t)BK, (uint64_t)ldT * 4, 128,
-                   64) &&
-          make_map(&mB, dt, D, (uint64_t)n, (uint64_t)n, (uint64_t)ld * sizeof(E), 128 * Op::EPW, 64) &&
+                   BK) &&
+          make_map(&mB, dt, D, (uint64_t)n, (uint64_t)n, (uint64_t)ld * sizeof(E), 128 * Op::EPW, BK) &&
           make_map(&mC, dt, D, (uint64_t)n, (uint64_t)n, (uint64_t)ld * sizeof(E), 128 * Op::EPW, 128);
     err = tma ? error_word() : nullptr;
     tma = tma && err != nullptr;
     if (tma) {
-      e = cudaFuncSetAttribute(fw_phase3_tma<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, P3T_SMEM);
+      e = cudaFuncSetAttribute(fw_phase3_tma<Op, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, P3T<BK>::SMEM);
       if (e != cudaSuccess) return e;
     }
   }
@@ -563,8 +482,8 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
       if (tm) tm->after(1, s, 2.0 * rest * w * w);
       if (tm) tm->before(2, s);
       if (tma)
-        fw_phase3_tma<Op><<<grid_tma, P3T_THREADS, P3T_SMEM, s>>>(mA, mB, mC, D, ld, n, p0, p1, tiles_x, tiles_total,
-                                                                  err);
+        fw_phase3_tma<Op, BK><<<grid_tma, P3T_THREADS, P3T<BK>::SMEM, s>>>(mA, mB, mC, D, ld, n, p0, p1, tiles_x,
+                                                                           tiles_total, err);
       else
         fw_phase3<Op, BK><<<g3, C3::THREADS, SMEM3, s>>>(D, ld, n, p0, p1, colT, ldT, vec ? 1 : 0);
       if (tm) tm->after(2, s, rest * rest * w);
@@ -578,20 +497,24 @@ static bool aligned16(const void *p, int64_t ld, size_t esz) {
   return (reinterpret_cast<uintptr_t>(p) % 16 == 0) && ((ld * (int64_t)esz) % 16 == 0);
 }
 
-cudaError_t launch_rounds(int dtype, void *D, int64_t ld, int64_t n, void *colT, int64_t ldT, cudaStream_t s,
-                          int64_t *launches, PhaseTimer *tm) {
-  if (n <= 0) return cudaSuccess;
-  switch (dtype) {
-    case 0: return rounds_impl<OpI32, 64>(D, ld, n, colT, ldT, aligned16(D, ld, 4), s, launches, tm);
-    case 1: return rounds_impl<OpU16, 64>(D, ld, n, colT, ldT, aligned16(D, ld, 2), s, launches, tm);
-    case 2: return rounds_impl<OpF32, 64>(D, ld, n, colT, ldT, aligned16(D, ld, 4), s, launches, tm);
-    default: return cudaErrorInvalidValue;
-  }
+template <class Op>
+static cudaError_t rounds_bk(const RoundConfig &cfg, void *D, int64_t ld, int64_t n, void *colT, int64_t ldT,
+                             cudaStream_t s, int64_t *launches, PhaseTimer *tm) {
+  const bool vec = aligned16(D, ld, sizeof(typename Op::elem));
+  if (cfg.bk == 32) return rounds_impl<Op, 32>(D, ld, n, colT, ldT, vec, cfg.tma, s, launches, tm);
+  if (cfg.bk == 64) return rounds_impl<Op, 64>(D, ld, n, colT, ldT, vec, cfg.tma, s, launches, tm);
+  return cudaErrorInvalidValue;
 }
 
-int64_t round_width(int dtype) {
-  (void)dtype;
-  return 64;
+cudaError_t launch_rounds(int dtype, void *D, int64_t ld, int64_t n, void *colT, int64_t ldT, cudaStream_t s,
+                          int64_t *launches, PhaseTimer *tm, const RoundConfig &cfg) {
+  if (n <= 0) return cudaSuccess;
+  switch (dtype) {
+    case 0: return rounds_bk<OpI32>(cfg, D, ld, n, colT, ldT, s, launches, tm);
+    case 1: return rounds_bk<OpU16>(cfg, D, ld, n, colT, ldT, s, launches, tm);
+    case 2: return rounds_bk<OpF32>(cfg, D, ld, n, colT, ldT, s, launches, tm);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <class Op>
@@ -613,6 +536,18 @@ cudaError_t launch_ingest(int dtype, const void *W, void *D, int64_t n, int64_t 
     case 2: return ingest_impl<OpF32>(W, D, n, ld, status, s, launches);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_synth(int dtype, void *D, int64_t n, int64_t ld, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  dim3 g(grid_cols(n, 256), grid_rows(n));
+  switch (dtype) {
+    case 0: synth_kernel<OpI32><<<g, 256, 0, s>>>(static_cast<int32_t *>(D), n, ld); break;
+    case 1: synth_kernel<OpU16><<<g, 256, 0, s>>>(static_cast<uint16_t *>(D), n, ld); break;
+    case 2: synth_kernel<OpF32><<<g, 256, 0, s>>>(static_cast<float *>(D), n, ld); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pack(const int32_t *src, int64_t lds, uint16_t *dst, int64_t ldd, int64_t n, cudaStream_t s,

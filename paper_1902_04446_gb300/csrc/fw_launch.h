@@ -14,16 +14,24 @@ struct PhaseTimer {
   virtual ~PhaseTimer() {}
 };
 
-// Round width Bk used by launch_rounds for a dtype.
-int64_t round_width(int dtype);
+// Tunable shape of the per-round kernels: round width Bk (32 or 64) and the
+// Phase-3 variant (persistent TMA kernel, or one CTA per tile).
+struct RoundConfig {
+  int bk = 64;
+  bool tma = true;
+};
+constexpr int64_t kMaxRoundWidth = 64;  // panel buffers are sized for this
 
 // q rounds of Phase 1 -> Phase 2 -> Phase 3 on D (n x n, leading dimension ld).
-// colT is a Bk x ldT panel buffer of 32-bit words, ldT a multiple of 256 and >= n.
+// colT is a kMaxRoundWidth x ldT panel buffer of 32-bit words, ldT a multiple
+// of 256 and >= n.
 cudaError_t launch_rounds(int dtype, void *D, int64_t ld, int64_t n, void *colT, int64_t ldT, cudaStream_t s,
-                          int64_t *launches, PhaseTimer *timer = nullptr);
+                          int64_t *launches, PhaseTimer *timer = nullptr, const RoundConfig &cfg = RoundConfig());
 // Copies W to D when they differ and checks the input (status |= 1 invalid, 2 range).
 cudaError_t launch_ingest(int dtype, const void *W, void *D, int64_t n, int64_t ld, int *status, cudaStream_t s,
                           int64_t *launches);
+// Fills D with a synthetic symmetric graph (autotuner input).
+cudaError_t launch_synth(int dtype, void *D, int64_t n, int64_t ld, cudaStream_t s);
 cudaError_t launch_pack(const int32_t *src, int64_t lds, uint16_t *dst, int64_t ldd, int64_t n, cudaStream_t s,
                         int64_t *launches);
 cudaError_t launch_unpack(const uint16_t *src, int64_t lds, int32_t *dst, int64_t ldd, int64_t n, cudaStream_t s,

@@ -1,0 +1,190 @@
+// Phase bodies of one round of blocked Floyd-Warshall (the paper's Sec. 4.4/4.5,
+// Alg. 3 and 4), as device functions shared by the per-round kernels
+// (fw_kernels.cu) and the batched persistent kernel (batch.cu).
+//
+// Round k covers vertices [p0, p1) = [k*BK, min(n, (k+1)*BK)); w = p1 - p0.
+//   phase1_body   Floyd-Warshall closure of D_kk (Table 1 FloydWarshall); also
+//                 writes D_kk transposed into the panel buffer colT.
+//   p2_row_task   D_kJ = min(D_kJ, D_kk (x) D_kJ) for one column chunk J.
+//   p2_col_task   D_Ik = min(D_Ik, D_Ik (x) D_kk) for one row chunk I; writes
+//                 the updated block transposed into colT.
+//   p3_task       D_IJ = min(D_IJ, D_Ik (x) D_kJ) for one output tile, rows and
+//                 columns of the panel excluded (Table 1 MatProd + MatMin).
+// CG = true reads everything through L2 (ld.global.cg), which is required when
+// the producer of the data ran earlier in the same launch.
+#pragma once
+#include "fw_device.cuh"
+
+namespace apsp {
+
+template <bool CG, class T>
+__device__ __forceinline__ T ld_elem(const T *p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
+// ---------------------------------------------------------------- Phase 1
+// Needs blockDim.x == NT (NT = 256) and BK*(BK+1) scalars of shared memory.
+template <class Op, int BK, int NT, bool CG>
+__device__ __forceinline__ void phase1_body(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
+                                            uint32_t *__restrict__ colT, int64_t ldT, typename Op::scalar (*s)[BK + 1],
+                                            int tid) {
+  using S = typename Op::scalar;
+  constexpr int G = 16;        // 16 x 16 thread grid
+  constexpr int PT = BK / G;   // each thread owns PT x PT entries
+  static_assert(BK % G == 0 && NT == G * G, "phase 1 layout");
+  const int by = tid / G, bx = tid % G;
+  const S INF = Op::to_s(Op::inf_elem());
+  for (int idx = tid; idx < BK * BK; idx += NT) {
+    const int i = idx / BK, j = idx % BK;
+    const int64_t r = p0 + i, c = p0 + j;
+    s[i][j] = (r < n && c < n) ? Op::to_s(ld_elem<CG>(D + r * ld + c)) : INF;
+  }
+  __syncthreads();
+  S v[PT][PT];
+#pragma unroll
+  for (int r = 0; r < PT; ++r)
+#pragma unroll
+    for (int c = 0; c < PT; ++c) v[r][c] = s[by + G * r][bx + G * c];
+  // Step t relaxes every entry through vertex p0 + t; entries live in
+  // registers.  Step t + 1 reads only row t + 1 and column t + 1, so only
+  // those entries are written back to shared memory after step t.  Row t and
+  // column t do not change in step t (D_tt = 0, and INF + x >= x on padded
+  // vertices), so a write-back that lands while another thread still reads
+  // step t's row / column stores the value already there; one barrier per
+  // step orders the steps.
+  for (int t = 0; t < BK; ++t) {
+    S a[PT], b[PT];
+#pragma unroll
+    for (int r = 0; r < PT; ++r) a[r] = s[by + G * r][t];
+#pragma unroll
+    for (int c = 0; c < PT; ++c) b[c] = s[t][bx + G * c];
+#pragma unroll
+    for (int r = 0; r < PT; ++r)
+#pragma unroll
+      for (int c = 0; c < PT; ++c) v[r][c] = Op::s_addmin(a[r], b[c], v[r][c]);
+    const int tn = t + 1;
+    if (tn < BK) {
+      if (by == tn % G) {
+#pragma unroll
+        for (int c = 0; c < PT; ++c) s[tn][bx + G * c] = v[tn / G][c];
+      }
+      if (bx == tn % G) {
+#pragma unroll
+        for (int r = 0; r < PT; ++r) s[by + G * r][tn] = v[r][tn / G];
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < PT; ++r)
+#pragma unroll
+    for (int c = 0; c < PT; ++c) s[by + G * r][bx + G * c] = v[r][c];
+  __syncthreads();
+  for (int idx = tid; idx < BK * BK; idx += NT) {
+    const int i = idx / BK, j = idx % BK;
+    const int64_t r = p0 + i, c = p0 + j;
+    if (r < n && c < n) D[r * ld + c] = Op::from_s(s[i][j]);
+  }
+  for (int idx = tid; idx < BK * BK; idx += NT) {
+    const int t = idx / BK, i = idx % BK;
+    colT[t * ldT + p0 + i] = Op::dup(Op::from_s(s[i][t]));
+  }
+}
+
+// ---------------------------------------------------------------- Phase 2
+// Row panel chunk: output rows [p0, p0+BK), words [col0/EPW, col0/EPW + BNW).
+// A = D_kk (from colT), B = C = the chunk itself.  Shared memory: BK*BK + BK*BNW words.
+template <class Op, int BK, int BNW, int NT, bool CG>
+__device__ __forceinline__ void p2_row_task(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
+                                            int64_t p1, const uint32_t *__restrict__ colT, int64_t ldT, int64_t col0,
+                                            bool vec, uint32_t *smem, int tid) {
+  using Map = TileMap<BK, BNW>;
+  static_assert(Map::THREADS == NT, "row tile");
+  uint32_t *As = smem;
+  uint32_t *Bs = smem + BK * BK;
+  const int tx = tid % Map::TX, ty = tid / Map::TX;
+  uint32_t acc[8][8];
+  load_As_colT<BK, BK, NT, CG>(As, colT, ldT, p0, tid);
+  load_Bs_rows<Op, BNW, BK, NT, CG>(Bs, D, ld, n, n, p0, col0, vec, tid);
+  load_acc<Op, BK, BNW, CG>(D, ld, n, n, p0, col0, vec, acc, ty, tx);
+  __syncthreads();
+  tile_minplus<Op, BK, BNW, BK>(As, Bs, acc, ty, tx);
+  store_acc<Op, BK, BNW>(D, ld, n, n, p0, col0, 0, 0, p0, p1, vec, acc, ty, tx);
+}
+
+// Column panel chunk: output rows [row0, row0+BM), element columns [p0, p0+BK).
+// A = C = the chunk (transposed load), B = D_kk.  Shared memory: BK*BM + BK*(BK/EPW) words.
+template <class Op, int BK, int BM, int NT, bool CG>
+__device__ __forceinline__ void p2_col_task(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
+                                            int64_t p1, uint32_t *__restrict__ colT, int64_t ldT, int64_t row0,
+                                            bool vec, uint32_t *smem, int tid) {
+  constexpr int BNW = BK / Op::EPW;
+  using Map = TileMap<BM, BNW>;
+  static_assert(Map::THREADS == NT, "col tile");
+  uint32_t *As = smem;
+  uint32_t *Bs = smem + BK * BM;
+  const int tx = tid % Map::TX, ty = tid / Map::TX;
+  uint32_t acc[8][8];
+  load_As_transposed<Op, BM, BK, NT, CG>(As, D, ld, n, n, row0, p0, vec, tid);
+  load_Bs_rows<Op, BNW, BK, NT, CG>(Bs, D, ld, n, n, p0, p0, vec, tid);
+  load_acc<Op, BM, BNW, CG>(D, ld, n, n, row0, p0, vec, acc, ty, tx);
+  __syncthreads();
+  tile_minplus<Op, BM, BNW, BK>(As, Bs, acc, ty, tx);
+  store_acc<Op, BM, BNW>(D, ld, n, n, row0, p0, p0, p1, 0, 0, vec, acc, ty, tx);
+  // transposed copy: colT[t][row0 + i] = word(D_Ik[i][t]) for rows outside [p0, p1)
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      const int ib = Map::row(ty, 4 * g);  // 4 consecutive rows ib .. ib+3
+      const int64_t rb = row0 + ib;
+      const bool all_out = (rb + 3 < p0) || (rb >= p1);
+#pragma unroll
+      for (int cw = 0; cw < 4; ++cw) {
+        const int w = Map::wcol(tx, h) + cw;
+#pragma unroll
+        for (int lane = 0; lane < Op::EPW; ++lane) {
+          const int t = w * Op::EPW + lane;
+          uint32_t q4[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const uint32_t word = acc[4 * g + q][4 * h + cw];
+            q4[q] = (Op::EPW == 2) ? Op::dup(bits_elem<Op>(lane ? (word >> 16) : (word & 0xFFFFu))) : word;
+          }
+          uint32_t *dst = colT + (int64_t)t * ldT + rb;
+          if (all_out) {
+            *reinterpret_cast<uint4 *>(dst) = make_uint4(q4[0], q4[1], q4[2], q4[3]);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (rb + q < p0 || rb + q >= p1) dst[q] = q4[q];
+          }
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- Phase 3 (one tile)
+// Output tile rows [row0, row0+128), words [col0/EPW, +128); 256 threads;
+// shared memory 2 * BK * 128 words.
+template <class Op, int BK, bool CG>
+__device__ __forceinline__ void p3_task(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
+                                        int64_t p1, const uint32_t *__restrict__ colT, int64_t ldT, int64_t row0,
+                                        int64_t col0, bool vec, uint32_t *smem, int tid) {
+  constexpr int BM = 128, BNW = 128, NT = 256;
+  using Map = TileMap<BM, BNW>;
+  uint32_t *As = smem;
+  uint32_t *Bs = smem + BK * BM;
+  const int tx = tid % Map::TX, ty = tid / Map::TX;
+  uint32_t acc[8][8];
+  load_As_colT<BM, BK, NT, CG>(As, colT, ldT, row0, tid);
+  load_Bs_rows<Op, BNW, BK, NT, CG>(Bs, D, ld, n, n, p0, col0, vec, tid);
+  load_acc<Op, BM, BNW, CG>(D, ld, n, n, row0, col0, vec, acc, ty, tx);
+  __syncthreads();
+  tile_minplus<Op, BM, BNW, BK>(As, Bs, acc, ty, tx);
+  store_acc<Op, BM, BNW>(D, ld, n, n, row0, col0, p0, p1, p0, p1, vec, acc, ty, tx);
+}
+
+}  // namespace apsp

@@ -157,6 +157,51 @@ class Handle:
                                          D.data_ptr(), ld, _stream(stream, D.device)), "apsp_solve_edges")
         return D
 
+    def solve_batch(self, Ws, Ds=None, stream=None):
+        """apsp_solve_batch: many int32 graphs of uneven n in one persistent launch; returns the D list."""
+        import torch
+        Ws = list(Ws)
+        if Ds is None:
+            Ds = [torch.empty_like(W) for W in Ws]
+        k = len(Ws)
+        Wp = (ctypes.c_void_p * k)()
+        Dp = (ctypes.c_void_p * k)()
+        ns = (ctypes.c_int64 * k)()
+        lds = (ctypes.c_int64 * k)()
+        for i, (W, D) in enumerate(zip(Ws, Ds)):
+            n, ld = _mat(W, "W")
+            _elem_ok(W, APSP_I32)
+            nd, ldd = _mat(D, "D")
+            if nd != n or ldd != ld or D.dtype != W.dtype:
+                raise ValueError("D must have W's shape, leading dimension and dtype")
+            Wp[i], Dp[i], ns[i], lds[i] = W.data_ptr(), D.data_ptr(), n, ld
+        dev = Ws[0].device if Ws else torch.device("cuda", self.device)
+        self._check(_L().apsp_solve_batch(self._h, k, Wp, ns, lds, Dp, _stream(stream, dev)), "apsp_solve_batch")
+        return Ds
+
+    def check_bounded_wait(self, spin_limit: int = 1 << 12) -> int:
+        """apsp_check_bounded_wait: status of a batched launch whose first wait can never be satisfied."""
+        return int(_L().apsp_check_bounded_wait(self._h, spin_limit))
+
+    def autotune(self, dtype="int32", n_max: int = 4096, cache_path: str | None = None):
+        """apsp_autotune: time the round shapes per n bucket; returns {bucket: (Bk, tma)}."""
+        code = dtype_code(dtype)
+        self._check(_L().apsp_autotune(self._h, code, n_max, cache_path.encode() if cache_path else None),
+                    "apsp_autotune")
+        out, b = {}, 128
+        while True:
+            out[b] = self.tuned_config(code, b)
+            if b >= n_max:
+                return out
+            b <<= 1
+
+    def tuned_config(self, dtype, n: int):
+        """apsp_tuned_config: (Bk, tma) the handle uses for (dtype, n)."""
+        bk, tma = ctypes.c_int(), ctypes.c_int()
+        self._check(_L().apsp_tuned_config(self._h, dtype_code(dtype), n, ctypes.byref(bk), ctypes.byref(tma)),
+                    "apsp_tuned_config")
+        return int(bk.value), int(tma.value)
+
     def last_status(self, stream=None) -> int:
         """apsp_last_status: the device-side input check of the last solve (0 = OK)."""
         import torch

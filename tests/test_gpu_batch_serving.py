@@ -1,0 +1,174 @@
+"""Batched persistent solves and the request loop, against the oracle (GPU).
+
+Bit-exact for every graph, alone and in a mix; admission against a memory
+budget; queue limits; cancellation; bounded device waits that report a
+timeout status instead of hanging.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+INF = oracle.INF32
+
+
+@pytest.fixture(scope="module")
+def H(lib):
+    h = lib.Handle(device=0)
+    yield h
+    h.close()
+
+
+def er_dense(n, seed, deg=6.0, wmax=1000):
+    s, d, w = gen.er_graph(n, seed, avg_degree=deg, wmax=wmax) if n > 1 else (np.zeros(0, np.int64),) * 3
+    return gen.dense_matrix(n, s, d, w, dtype=np.int32)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+SIZES = [1, 2, 64, 65, 100, 257, 513, 700, 1000]
+
+
+def test_solve_batch_mixed_sizes_bit_exact(H):
+    Ws = [er_dense(n, 100 + n) for n in SIZES]
+    Ds = H.solve_batch([dev(W) for W in Ws])
+    assert H.last_status() == 0
+    for W, D in zip(Ws, Ds):
+        np.testing.assert_array_equal(D.cpu().numpy().astype(np.int64), oracle.fw(W.astype(np.int64)))
+
+
+def test_solve_batch_equals_alone_and_handles_in_place_and_empty(H):
+    Ws = [er_dense(n, 7 * n) for n in (300, 129, 640)]
+    alone = [H.solve_t("int32", dev(W)).cpu() for W in Ws]
+    ins = [dev(W) for W in Ws]
+    H.solve_batch(ins, ins)  # in place
+    for a, b in zip(alone, ins):
+        assert torch.equal(a, b.cpu())
+    assert H.solve_batch([]) == []
+    z = torch.zeros((0, 0), dtype=torch.int32, device="cuda")
+    H.solve_batch([z, dev(Ws[1])])
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(H):
+    assert H.check_bounded_wait(1 << 10) == 7  # APSP_E_TIMEOUT
+    W = er_dense(200, 3)
+    D = H.solve_t("int32", dev(W))
+    np.testing.assert_array_equal(D.cpu().numpy().astype(np.int64), oracle.fw(W.astype(np.int64)))
+
+
+def test_serving_mixed_equals_alone_and_oracle(H):
+    reqs = [gen.serving_request(1000 + i, n_lo=64, n_hi=900) for i in range(24)]
+    Ws = [gen.dense_matrix(r.n, r.src, r.dst, r.w, dtype=np.int32) for r in reqs]
+    # half device, half host (pinned and pageable) inputs
+    ins = [dev(W) if i % 2 == 0 else (torch.from_numpy(W).pin_memory() if i % 4 == 1 else torch.from_numpy(W))
+           for i, W in enumerate(Ws)]
+    tickets = [H.submit(x) for x in ins]
+    outs = []
+    for t, W in zip(tickets, Ws):
+        assert H.wait(t, 60000) == 0
+        st, ptr, rc = H.poll(t)
+        assert st == 3 and rc == 0 and ptr
+        out = torch.empty((W.shape[0], W.shape[0]), dtype=torch.int32, device="cuda")
+        H.fetch(t, out)
+        torch.cuda.synchronize()
+        outs.append(out.cpu())
+        assert H.release(t) == 0
+    for W, o in zip(Ws, outs):
+        alone = H.solve_t("int32", dev(W)).cpu()
+        assert torch.equal(o, alone)
+        np.testing.assert_array_equal(o.numpy().astype(np.int64), oracle.fw(W.astype(np.int64)))
+
+
+def test_serving_budget_admission_busy_cancel(lib):
+    big = er_dense(1000, 5)
+    small = [er_dense(n, n) for n in (100, 150, 200)]
+    budget = 1000 * 1000 * 4 + 64 * 1024 * 4 + 256  # exactly the big request
+    with lib.Handle(device=0, memory_budget=budget, queue_depth=2) as h:
+        with pytest.raises(lib.ApspError) as ei:
+            h.submit(dev(er_dense(1100, 1)))  # larger than the whole budget
+        assert ei.value.name == "APSP_E_NOMEM"
+        tb = h.submit(dev(big))
+        assert h.wait(tb, 60000) == 0
+        # the big matrix is held until released: the small ones stay queued
+        t1 = h.submit(dev(small[0]))
+        t2 = h.submit(dev(small[1]))
+        with pytest.raises(lib.ApspError) as ei:
+            h.submit(dev(small[2]))
+        assert ei.value.name == "APSP_E_BUSY"
+        import time
+        time.sleep(0.05)
+        assert h.poll(t1)[0] == 0 and h.poll(t2)[0] == 0  # QUEUED
+        assert h.cancel(t2) == 0
+        st, _, rc = h.poll(t2)
+        assert st == 4 and rc == 8  # ERROR, APSP_E_CANCELLED
+        assert h.release(tb) == 0  # memory returns: t1 is admitted and runs
+        assert h.wait(t1, 60000) == 0
+        out = torch.empty((100, 100), dtype=torch.int32, device="cuda")
+        h.fetch(t1, out)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out.cpu().numpy().astype(np.int64), oracle.fw(small[0].astype(np.int64)))
+        h.release(t1)
+        h.release(t2)
+
+
+def test_serving_reports_input_errors_per_request(H):
+    good1, good2 = er_dense(120, 11), er_dense(90, 12)
+    bad = er_dense(90, 2)
+    bad[5, 7] = -1
+    ts = [H.submit(dev(x)) for x in (good1, bad, good2)]  # usually admitted as one group
+    assert [H.wait(t, 60000) for t in ts] == [0, 1, 0]  # only the bad one is APSP_E_INVALID
+    st, _, rc = H.poll(ts[1])
+    assert st == 4 and rc == 1
+    for t, W in ((ts[0], good1), (ts[2], good2)):
+        out = torch.empty(W.shape, dtype=torch.int32, device="cuda")
+        H.fetch(t, out)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out.cpu().numpy().astype(np.int64), oracle.fw(W.astype(np.int64)))
+    for t in ts:
+        H.release(t)
+
+
+def test_autotune_cache_and_bit_exact_with_every_shape(lib, tmp_path):
+    cache = str(tmp_path / "tune.json")
+    with lib.Handle(device=0) as h:
+        table = h.autotune("int32", 512, cache)
+        assert set(table) == {128, 256, 512}
+        assert all(bk in (32, 64) and tma in (0, 1) for bk, tma in table.values())
+    import json
+    entries = json.load(open(cache))["entries"]
+    assert {e["n"] for e in entries} == {128, 256, 512} and all(e["ms"] > 0 for e in entries)
+    with lib.Handle(device=0) as h2:
+        assert h2.autotune("int32", 512, cache) == table  # loaded from the cache
+    # every round shape gives the same exact answer
+    W = er_dense(300, 77)
+    E = oracle.fw(W.astype(np.int64))
+    for bk in (32, 64):
+        with lib.Handle(device=0, block_k=bk) as hb:
+            assert hb.tuned_config("int32", 300)[0] == bk
+            for dt, Wx in (("int32", W), ("u16", None)):
+                if dt == "u16":
+                    Wx = np.where(W >= INF, 0x7FFF, W).astype(np.int16)
+                    if E[E < INF].max() >= 0x7FFF:
+                        continue
+                D = hb.solve_t(dt, dev(Wx)).cpu().numpy()
+                if dt == "u16":
+                    D = oracle.unpack_u16(D.view(np.uint16))
+                np.testing.assert_array_equal(D.astype(np.int64), E)
+
+
+@pytest.mark.parametrize("n", [31, 100, 257, 1000])
+def test_block_k_32_matches_oracle(lib, n):
+    W = er_dense(n, 5 + n)
+    with lib.Handle(device=0, block_k=32) as h:
+        D = h.solve_t("int32", dev(W)).cpu().numpy()
+        np.testing.assert_array_equal(D.astype(np.int64), oracle.fw(W.astype(np.int64)))
+        Wf = np.where(W >= INF, np.inf, W).astype(np.float32)
+        Df = h.solve_t("fp32", dev(Wf)).cpu().numpy()
+        E = oracle.fw(W.astype(np.int64)).astype(np.float64)
+        E[E >= INF] = np.inf
+        np.testing.assert_array_equal(Df.astype(np.float64), E)  # small integers: exact in fp32
