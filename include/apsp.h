@@ -80,6 +80,8 @@ typedef struct {
   int queue_depth;       /* serving: pending requests before APSP_E_BUSY (default 4096) */
   int64_t memory_budget; /* serving: bytes of device memory for admitted requests (0 = free HBM - reserve) */
   int64_t spin_limit;    /* bounded device waits: iterations before APSP_E_TIMEOUT (0 = default) */
+  int phase3_variant;    /* Phase-3 kernel: 0 = tuned or default, 1 = one CTA per tile, 2 = persistent
+                            TMA kernel with 256 threads, 3 = persistent TMA kernel with 512 threads */
 } apsp_config;
 
 /* Fills *cfg with the defaults. */

@@ -210,15 +210,19 @@ int64_t bucket_of(int64_t n) {
 // largest tuned bucket for larger n), else Bk = 64 with the TMA Phase 3.
 apsp::RoundConfig config_for(apsp_handle *h, int dtype, int64_t n) {
   apsp::RoundConfig c;
-  if (h->cfg.block_k == 32 || h->cfg.block_k == 64) {
-    c.bk = h->cfg.block_k;
-    return c;
-  }
   const int64_t b = bucket_of(n);
   auto it = h->tuned.find({dtype, b});
-  if (it != h->tuned.end()) return it->second;
-  for (auto r = h->tuned.rbegin(); r != h->tuned.rend(); ++r)
-    if (r->first.first == dtype && r->first.second < b) return r->second;
+  if (it != h->tuned.end()) {
+    c = it->second;
+  } else {
+    for (auto r = h->tuned.rbegin(); r != h->tuned.rend(); ++r)
+      if (r->first.first == dtype && r->first.second < b) {
+        c = r->second;
+        break;
+      }
+  }
+  if (h->cfg.block_k == 32 || h->cfg.block_k == 64) c.bk = h->cfg.block_k;
+  if (h->cfg.phase3_variant >= 1 && h->cfg.phase3_variant <= 3) c.p3 = h->cfg.phase3_variant - 1;
   return c;
 }
 
@@ -336,6 +340,7 @@ apsp_status apsp_create(apsp_handle **out, const apsp_config *cfg) {
   if (cfg) c = *cfg;
   if (c.dtype != APSP_AUTO && !valid_dtype(c.dtype)) return APSP_E_INVALID;
   if (c.block_k != 0 && c.block_k != 32 && c.block_k != 64) return APSP_E_INVALID;
+  if (c.phase3_variant < 0 || c.phase3_variant > 3) return APSP_E_INVALID;
   if (c.max_batch <= 0) c.max_batch = 64;
   if (c.queue_depth <= 0) c.queue_depth = 4096;
   int ndev = 0;
@@ -715,7 +720,8 @@ std::vector<TuneEntry> read_cache(const char *path) {
     e.bk = (int)json_num_field(obj, "bk", 64);
     e.tma = (int)json_num_field(obj, "tma", 1);
     e.ms = json_num_field(obj, "ms", 0);
-    if (!e.gpu.empty() && e.dtype >= 0 && e.n > 0 && (e.bk == 32 || e.bk == 64)) out.push_back(e);
+    if (!e.gpu.empty() && e.dtype >= 0 && e.n > 0 && (e.bk == 32 || e.bk == 64) && e.tma >= 0 && e.tma <= 2)
+      out.push_back(e);
     p = b + 1;
   }
   return out;
@@ -760,7 +766,7 @@ apsp_status apsp_autotune(apsp_handle *h, int dtype, int64_t n_max, const char *
       if (t.gpu == gpu && t.dtype == dtype && t.n == b) {
         apsp::RoundConfig c;
         c.bk = t.bk;
-        c.tma = t.tma != 0;
+        c.p3 = t.tma;
         h->tuned[{dtype, b}] = c;
         cached = true;
       }
@@ -778,10 +784,10 @@ apsp_status apsp_autotune(apsp_handle *h, int dtype, int64_t n_max, const char *
     double best = 1e30;
     apsp::RoundConfig best_c;
     for (int bk : {32, 64})
-      for (int tma : {1, 0}) {
+      for (int var : {1, 2, 0}) {
         apsp::RoundConfig c;
         c.bk = bk;
-        c.tma = tma != 0;
+        c.p3 = var;
         double t_min = 1e30;
         for (int rep = 0; rep < 4; ++rep) {
           apsp::launch_synth(dtype, M, b, b, nullptr);
@@ -810,7 +816,7 @@ apsp_status apsp_autotune(apsp_handle *h, int dtype, int64_t n_max, const char *
     t.dtype = dtype;
     t.n = b;
     t.bk = best_c.bk;
-    t.tma = best_c.tma ? 1 : 0;
+    t.tma = best_c.p3;
     t.ms = best;
     cache.push_back(t);
     wrote = true;
@@ -824,7 +830,7 @@ apsp_status apsp_tuned_config(apsp_handle *h, int dtype, int64_t n, int *block_k
   std::lock_guard<std::mutex> g(h->mu);
   const apsp::RoundConfig c = config_for(h, dtype, n);
   *block_k = c.bk;
-  *tma = c.tma ? 1 : 0;
+  *tma = c.p3;
   return APSP_OK;
 }
 

@@ -38,14 +38,16 @@ constexpr int NT = 256;
 constexpr int P2_ROW_BNW = 256;  // row-panel chunk: 64 x 256 words
 constexpr int P2_COL_BM = 256;   // column-panel chunk: 256 x 64 words
 constexpr int SMEM_WORDS = BK * BK + BK * P2_ROW_BNW;  // 80 KB: the largest task (Phase 2)
-static_assert(SMEM_WORDS >= BK * P2_COL_BM + BK * BK && SMEM_WORDS >= 2 * BK * 128, "shared memory");
+static_assert(SMEM_WORDS >= BK * P2_COL_BM + BK * BK && SMEM_WORDS >= 2 * BK * 128 &&
+                  SMEM_WORDS * 4 >= (int)sizeof(P1Smem<OpI32, BK>),
+              "shared memory");
 
 __device__ __forceinline__ int ld_volatile(const int *p) { return *reinterpret_cast<const volatile int *>(p); }
 
 // Each task kind is compiled as its own function so that its register
 // allocation does not add to the others' under the kernel's 128-register cap.
 __device__ __noinline__ void task_p1(const BatchGraph &g, int64_t p0, uint32_t *smem, int tid) {
-  auto *s = reinterpret_cast<int32_t(*)[BK + 1]>(smem);
+  auto &s = *reinterpret_cast<P1Smem<OpI32, BK> *>(smem);
   phase1_body<OpI32, BK, NT, true>(g.D, g.ld, g.n, p0, g.colT, g.ldT, s, tid);
 }
 __device__ __noinline__ void task_p2_row(const BatchGraph &g, int64_t p0, int64_t p1, int idx, uint32_t *smem,

@@ -182,44 +182,52 @@ __device__ __forceinline__ uint32_t col_mask(int64_t c0, int64_t ncols, int64_t 
 //                              over the lanes of its word
 //   Bs[t][w]  (BK x BNW words) B operand
 //   acc[r][c] += min-plus over t:  acc = min(acc, As[t][row r] + Bs[t][col c])
-template <int BM, int BNW>
+template <int BM, int BNW, int TN = 8>
 struct TileMap {
-  static constexpr int TX = BNW / 8;
+  static_assert(TN == 8 || TN == 4, "8 or 4 words per thread and row");
+  static constexpr int TX = BNW / TN;
   static constexpr int TY = BM / 8;
   static constexpr int THREADS = TX * TY;
+  static constexpr int NH = TN / 4;  // 16-byte column chunks per thread and row
   __device__ __forceinline__ static int row(int ty, int r) { return (r < 4) ? (ty * 4 + r) : (BM / 2 + ty * 4 + r - 4); }
   __device__ __forceinline__ static int wcol(int tx, int h) { return h == 0 ? tx * 4 : BNW / 2 + tx * 4; }
 };
 
-template <class Op, int BM, int BNW, int BK>
+template <class Op, int BM, int BNW, int BK, int TN = 8>
 __device__ __forceinline__ void tile_minplus(const uint32_t *__restrict__ As, const uint32_t *__restrict__ Bs,
-                                             uint32_t (&acc)[8][8], int ty, int tx) {
+                                             uint32_t (&acc)[8][TN], int ty, int tx) {
 #pragma unroll 4
   for (int t = 0; t < BK; ++t) {
     const uint4 a0 = *reinterpret_cast<const uint4 *>(As + t * BM + ty * 4);
     const uint4 a1 = *reinterpret_cast<const uint4 *>(As + t * BM + BM / 2 + ty * 4);
-    const uint4 b0 = *reinterpret_cast<const uint4 *>(Bs + t * BNW + tx * 4);
-    const uint4 b1 = *reinterpret_cast<const uint4 *>(Bs + t * BNW + BNW / 2 + tx * 4);
     const uint32_t a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-    const uint32_t b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+    uint32_t b[TN];
+#pragma unroll
+    for (int h = 0; h < TN / 4; ++h) {
+      const uint4 bv = *reinterpret_cast<const uint4 *>(Bs + t * BNW + (h == 0 ? tx * 4 : BNW / 2 + tx * 4));
+      b[4 * h + 0] = bv.x;
+      b[4 * h + 1] = bv.y;
+      b[4 * h + 2] = bv.z;
+      b[4 * h + 3] = bv.w;
+    }
 #pragma unroll
     for (int r = 0; r < 8; ++r)
 #pragma unroll
-      for (int c = 0; c < 8; ++c) acc[r][c] = Op::addmin(a[r], b[c], acc[r][c]);
+      for (int c = 0; c < TN; ++c) acc[r][c] = Op::addmin(a[r], b[c], acc[r][c]);
   }
 }
 
 // Loads the thread's 8 x 8 word block of the output tile whose top-left
 // element is (row0, col0) from M (INF outside [0,nrows) x [0,ncols)).
-template <class Op, int BM, int BNW, bool CG = false>
+template <class Op, int BM, int BNW, bool CG = false, int TN = 8>
 __device__ __forceinline__ void load_acc(const typename Op::elem *M, int64_t ld, int64_t nrows, int64_t ncols,
-                                         int64_t row0, int64_t col0, bool vec, uint32_t (&acc)[8][8], int ty,
+                                         int64_t row0, int64_t col0, bool vec, uint32_t (&acc)[8][TN], int ty,
                                          int tx) {
-  using Map = TileMap<BM, BNW>;
+  using Map = TileMap<BM, BNW, TN>;
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < Map::NH; ++h) {
       const uint4 v = load_chunk<Op, CG>(M, ld, nrows, ncols, row0 + Map::row(ty, r),
                                          col0 + (int64_t)Map::wcol(tx, h) * Op::EPW, vec);
       acc[r][4 * h + 0] = v.x;
@@ -233,13 +241,13 @@ __device__ __forceinline__ void load_acc(const typename Op::elem *M, int64_t ld,
 // Stores the thread's block: row r is written when it lies in [0, nrows) and
 // outside [xr0, xr1); an element column when it lies in [0, ncols) and outside
 // [xc0, xc1).
-template <class Op, int BM, int BNW>
+template <class Op, int BM, int BNW, int TN = 8>
 __device__ __forceinline__ void store_acc(typename Op::elem *M, int64_t ld, int64_t nrows, int64_t ncols,
                                           int64_t row0, int64_t col0, int64_t xr0, int64_t xr1, int64_t xc0,
-                                          int64_t xc1, bool vec, const uint32_t (&acc)[8][8], int ty, int tx) {
-  using Map = TileMap<BM, BNW>;
+                                          int64_t xc1, bool vec, const uint32_t (&acc)[8][TN], int ty, int tx) {
+  using Map = TileMap<BM, BNW, TN>;
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
+  for (int h = 0; h < Map::NH; ++h) {
     const int64_t c0 = col0 + (int64_t)Map::wcol(tx, h) * Op::EPW;
     const uint32_t cm = col_mask<Op>(c0, ncols, xc0, xc1);
 #pragma unroll

@@ -44,7 +44,7 @@ constexpr int P1_THREADS = 256;
 template <class Op, int BK>
 __global__ void __launch_bounds__(P1_THREADS) fw_phase1(typename Op::elem *__restrict__ D, int64_t ld, int64_t n,
                                                         int64_t p0, uint32_t *__restrict__ colT, int64_t ldT) {
-  __shared__ typename Op::scalar s[BK][BK + 1];
+  __shared__ P1Smem<Op, BK> s;
   phase1_body<Op, BK, P1_THREADS, false>(D, ld, n, p0, colT, ldT, s, threadIdx.x);
 }
 
@@ -111,7 +111,6 @@ __global__ void __launch_bounds__(256, 2) fw_phase3(typename Op::elem *__restric
 // >= n, never stored, and (c) B rows >= n of the last, partial round, which
 // meet A words colT[t][.] that Phases 1 and 2 set to INF for those t, so the
 // sum is INF and never wins.
-constexpr int P3T_THREADS = 256;
 constexpr int P3T_C_BYTES = 128 * 128 * 4;
 constexpr uint32_t P3T_WAIT_LIMIT = 1u << 26;
 template <int BK>
@@ -120,14 +119,16 @@ struct P3T {
   static constexpr int SMEM = 2 * STAGE_BYTES + P3T_C_BYTES + 1024;
 };
 
-template <class Op, int BK>
-__global__ void __launch_bounds__(P3T_THREADS, 1)
+// TN = 8: 256 threads with 8 x 8 words each; TN = 4: 512 threads with 8 x 4
+// words each (twice the warps per SM to hide instruction latency).
+template <class Op, int BK, int TN>
+__global__ void __launch_bounds__(TileMap<128, 128, TN>::THREADS, 1)
     fw_phase3_tma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                   const __grid_constant__ CUtensorMap mapC, typename Op::elem *__restrict__ D, int64_t ld, int64_t n,
                   int64_t p0, int64_t p1, int tiles_x, int tiles_total, int *err) {
   constexpr int BM = 128, BNW = 128;
   constexpr int P3T_STAGE_BYTES = P3T<BK>::STAGE_BYTES;
-  using Map = TileMap<BM, BNW>;
+  using Map = TileMap<BM, BNW, TN>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t bar_ab[2];
   __shared__ __align__(8) uint64_t bar_c;
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(P3T_THREADS, 1)
   // parity of the next completion of bar_c (bit 0) and bar_ab[s] (bit 1 + s);
   // `pend` has the same bits set while a copy on that barrier is in flight
   uint32_t par = 0u, pend = 1u | 2u;
-  uint32_t acc[8][8];
+  uint32_t acc[8][TN];
   for (int t = t_begin; t < t_end; ++t) {
     const int s = (t - t_begin) & 1;
     if (!mbar_wait_bounded(&bar_c, par & 1u, P3T_WAIT_LIMIT)) abort_flag = 1;
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(P3T_THREADS, 1)
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < Map::NH; ++h) {
         const uint4 v = *reinterpret_cast<const uint4 *>(Cs + Map::row(ty, r) * BNW + Map::wcol(tx, h));
         acc[r][4 * h + 0] = v.x;
         acc[r][4 * h + 1] = v.y;
@@ -207,8 +208,8 @@ __global__ void __launch_bounds__(P3T_THREADS, 1)
     pend &= ~bit;
     __syncwarp();
     if (abort_flag) break;
-    tile_minplus<Op, BM, BNW, BK>(stA(s), stB(s), acc, ty, tx);
-    store_acc<Op, BM, BNW>(D, ld, n, n, tile_row0(t), tile_col0(t), p0, p1, p0, p1, true, acc, ty, tx);
+    tile_minplus<Op, BM, BNW, BK, TN>(stA(s), stB(s), acc, ty, tx);
+    store_acc<Op, BM, BNW, TN>(D, ld, n, n, tile_row0(t), tile_col0(t), p0, p1, p0, p1, true, acc, ty, tx);
   }
   if (abort_flag && tid == 0) {
     // a wait gave up: wait (bounded) for this CTA's copies still in flight
@@ -429,8 +430,9 @@ static inline unsigned grid_cols(int64_t n, int threads) {
 }
 
 template <class Op, int BK>
-static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int64_t ldT, bool vec, bool use_tma,
+static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int64_t ldT, bool vec, int variant,
                                cudaStream_t s, int64_t *launches, PhaseTimer *tm) {
+  const bool use_tma = variant != 0;
   using E = typename Op::elem;
   E *D = static_cast<E *>(Dv);
   uint32_t *colT = static_cast<uint32_t *>(colTv);
@@ -458,7 +460,10 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
     err = tma ? error_word() : nullptr;
     tma = tma && err != nullptr;
     if (tma) {
-      e = cudaFuncSetAttribute(fw_phase3_tma<Op, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, P3T<BK>::SMEM);
+      e = cudaFuncSetAttribute(fw_phase3_tma<Op, BK, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, P3T<BK>::SMEM);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fw_phase3_tma<Op, BK, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 P3T<BK>::SMEM);
       if (e != cudaSuccess) return e;
     }
   }
@@ -481,9 +486,12 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
       fw_phase2<Op, BK><<<nrow + ncol, C2::THREADS, C2::SMEM, s>>>(D, ld, n, p0, p1, colT, ldT, nrow, vec ? 1 : 0);
       if (tm) tm->after(1, s, 2.0 * rest * w * w);
       if (tm) tm->before(2, s);
-      if (tma)
-        fw_phase3_tma<Op, BK><<<grid_tma, P3T_THREADS, P3T<BK>::SMEM, s>>>(mA, mB, mC, D, ld, n, p0, p1, tiles_x,
-                                                                           tiles_total, err);
+      if (tma && variant == 2)
+        fw_phase3_tma<Op, BK, 4><<<grid_tma, TileMap<128, 128, 4>::THREADS, P3T<BK>::SMEM, s>>>(
+            mA, mB, mC, D, ld, n, p0, p1, tiles_x, tiles_total, err);
+      else if (tma)
+        fw_phase3_tma<Op, BK, 8><<<grid_tma, TileMap<128, 128, 8>::THREADS, P3T<BK>::SMEM, s>>>(
+            mA, mB, mC, D, ld, n, p0, p1, tiles_x, tiles_total, err);
       else
         fw_phase3<Op, BK><<<g3, C3::THREADS, SMEM3, s>>>(D, ld, n, p0, p1, colT, ldT, vec ? 1 : 0);
       if (tm) tm->after(2, s, rest * rest * w);
@@ -501,8 +509,8 @@ template <class Op>
 static cudaError_t rounds_bk(const RoundConfig &cfg, void *D, int64_t ld, int64_t n, void *colT, int64_t ldT,
                              cudaStream_t s, int64_t *launches, PhaseTimer *tm) {
   const bool vec = aligned16(D, ld, sizeof(typename Op::elem));
-  if (cfg.bk == 32) return rounds_impl<Op, 32>(D, ld, n, colT, ldT, vec, cfg.tma, s, launches, tm);
-  if (cfg.bk == 64) return rounds_impl<Op, 64>(D, ld, n, colT, ldT, vec, cfg.tma, s, launches, tm);
+  if (cfg.bk == 32) return rounds_impl<Op, 32>(D, ld, n, colT, ldT, vec, cfg.p3, s, launches, tm);
+  if (cfg.bk == 64) return rounds_impl<Op, 64>(D, ld, n, colT, ldT, vec, cfg.p3, s, launches, tm);
   return cudaErrorInvalidValue;
 }
 

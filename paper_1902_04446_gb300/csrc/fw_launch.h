@@ -15,10 +15,13 @@ struct PhaseTimer {
 };
 
 // Tunable shape of the per-round kernels: round width Bk (32 or 64) and the
-// Phase-3 variant (persistent TMA kernel, or one CTA per tile).
+// Phase-3 variant: 0 = one CTA per tile, 1 = persistent TMA kernel with 256
+// threads (8 x 8 words each), 2 = persistent TMA kernel with 512 threads
+// (8 x 4 words each).  The TMA variants need a 16-byte addressable matrix and
+// fall back to variant 0 otherwise.
 struct RoundConfig {
   int bk = 64;
-  bool tma = true;
+  int p3 = 1;
 };
 constexpr int64_t kMaxRoundWidth = 64;  // panel buffers are sized for this
 

@@ -24,15 +24,22 @@ __device__ __forceinline__ T ld_elem(const T *p) {
 }
 
 // ---------------------------------------------------------------- Phase 1
-// Needs blockDim.x == NT (NT = 256) and BK*(BK+1) scalars of shared memory.
+// Needs blockDim.x == NT (NT = 256) and BK * (BK + 4) scalars of shared memory.
+// Thread (by, bx) of a 16 x 16 grid owns the PT x PT block of rows by*PT + r,
+// columns bx*PT + c (PT = BK / 16) in registers.
+template <class Op, int BK>
+struct P1Smem {
+  typename Op::scalar s[BK][BK + 4];
+};
+
 template <class Op, int BK, int NT, bool CG>
 __device__ __forceinline__ void phase1_body(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
-                                            uint32_t *__restrict__ colT, int64_t ldT, typename Op::scalar (*s)[BK + 1],
-                                            int tid) {
+                                            uint32_t *__restrict__ colT, int64_t ldT, P1Smem<Op, BK> &sm, int tid) {
   using S = typename Op::scalar;
-  constexpr int G = 16;        // 16 x 16 thread grid
-  constexpr int PT = BK / G;   // each thread owns PT x PT entries
+  constexpr int G = 16;
+  constexpr int PT = BK / G;
   static_assert(BK % G == 0 && NT == G * G, "phase 1 layout");
+  auto &s = sm.s;
   const int by = tid / G, bx = tid % G;
   const S INF = Op::to_s(Op::inf_elem());
   for (int idx = tid; idx < BK * BK; idx += NT) {
@@ -45,41 +52,47 @@ __device__ __forceinline__ void phase1_body(typename Op::elem *__restrict__ D, i
 #pragma unroll
   for (int r = 0; r < PT; ++r)
 #pragma unroll
-    for (int c = 0; c < PT; ++c) v[r][c] = s[by + G * r][bx + G * c];
+    for (int c = 0; c < PT; ++c) v[r][c] = s[by * PT + r][bx * PT + c];
   // Step t relaxes every entry through vertex p0 + t; entries live in
   // registers.  Step t + 1 reads only row t + 1 and column t + 1, so only
-  // those entries are written back to shared memory after step t.  Row t and
-  // column t do not change in step t (D_tt = 0, and INF + x >= x on padded
-  // vertices), so a write-back that lands while another thread still reads
-  // step t's row / column stores the value already there; one barrier per
-  // step orders the steps.
-  for (int t = 0; t < BK; ++t) {
-    S a[PT], b[PT];
+  // those entries go back to shared memory after step t.  Row t and column t
+  // do not change in step t (D_tt = 0, and INF + x >= x on padded vertices),
+  // so a write-back that lands while another thread still reads step t's row
+  // or column stores the value already there; one barrier per step orders the
+  // steps.  The step loop is unrolled by PT so that every register index is a
+  // compile-time constant.
+  for (int t0 = 0; t0 < BK; t0 += PT) {
 #pragma unroll
-    for (int r = 0; r < PT; ++r) a[r] = s[by + G * r][t];
+    for (int tt = 0; tt < PT; ++tt) {
+      const int t = t0 + tt;
+      S a[PT], b[PT];
 #pragma unroll
-    for (int c = 0; c < PT; ++c) b[c] = s[t][bx + G * c];
+      for (int r = 0; r < PT; ++r) a[r] = s[by * PT + r][t];
 #pragma unroll
-    for (int r = 0; r < PT; ++r)
+      for (int c = 0; c < PT; ++c) b[c] = s[t][bx * PT + c];
 #pragma unroll
-      for (int c = 0; c < PT; ++c) v[r][c] = Op::s_addmin(a[r], b[c], v[r][c]);
-    const int tn = t + 1;
-    if (tn < BK) {
-      if (by == tn % G) {
+      for (int r = 0; r < PT; ++r)
 #pragma unroll
-        for (int c = 0; c < PT; ++c) s[tn][bx + G * c] = v[tn / G][c];
+        for (int c = 0; c < PT; ++c) v[r][c] = Op::s_addmin(a[r], b[c], v[r][c]);
+      const int q = (tt + 1) % PT;                 // local index of row / column t + 1 (constant once unrolled)
+      const int owner = t0 / PT + (tt + 1) / PT;   // block index of row / column t + 1
+      if (t + 1 < BK) {
+        if (by == owner) {
+#pragma unroll
+          for (int c = 0; c < PT; ++c) s[t + 1][bx * PT + c] = v[q][c];
+        }
+        if (bx == owner) {
+#pragma unroll
+          for (int r = 0; r < PT; ++r) s[by * PT + r][t + 1] = v[r][q];
+        }
       }
-      if (bx == tn % G) {
-#pragma unroll
-        for (int r = 0; r < PT; ++r) s[by + G * r][tn] = v[r][tn / G];
-      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 #pragma unroll
   for (int r = 0; r < PT; ++r)
 #pragma unroll
-    for (int c = 0; c < PT; ++c) s[by + G * r][bx + G * c] = v[r][c];
+    for (int c = 0; c < PT; ++c) s[by * PT + r][bx * PT + c] = v[r][c];
   __syncthreads();
   for (int idx = tid; idx < BK * BK; idx += NT) {
     const int i = idx / BK, j = idx % BK;

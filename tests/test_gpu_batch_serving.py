@@ -86,7 +86,7 @@ def test_serving_mixed_equals_alone_and_oracle(H):
 
 def test_serving_budget_admission_busy_cancel(lib):
     big = er_dense(1000, 5)
-    small = [er_dense(n, n) for n in (100, 150, 200)]
+    small = [er_dense(n, n) for n in (300, 320, 340)]  # each larger than the big one's panel buffer
     budget = 1000 * 1000 * 4 + 64 * 1024 * 4 + 256  # exactly the big request
     with lib.Handle(device=0, memory_budget=budget, queue_depth=2) as h:
         with pytest.raises(lib.ApspError) as ei:
@@ -108,7 +108,7 @@ def test_serving_budget_admission_busy_cancel(lib):
         assert st == 4 and rc == 8  # ERROR, APSP_E_CANCELLED
         assert h.release(tb) == 0  # memory returns: t1 is admitted and runs
         assert h.wait(t1, 60000) == 0
-        out = torch.empty((100, 100), dtype=torch.int32, device="cuda")
+        out = torch.empty((300, 300), dtype=torch.int32, device="cuda")
         h.fetch(t1, out)
         torch.cuda.synchronize()
         np.testing.assert_array_equal(out.cpu().numpy().astype(np.int64), oracle.fw(small[0].astype(np.int64)))

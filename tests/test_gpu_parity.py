@@ -304,3 +304,23 @@ def test_gmm16k_auto_equals_int32(H):
     A = H.solve_t("auto", W)
     B = H.solve_t("int32", W)
     assert torch.equal(A, B)
+
+
+# ------------------------------------------------------------------ every round shape
+@pytest.mark.parametrize("block_k", [32, 64])
+@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("dt", ["int32", "u16", "fp32"])
+def test_every_round_shape_matches_oracle(lib, block_k, variant, dt):
+    n = 777
+    s, d, w = er_edges(n, seed=block_k + 10 * variant, deg=3.0, wmax=40)
+    E = expect_fw(gen.dense_matrix(n, s, d, w, dtype=np.int32))
+    with lib.Handle(device=0, block_k=block_k, phase3_variant=variant) as h:
+        if dt == "int32":
+            D = h.solve_t(dt, dev(gen.dense_matrix(n, s, d, w, dtype=np.int32))).cpu().numpy().astype(np.int64)
+        elif dt == "u16":
+            D16 = h.solve_t(dt, dev(gen.dense_matrix(n, s, d, w, dtype=np.int16, inf=0x7FFF))).cpu().numpy()
+            D = oracle.unpack_u16(D16.view(np.uint16)).astype(np.int64)
+        else:
+            Df = h.solve_t(dt, dev(gen.dense_matrix(n, s, d, w, dtype=np.float32))).cpu().numpy()
+            D = np.where(np.isinf(Df), INF, Df.astype(np.float64)).astype(np.int64)  # small integers: exact
+        np.testing.assert_array_equal(D, E)
