@@ -237,7 +237,8 @@ apsp_status run_rounds_locked(apsp_handle *h, int dtype, void *D, int64_t n, int
     return e == cudaErrorMemoryAllocation ? APSP_E_NOMEM : APSP_E_CUDA;
   }
   int64_t l = 0;
-  e = apsp::launch_rounds(dtype, D, ld, n, h->colT, ldT, s, &l, h->prof.get(), config_for(h, dtype, n));
+  e = apsp::launch_rounds(dtype, D, ld, n, h->colT, ldT, s, &l, h->prof.get(), config_for(h, dtype, n),
+                          h->d_status);
   h->launches += l;
   if (e != cudaSuccess) {
     h->last_error = std::string("rounds: ") + cudaGetErrorString(e);

@@ -431,7 +431,7 @@ static inline unsigned grid_cols(int64_t n, int threads) {
 
 template <class Op, int BK>
 static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int64_t ldT, bool vec, int variant,
-                               cudaStream_t s, int64_t *launches, PhaseTimer *tm) {
+                               cudaStream_t s, int64_t *launches, PhaseTimer *tm, int *wait_err) {
   const bool use_tma = variant != 0;
   using E = typename Op::elem;
   E *D = static_cast<E *>(Dv);
@@ -457,7 +457,7 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
                    BK) &&
           make_map(&mB, dt, D, (uint64_t)n, (uint64_t)n, (uint64_t)ld * sizeof(E), 128 * Op::EPW, BK) &&
           make_map(&mC, dt, D, (uint64_t)n, (uint64_t)n, (uint64_t)ld * sizeof(E), 128 * Op::EPW, 128);
-    err = tma ? error_word() : nullptr;
+    err = tma ? (wait_err ? wait_err : error_word()) : nullptr;
     tma = tma && err != nullptr;
     if (tma) {
       e = cudaFuncSetAttribute(fw_phase3_tma<Op, BK, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, P3T<BK>::SMEM);
@@ -507,20 +507,20 @@ static bool aligned16(const void *p, int64_t ld, size_t esz) {
 
 template <class Op>
 static cudaError_t rounds_bk(const RoundConfig &cfg, void *D, int64_t ld, int64_t n, void *colT, int64_t ldT,
-                             cudaStream_t s, int64_t *launches, PhaseTimer *tm) {
+                             cudaStream_t s, int64_t *launches, PhaseTimer *tm, int *wait_err) {
   const bool vec = aligned16(D, ld, sizeof(typename Op::elem));
-  if (cfg.bk == 32) return rounds_impl<Op, 32>(D, ld, n, colT, ldT, vec, cfg.p3, s, launches, tm);
-  if (cfg.bk == 64) return rounds_impl<Op, 64>(D, ld, n, colT, ldT, vec, cfg.p3, s, launches, tm);
+  if (cfg.bk == 32) return rounds_impl<Op, 32>(D, ld, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err);
+  if (cfg.bk == 64) return rounds_impl<Op, 64>(D, ld, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err);
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_rounds(int dtype, void *D, int64_t ld, int64_t n, void *colT, int64_t ldT, cudaStream_t s,
-                          int64_t *launches, PhaseTimer *tm, const RoundConfig &cfg) {
+                          int64_t *launches, PhaseTimer *tm, const RoundConfig &cfg, int *wait_err) {
   if (n <= 0) return cudaSuccess;
   switch (dtype) {
-    case 0: return rounds_bk<OpI32>(cfg, D, ld, n, colT, ldT, s, launches, tm);
-    case 1: return rounds_bk<OpU16>(cfg, D, ld, n, colT, ldT, s, launches, tm);
-    case 2: return rounds_bk<OpF32>(cfg, D, ld, n, colT, ldT, s, launches, tm);
+    case 0: return rounds_bk<OpI32>(cfg, D, ld, n, colT, ldT, s, launches, tm, wait_err);
+    case 1: return rounds_bk<OpU16>(cfg, D, ld, n, colT, ldT, s, launches, tm, wait_err);
+    case 2: return rounds_bk<OpF32>(cfg, D, ld, n, colT, ldT, s, launches, tm, wait_err);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -21,15 +21,19 @@ struct PhaseTimer {
 // fall back to variant 0 otherwise.
 struct RoundConfig {
   int bk = 64;
-  int p3 = 1;
+  int p3 = 2;  // fastest on GB300 at n = 16384 (profiles/phase3_variants_gmm16k.md)
 };
 constexpr int64_t kMaxRoundWidth = 64;  // panel buffers are sized for this
 
 // q rounds of Phase 1 -> Phase 2 -> Phase 3 on D (n x n, leading dimension ld).
 // colT is a kMaxRoundWidth x ldT panel buffer of 32-bit words, ldT a multiple
 // of 256 and >= n.
+// wait_err: device word that the persistent Phase-3 kernel ORs 4 into when a
+// bounded wait gives up; nullptr = a per-device word the library allocates on
+// first use.
 cudaError_t launch_rounds(int dtype, void *D, int64_t ld, int64_t n, void *colT, int64_t ldT, cudaStream_t s,
-                          int64_t *launches, PhaseTimer *timer = nullptr, const RoundConfig &cfg = RoundConfig());
+                          int64_t *launches, PhaseTimer *timer = nullptr, const RoundConfig &cfg = RoundConfig(),
+                          int *wait_err = nullptr);
 // Copies W to D when they differ and checks the input (status |= 1 invalid, 2 range).
 cudaError_t launch_ingest(int dtype, const void *W, void *D, int64_t n, int64_t ld, int *status, cudaStream_t s,
                           int64_t *launches);
