@@ -229,6 +229,31 @@ apsp_status apsp_autotune(apsp_handle *h, int dtype, int64_t n_max, const char *
  * persistent TMA Phase 3). */
 apsp_status apsp_tuned_config(apsp_handle *h, int dtype, int64_t n, int *block_k, int *tma);
 
+/* ---- solve without allocation -------------------------------------------- */
+/* Largest n accepted by apsp_solve_i32_noalloc. */
+#define APSP_NOALLOC_MAX_N 16384
+
+/* An int32 solve (same result as apsp_solve_t with APSP_I32) that allocates
+ * no memory at all: no handle, no cudaMalloc, no allocating library call.
+ * The paper has no counterpart; this exists for callers that cannot allocate
+ * device memory where they solve -- code that runs inside another
+ * framework's memory pool or allocator hooks and must not allocate behind its
+ * back, or a latency-bound loop that cannot afford the device-wide
+ * synchronization an allocation may cause.  The caller passes W and D
+ * (device, n rows of ld elements, W == D allowed) and a stream (void*, NULL =
+ * legacy default stream); the call is asynchronous on it.
+ * Scratch memory: a fixed array in device global memory inside the library,
+ * sized for n <= APSP_NOALLOC_MAX_N (about 4 MiB), which every GPU that loads
+ * the library keeps until the process exits.  Every call shares that array:
+ * calls that overlap on the GPU (different streams, or different host
+ * threads) race on it and give wrong results -- order them on one stream.
+ * The first call on each device looks up the array's device address; make
+ * that first call before any stream capture.  Inputs are not checked on the
+ * device (use apsp_solve for checked solves).
+ * Errors: APSP_E_INVALID (n < 0, ld < n, null pointer), APSP_E_RANGE (n >
+ * APSP_NOALLOC_MAX_N), APSP_E_CUDA (a CUDA call failed). */
+apsp_status apsp_solve_i32_noalloc(const int32_t *W, int64_t n, int64_t ld, int32_t *D, void *stream);
+
 /* ---- diagnostics -------------------------------------------------------- */
 const char *apsp_strerror(apsp_status s);
 /* Text of the last failure on this handle (thread-local per handle); never NULL. */

@@ -66,6 +66,7 @@ def _load():
                                   ctypes.POINTER(vp), vp]),
         "apsp_check_bounded_wait": (st, [H, i64]),
         "apsp_autotune": (st, [H, i32, i64, ctypes.c_char_p]),
+        "apsp_solve_i32_noalloc": (st, [vp, i64, i64, vp, vp]),
         "apsp_tuned_config": (st, [H, i32, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "apsp_profile_read": (st, [H, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double)]),
@@ -93,4 +94,4 @@ ENTRY_POINTS = sorted(["apsp_config_default", "apsp_create", "apsp_destroy", "ap
                        "apsp_unpack_u16", "apsp_submit", "apsp_poll", "apsp_wait", "apsp_fetch", "apsp_release",
                        "apsp_cancel", "apsp_strerror", "apsp_last_error", "apsp_launch_count",
                        "apsp_profile", "apsp_profile_read", "apsp_solve_batch", "apsp_check_bounded_wait",
-                       "apsp_autotune", "apsp_tuned_config"])
+                       "apsp_autotune", "apsp_tuned_config", "apsp_solve_i32_noalloc"])
