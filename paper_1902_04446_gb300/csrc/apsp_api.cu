@@ -902,6 +902,9 @@ apsp_status apsp_profile_read(apsp_handle *h, int64_t launches[3], double ms[3],
 namespace {
 
 constexpr int kMaxGroupsInFlight = 16;
+// A request this large fills the GPU by itself: it gets its own group and
+// the per-round kernels (persistent TMA Phase 3) instead of the batched kernel.
+constexpr int64_t kLargeN = 1536;
 
 int64_t panel_bytes(int64_t n) { return 64 * apsp::batch_panel_ld(n) * 4 + 256; }
 
@@ -986,6 +989,21 @@ apsp_status admit_group(apsp_handle *h, const std::vector<Request *> &rs) {
     if (rn > 0 && apsp::launch_ingest(APSP_I32, rs[i]->D, rs[i]->D, rn, rn, g->status + i, s, &l) != cudaSuccess)
       return APSP_E_CUDA;
   }
+  if (rs.size() == 1 && rs[0]->req.n >= kLargeN) {
+    // one large graph: per-round kernels on the group's stream
+    const int64_t rn = rs[0]->req.n;
+    const int64_t ldT = panel_ld(rn);
+    if (cudaMallocAsync(&g->ws, (size_t)apsp::kMaxRoundWidth * ldT * 4, s) != cudaSuccess) return APSP_E_CUDA;
+    if (apsp::launch_rounds(APSP_I32, rs[0]->D, rn, rn, g->ws, ldT, s, &l, nullptr, config_for(h, APSP_I32, rn),
+                            g->status + 1) != cudaSuccess)
+      return APSP_E_CUDA;
+    h->launches += l;
+    if (cudaEventRecord(g->done_ev, s) != cudaSuccess) return APSP_E_CUDA;
+    g->graphs_dev = nullptr;
+    rs[0]->admitted = true;
+    h->groups.push_back(g);
+    return APSP_OK;
+  }
   // only graphs with n > 0 take part; group indices follow the tickets
   apsp::BatchPlan plan;
   std::vector<uint32_t *> colT(D.size(), nullptr);
@@ -1019,12 +1037,15 @@ void worker_loop(apsp_handle *h) {
       int64_t add = 0;
       while (!h->queue.empty() && (int)rs.size() < h->cfg.max_batch) {
         Request *r = h->reqs[h->queue.front()].get();
-        const int64_t b = r->bytes + panel_bytes(r->req.n);
+        const bool large = r->req.n >= kLargeN;
+        if (large && !rs.empty()) break;  // a large request starts its own group
+        const int64_t b = r->bytes + panel_bytes(r->req.n) + (large ? 64 * panel_ld(r->req.n) * 4 : 0);
         if (h->used + add + b > h->budget) break;  // wait for memory to free up
         h->queue.pop_front();
-        r->transient = panel_bytes(r->req.n);
+        r->transient = b - r->bytes;
         add += b;
         rs.push_back(r);
+        if (large) break;
       }
       if (!rs.empty()) {
         h->used += add;
