@@ -201,20 +201,33 @@ def timed_solves(torch, h, dtype, Wd, Dd, steps, warmup, dist=None, profile=Fals
     return ms, launches, prof
 
 
+def _reduce_device(dist):
+    # NCCL reduces CUDA tensors; gloo (CPU tests of the multi-rank logic) CPU tensors
+    return "cuda" if dist.get_backend() == "nccl" else "cpu"
+
+
 def max_over_ranks(torch, dist, x):
+    """Timing across ranks: the slowest rank's time."""
     if dist is None:
         return x
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_reduce_device(dist))
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
 
 def sum_over_ranks(torch, dist, x):
+    """Work across ranks: every rank solves its own replica, the job did the sum."""
     if dist is None:
         return x
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_reduce_device(dist))
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def job_value(torch, dist, relax_per_rank, ms_this_rank):
+    """Whole-job GRelax/s: all ranks' relaxations / the slowest rank's time."""
+    ms = max_over_ranks(torch, dist, ms_this_rank)
+    return sum_over_ranks(torch, dist, relax_per_rank) / (ms / 1e3) / 1e9, ms
 
 
 def sample_graph(workload: str, n_s: int):
@@ -368,9 +381,8 @@ def run_gpu(args):
     with ClockSampler(device) as clk:
         ms, launches, prof = timed_solves(torch, h, "int32", Wd, Dd, args.steps, args.warmup, dist, profile=True)
     clocks = clk.summary()
-    ms_max = max_over_ranks(torch, dist, ms)
     relax_step = float(n) ** 3
-    value = sum_over_ranks(torch, dist, relax_step * args.steps) / (ms_max / 1e3) / 1e9
+    value, ms_max = job_value(torch, dist, relax_step * args.steps, ms)
 
     # roofline of the dominant kernel (Phase 3), from the live event timings
     sms = props.multi_processor_count
