@@ -196,7 +196,11 @@ struct TileMap {
 template <class Op, int BM, int BNW, int BK, int TN = 8>
 __device__ __forceinline__ void tile_minplus(const uint32_t *__restrict__ As, const uint32_t *__restrict__ Bs,
                                              uint32_t (&acc)[8][TN], int ty, int tx) {
-#pragma unroll 4
+  // deeper unrolling for the 8 x 8 block (fewer loop instructions on the
+  // add-min pipe); the 8 x 4 block of the 512-thread kernel must stay within
+  // 128 registers
+  constexpr int UNROLL = TN == 8 ? 8 : 4;
+#pragma unroll UNROLL
   for (int t = 0; t < BK; ++t) {
     const uint4 a0 = *reinterpret_cast<const uint4 *>(As + t * BM + ty * 4);
     const uint4 a1 = *reinterpret_cast<const uint4 *>(As + t * BM + BM / 2 + ty * 4);
@@ -241,6 +245,22 @@ __device__ __forceinline__ void load_acc(const typename Op::elem *M, int64_t ld,
 // Stores the thread's block: row r is written when it lies in [0, nrows) and
 // outside [xr0, xr1); an element column when it lies in [0, ncols) and outside
 // [xc0, xc1).
+// Stores an interior tile (every element inside the matrix, none excluded)
+// with unconditional 16-byte stores; needs `vec`.
+template <class Op, int BM, int BNW, int TN = 8>
+__device__ __forceinline__ void store_acc_interior(typename Op::elem *M, int64_t ld, int64_t row0, int64_t col0,
+                                                   const uint32_t (&acc)[8][TN], int ty, int tx) {
+  using Map = TileMap<BM, BNW, TN>;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    typename Op::elem *rowp = M + (row0 + Map::row(ty, r)) * ld + col0;
+#pragma unroll
+    for (int h = 0; h < Map::NH; ++h)
+      *reinterpret_cast<uint4 *>(rowp + (int64_t)Map::wcol(tx, h) * Op::EPW) =
+          make_uint4(acc[r][4 * h + 0], acc[r][4 * h + 1], acc[r][4 * h + 2], acc[r][4 * h + 3]);
+  }
+}
+
 template <class Op, int BM, int BNW, int TN = 8>
 __device__ __forceinline__ void store_acc(typename Op::elem *M, int64_t ld, int64_t nrows, int64_t ncols,
                                           int64_t row0, int64_t col0, int64_t xr0, int64_t xr1, int64_t xc0,

@@ -158,20 +158,20 @@ __global__ void __launch_bounds__(TileMap<128, 128, TN>::THREADS, 1)
   }
   __syncthreads();
 
-  auto tile_row0 = [&](int t) { return (t / tiles_x) * BM; };
-  auto tile_col0 = [&](int t) { return (t % tiles_x) * BNW * Op::EPW; };
-  auto issue_ab = [&](int t, int s) {
+  // tile coordinates advance incrementally (row-major over the tile grid)
+  int cur_ty = t_begin / tiles_x, cur_tx = t_begin % tiles_x;
+  auto issue_ab = [&](int ty_, int tx_, int s) {
     mbar_arrive_expect_tx(&bar_ab[s], P3T_STAGE_BYTES);
-    tma_load_2d(stA(s), &mapA, &bar_ab[s], tile_row0(t), 0);
-    tma_load_2d(stB(s), &mapB, &bar_ab[s], tile_col0(t), (int)p0);
+    tma_load_2d(stA(s), &mapA, &bar_ab[s], ty_ * BM, 0);
+    tma_load_2d(stB(s), &mapB, &bar_ab[s], tx_ * BNW * Op::EPW, (int)p0);
   };
-  auto issue_c = [&](int t) {
+  auto issue_c = [&](int ty_, int tx_) {
     mbar_arrive_expect_tx(&bar_c, P3T_C_BYTES);
-    tma_load_2d(Cs, &mapC, &bar_c, tile_col0(t), tile_row0(t));
+    tma_load_2d(Cs, &mapC, &bar_c, tx_ * BNW * Op::EPW, ty_ * BM);
   };
   if (tid == 0) {
-    issue_ab(t_begin, 0);
-    issue_c(t_begin);
+    issue_ab(cur_ty, cur_tx, 0);
+    issue_c(cur_ty, cur_tx);
   }
   // parity of the next completion of bar_c (bit 0) and bar_ab[s] (bit 1 + s);
   // `pend` has the same bits set while a copy on that barrier is in flight
@@ -179,6 +179,8 @@ __global__ void __launch_bounds__(TileMap<128, 128, TN>::THREADS, 1)
   uint32_t acc[8][TN];
   for (int t = t_begin; t < t_end; ++t) {
     const int s = (t - t_begin) & 1;
+    const int nxt_tx = (cur_tx + 1 == tiles_x) ? 0 : cur_tx + 1;
+    const int nxt_ty = (cur_tx + 1 == tiles_x) ? cur_ty + 1 : cur_ty;
     if (!mbar_wait_bounded(&bar_c, par & 1u, P3T_WAIT_LIMIT)) abort_flag = 1;
     par ^= 1u;
     pend &= ~1u;
@@ -197,8 +199,8 @@ __global__ void __launch_bounds__(TileMap<128, 128, TN>::THREADS, 1)
     if (abort_flag) break;
     if (t + 1 < t_end) {
       if (tid == 0) {
-        issue_c(t + 1);
-        issue_ab(t + 1, s ^ 1);
+        issue_c(nxt_ty, nxt_tx);
+        issue_ab(nxt_ty, nxt_tx, s ^ 1);
       }
       pend |= 1u | (2u << (s ^ 1));
     }
@@ -209,7 +211,15 @@ __global__ void __launch_bounds__(TileMap<128, 128, TN>::THREADS, 1)
     __syncwarp();
     if (abort_flag) break;
     tile_minplus<Op, BM, BNW, BK, TN>(stA(s), stB(s), acc, ty, tx);
-    store_acc<Op, BM, BNW, TN>(D, ld, n, n, tile_row0(t), tile_col0(t), p0, p1, p0, p1, true, acc, ty, tx);
+    const int64_t r0 = (int64_t)cur_ty * BM, c0 = (int64_t)cur_tx * BNW * Op::EPW;
+    const bool interior = r0 + BM <= n && c0 + BNW * Op::EPW <= n && (r0 + BM <= p0 || r0 >= p1) &&
+                          (c0 + BNW * Op::EPW <= p0 || c0 >= p1);
+    if (interior)
+      store_acc_interior<Op, BM, BNW, TN>(D, ld, r0, c0, acc, ty, tx);
+    else
+      store_acc<Op, BM, BNW, TN>(D, ld, n, n, r0, c0, p0, p1, p0, p1, true, acc, ty, tx);
+    cur_tx = nxt_tx;
+    cur_ty = nxt_ty;
   }
   if (abort_flag && tid == 0) {
     // a wait gave up: wait (bounded) for this CTA's copies still in flight
