@@ -82,6 +82,12 @@ typedef struct {
   int64_t spin_limit;    /* bounded device waits: iterations before APSP_E_TIMEOUT (0 = default) */
   int phase3_variant;    /* Phase-3 kernel: 0 = tuned or default, 1 = one CTA per tile, 2 = persistent
                             TMA kernel with 256 threads, 3 = persistent TMA kernel with 512 threads */
+  int symmetric;         /* symmetric mode for undirected graphs (Sec. 3: A_ij = A_ji; the paper keeps
+                            only the upper triangle): Phase 3 updates only the tiles touching the upper
+                            triangle and the lower triangle is mirrored at the end -- same result, about
+                            half the relaxations.  0 = use it when a device check finds W symmetric
+                            (one stream synchronization per solve), 1 = the caller guarantees W is
+                            symmetric, 2 = never.  Edge-list solves are symmetric by construction. */
 } apsp_config;
 
 /* Fills *cfg with the defaults. */

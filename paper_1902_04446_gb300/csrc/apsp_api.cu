@@ -132,6 +132,8 @@ struct apsp_handle {
   size_t ws16_bytes = 0;
   void *wsb = nullptr;  // batched solve: plan + panel buffers
   size_t wsb_bytes = 0;
+  void *rowP = nullptr;  // symmetric mode, packed 16-bit: element panel
+  size_t rowP_bytes = 0;
   int *d_status = nullptr;
   int *h_status = nullptr;  // pinned
   std::string last_error;
@@ -227,7 +229,9 @@ apsp::RoundConfig config_for(apsp_handle *h, int dtype, int64_t n) {
 }
 
 // Enqueues the q rounds on D (already holding W) using the handle's panel buffer.
-apsp_status run_rounds_locked(apsp_handle *h, int dtype, void *D, int64_t n, int64_t ld, cudaStream_t s) {
+// known_sym: D is symmetric by construction (edge-list input).
+apsp_status run_rounds_locked(apsp_handle *h, int dtype, void *D, int64_t n, int64_t ld, cudaStream_t s,
+                              bool known_sym = false) {
   const int64_t bk = apsp::kMaxRoundWidth;
   const int64_t ldT = panel_ld(n);
   const size_t need = (size_t)bk * ldT * 4;  // panel buffer of 32-bit words
@@ -236,9 +240,33 @@ apsp_status run_rounds_locked(apsp_handle *h, int dtype, void *D, int64_t n, int
     h->last_error = std::string("panel workspace: ") + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? APSP_E_NOMEM : APSP_E_CUDA;
   }
+  apsp::RoundConfig rc = config_for(h, dtype, n);
+  if (h->cfg.symmetric == 1 || (h->cfg.symmetric == 0 && known_sym)) {
+    rc.sym = true;
+  } else if (h->cfg.symmetric == 0 && n > 1) {
+    // device check of W == W^T; the answer is read back before the rounds are enqueued
+    int *flag = h->d_status + 1;
+    e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = apsp::launch_symmetry_check(dtype, D, n, ld, flag, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_status + 1, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      h->last_error = std::string("symmetry check: ") + cudaGetErrorString(e);
+      return APSP_E_CUDA;
+    }
+    h->launches += 1;
+    rc.sym = h->h_status[1] == 0;
+  }
+  if (rc.sym && dtype == APSP_U16) {
+    e = ensure(&h->rowP, &h->rowP_bytes, (size_t)bk * ldT * 2);
+    if (e != cudaSuccess) {
+      h->last_error = std::string("panel workspace: ") + cudaGetErrorString(e);
+      return e == cudaErrorMemoryAllocation ? APSP_E_NOMEM : APSP_E_CUDA;
+    }
+    rc.rowP = h->rowP;
+  }
   int64_t l = 0;
-  e = apsp::launch_rounds(dtype, D, ld, n, h->colT, ldT, s, &l, h->prof.get(), config_for(h, dtype, n),
-                          h->d_status);
+  e = apsp::launch_rounds(dtype, D, ld, n, h->colT, ldT, s, &l, h->prof.get(), rc, h->d_status);
   h->launches += l;
   if (e != cudaSuccess) {
     h->last_error = std::string("rounds: ") + cudaGetErrorString(e);
@@ -294,7 +322,8 @@ apsp_status solve_locked(apsp_handle *h, int dtype, const void *W, int64_t n, in
         h->last_error = std::string("pack: ") + cudaGetErrorString(e);
         return APSP_E_CUDA;
       }
-      apsp_status st = run_rounds_locked(h, APSP_U16, P, n, ld16, s);
+      // the bound accepts only a symmetric W, so the packed copy is symmetric
+      apsp_status st = run_rounds_locked(h, APSP_U16, P, n, ld16, s, true);
       if (st != APSP_OK) return st;
       e = apsp::launch_unpack(P, ld16, static_cast<int32_t *>(D), ld, n, s, &l);
       h->launches += l;
@@ -342,6 +371,7 @@ apsp_status apsp_create(apsp_handle **out, const apsp_config *cfg) {
   if (c.dtype != APSP_AUTO && !valid_dtype(c.dtype)) return APSP_E_INVALID;
   if (c.block_k != 0 && c.block_k != 32 && c.block_k != 64) return APSP_E_INVALID;
   if (c.phase3_variant < 0 || c.phase3_variant > 3) return APSP_E_INVALID;
+  if (c.symmetric < 0 || c.symmetric > 2) return APSP_E_INVALID;
   if (c.max_batch <= 0) c.max_batch = 64;
   if (c.queue_depth <= 0) c.queue_depth = 4096;
   int ndev = 0;
@@ -387,6 +417,7 @@ apsp_status apsp_destroy(apsp_handle *h) {
   if (h->colT) cudaFree(h->colT);
   if (h->ws16) cudaFree(h->ws16);
   if (h->wsb) cudaFree(h->wsb);
+  if (h->rowP) cudaFree(h->rowP);
   if (h->d_status) cudaFree(h->d_status);
   if (h->h_status) cudaFreeHost(h->h_status);
   delete h;
@@ -453,7 +484,7 @@ apsp_status apsp_solve_edges(apsp_handle *h, int dtype, const int32_t *src, cons
         h->launches += l;
         l = 0;
         if (e != cudaSuccess) return cuda_fail(h, e, "densify/pack");
-        apsp_status st = run_rounds_locked(h, APSP_U16, P, n, ld16, s);
+        apsp_status st = run_rounds_locked(h, APSP_U16, P, n, ld16, s, true);
         if (st != APSP_OK) return st;
         e = apsp::launch_unpack(P, ld16, static_cast<int32_t *>(D), ld, n, s, &l);
         h->launches += l;
@@ -469,7 +500,7 @@ apsp_status apsp_solve_edges(apsp_handle *h, int dtype, const int32_t *src, cons
     h->last_error = std::string("densify: ") + cudaGetErrorString(e);
     return APSP_E_CUDA;
   }
-  return run_rounds_locked(h, solve_dtype, D, n, ld, s);
+  return run_rounds_locked(h, solve_dtype, D, n, ld, s, true);
 }
 
 apsp_status apsp_last_status(apsp_handle *h, void *stream) {

@@ -280,15 +280,30 @@ __device__ __forceinline__ void store_acc(typename Op::elem *M, int64_t ld, int6
   }
 }
 
+// The loaders below issue all of a thread's global loads before the first
+// shared-memory store (compile-time trip counts, fully unrolled in batches of
+// up to 8), so their latencies overlap instead of adding up.
+
 // As[t][i] = colT[t][i0 + i] for t < BK, i < BM (colT rows are aligned words).
 template <int BM, int BK, int NT, bool CG = false>
 __device__ __forceinline__ void load_As_colT(uint32_t *As, const uint32_t *__restrict__ colT, int64_t ldT, int64_t i0,
                                              int tid) {
   constexpr int CH = BK * BM / 4;
-  for (int c = tid; c < CH; c += NT) {
-    const int t = c / (BM / 4);
-    const int i = (c % (BM / 4)) * 4;
-    *reinterpret_cast<uint4 *>(As + t * BM + i) = ld16<CG>(colT + t * ldT + i0 + i);
+  static_assert(CH % NT == 0, "chunk count");
+  constexpr int IT = CH / NT, BATCH = IT < 8 ? IT : 8;
+#pragma unroll
+  for (int k0 = 0; k0 < IT; k0 += BATCH) {
+    uint4 v[BATCH];
+#pragma unroll
+    for (int k = 0; k < BATCH; ++k) {
+      const int c = tid + (k0 + k) * NT;
+      v[k] = ld16<CG>(colT + (c / (BM / 4)) * ldT + i0 + (c % (BM / 4)) * 4);
+    }
+#pragma unroll
+    for (int k = 0; k < BATCH; ++k) {
+      const int c = tid + (k0 + k) * NT;
+      *reinterpret_cast<uint4 *>(As + (c / (BM / 4)) * BM + (c % (BM / 4)) * 4) = v[k];
+    }
   }
 }
 
@@ -298,11 +313,22 @@ __device__ __forceinline__ void load_Bs_rows(uint32_t *Bs, const typename Op::el
                                              int64_t nrows, int64_t ncols, int64_t r0, int64_t c0, bool vec,
                                              int tid) {
   constexpr int CH = BK * BNW / 4;
-  for (int c = tid; c < CH; c += NT) {
-    const int t = c / (BNW / 4);
-    const int w = (c % (BNW / 4)) * 4;
-    const uint4 v = load_chunk<Op, CG>(M, ld, nrows, ncols, r0 + t, c0 + (int64_t)w * Op::EPW, vec);
-    *reinterpret_cast<uint4 *>(Bs + t * BNW + w) = v;
+  static_assert(CH % NT == 0, "chunk count");
+  constexpr int IT = CH / NT, BATCH = IT < 8 ? IT : 8;
+#pragma unroll
+  for (int k0 = 0; k0 < IT; k0 += BATCH) {
+    uint4 v[BATCH];
+#pragma unroll
+    for (int k = 0; k < BATCH; ++k) {
+      const int c = tid + (k0 + k) * NT;
+      v[k] = load_chunk<Op, CG>(M, ld, nrows, ncols, r0 + c / (BNW / 4), c0 + (int64_t)((c % (BNW / 4)) * 4) * Op::EPW,
+                                vec);
+    }
+#pragma unroll
+    for (int k = 0; k < BATCH; ++k) {
+      const int c = tid + (k0 + k) * NT;
+      *reinterpret_cast<uint4 *>(Bs + (c / (BNW / 4)) * BNW + (c % (BNW / 4)) * 4) = v[k];
+    }
   }
 }
 
@@ -315,13 +341,23 @@ __device__ __forceinline__ void load_As_transposed(uint32_t *As, const typename 
                                                    int tid) {
   constexpr int E = 4 * Op::EPW;
   constexpr int CH = BM * (BK / E);
-  for (int c = tid; c < CH; c += NT) {
-    const int i = c % BM;
-    const int tq = (c / BM) * E;
-    const uint4 v = load_chunk<Op, CG>(M, ld, nrows, ncols, i0 + i, c0 + tq, vec);
+  static_assert(CH % NT == 0, "chunk count");
+  constexpr int IT = CH / NT, BATCH = IT < 8 ? IT : 8;
 #pragma unroll
-    for (int e = 0; e < E; ++e)
-      As[(tq + e) * BM + i] = Op::dup(bits_elem<Op>(chunk_get<Op>(v, e)));
+  for (int k0 = 0; k0 < IT; k0 += BATCH) {
+    uint4 v[BATCH];
+#pragma unroll
+    for (int k = 0; k < BATCH; ++k) {
+      const int c = tid + (k0 + k) * NT;
+      v[k] = load_chunk<Op, CG>(M, ld, nrows, ncols, i0 + c % BM, c0 + (c / BM) * E, vec);
+    }
+#pragma unroll
+    for (int k = 0; k < BATCH; ++k) {
+      const int c = tid + (k0 + k) * NT;
+      const int i = c % BM, tq = (c / BM) * E;
+#pragma unroll
+      for (int e = 0; e < E; ++e) As[(tq + e) * BM + i] = Op::dup(bits_elem<Op>(chunk_get<Op>(v[k], e)));
+    }
   }
 }
 

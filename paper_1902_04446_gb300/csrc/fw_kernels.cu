@@ -65,20 +65,75 @@ struct P2Cfg {
   static constexpr int SMEM = ROW_SMEM > COL_SMEM ? ROW_SMEM : COL_SMEM;
 };
 
+// The first nrow_ctas CTAs take row-panel chunks row_chunk0, row_chunk0 + 1,
+// ...; the rest take column-panel chunks 0, 1, ....  sym != 0: symmetric
+// mode (see p2_row_task / p2_col_task).
 template <class Op, int BK>
-__global__ void __launch_bounds__(P2Cfg<Op, BK>::THREADS) fw_phase2(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
-                                                 int64_t p1, uint32_t *__restrict__ colT, int64_t ldT, int nrow_ctas,
-                                                 int vec) {
+__global__ void __launch_bounds__(P2Cfg<Op, BK>::THREADS)
+    fw_phase2(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0, int64_t p1,
+              uint32_t *__restrict__ colT, int64_t ldT, int nrow_ctas, int vec, int row_chunk0, int sym,
+              SymPanel<Op> sp) {
   using C = P2Cfg<Op, BK>;
   extern __shared__ __align__(16) uint32_t smem[];
+  const SymPanel<Op> *spp = sym ? &sp : nullptr;
   if ((int)blockIdx.x < nrow_ctas)
-    p2_row_task<Op, BK, C::ROW_BNW, C::THREADS, false>(D, ld, n, p0, p1, colT, ldT,
-                                                       (int64_t)blockIdx.x * C::ROW_BNW * Op::EPW, vec, smem,
-                                                       threadIdx.x);
+    p2_row_task<Op, BK, C::ROW_BNW, C::THREADS, false>(
+        D, ld, n, p0, p1, colT, ldT, (int64_t)(row_chunk0 + (int)blockIdx.x) * C::ROW_BNW * Op::EPW, vec, smem,
+        threadIdx.x, spp);
   else
     p2_col_task<Op, BK, C::COL_BM, C::THREADS, false>(D, ld, n, p0, p1, colT, ldT,
                                                       (int64_t)(blockIdx.x - nrow_ctas) * C::COL_BM, vec, smem,
-                                                      threadIdx.x);
+                                                      threadIdx.x, spp);
+}
+
+// Phase 1 kernel with the optional element panel (symmetric mode).
+template <class Op, int BK>
+__global__ void __launch_bounds__(P1_THREADS) fw_phase1_sym(typename Op::elem *__restrict__ D, int64_t ld, int64_t n,
+                                                            int64_t p0, uint32_t *__restrict__ colT, int64_t ldT,
+                                                            typename Op::elem *rowP) {
+  __shared__ P1Smem<Op, BK> s;
+  phase1_body<Op, BK, P1_THREADS, false>(D, ld, n, p0, colT, ldT, s, threadIdx.x, rowP);
+}
+
+// ---------------------------------------------------------------- symmetry
+// D[r][c] = D[c][r] for every r > c (the lower triangle from the upper), by
+// 32 x 32 blocks through shared memory; block (R, C) with R >= C.
+template <class Op>
+__global__ void mirror_kernel(typename Op::elem *__restrict__ D, int64_t n, int64_t ld) {
+  __shared__ typename Op::elem tile[32][33];
+  const int64_t R = blockIdx.y, Cb = blockIdx.x;
+  if (R < Cb) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  // read block (Cb, R) of the upper triangle: rows Cb*32.., columns R*32..
+  for (int k = ty; k < 32; k += 8) {
+    const int64_t r = Cb * 32 + k, c = R * 32 + tx;
+    if (r < n && c < n) tile[k][tx] = D[r * ld + c];
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    const int64_t r = R * 32 + k, c = Cb * 32 + tx;  // target (r, c) = source (c, r)
+    if (r < n && c < n && r > c) D[r * ld + c] = tile[tx][k];
+  }
+}
+
+// flag |= 1 when some D[r][c] != D[c][r] (compared bitwise), same blocking.
+template <class Op>
+__global__ void symmetry_check_kernel(const typename Op::elem *__restrict__ D, int64_t n, int64_t ld, int *flag) {
+  __shared__ typename Op::elem tile[32][33];
+  const int64_t R = blockIdx.y, Cb = blockIdx.x;
+  if (R < Cb) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int k = ty; k < 32; k += 8) {
+    const int64_t r = Cb * 32 + k, c = R * 32 + tx;
+    if (r < n && c < n) tile[k][tx] = D[r * ld + c];
+  }
+  __syncthreads();
+  int bad = 0;
+  for (int k = ty; k < 32; k += 8) {
+    const int64_t r = R * 32 + k, c = Cb * 32 + tx;
+    if (r < n && c < n && elem_bits<Op>(D[r * ld + c]) != elem_bits<Op>(tile[tx][k])) bad = 1;
+  }
+  if (__syncthreads_or(bad) && tx == 0 && ty == 0) atomicOr(flag, 1);
 }
 
 // ---------------------------------------------------------------- Phase 3
@@ -91,10 +146,12 @@ struct P3Cfg {
 template <class Op, int BK>
 __global__ void __launch_bounds__(256, 2) fw_phase3(typename Op::elem *__restrict__ D, int64_t ld, int64_t n,
                                                     int64_t p0, int64_t p1, const uint32_t *__restrict__ colT,
-                                                    int64_t ldT, int vec) {
+                                                    int64_t ldT, int vec, const typename Op::elem *symB) {
   extern __shared__ __align__(16) uint32_t smem[];
+  // symmetric mode (symB != nullptr): tiles below the band are skipped and B is the panel
+  if (symB && (int)blockIdx.x < (int)blockIdx.y / Op::EPW) return;
   p3_task<Op, BK, false>(D, ld, n, p0, p1, colT, ldT, (int64_t)blockIdx.y * P3Cfg<Op>::BM,
-                         (int64_t)blockIdx.x * P3Cfg<Op>::BNW * Op::EPW, vec, smem, threadIdx.x);
+                         (int64_t)blockIdx.x * P3Cfg<Op>::BNW * Op::EPW, vec, smem, threadIdx.x, symB);
 }
 
 // ---------------------------------------------------------------- Phase 3, persistent + TMA
@@ -121,11 +178,27 @@ struct P3T {
 
 // TN = 8: 256 threads with 8 x 8 words each; TN = 4: 512 threads with 8 x 4
 // words each (twice the warps per SM to hide instruction latency).
+// Symmetric mode (sym = 1): only tiles (ty, tx) with tx >= ty / EPW -- the
+// tiles that touch the upper triangle -- are processed, in row-major order,
+// and B comes from the symmetric panel (mapB over the panel buffer) instead of
+// D's row panel.  Number of processed tiles before tile row ty:
+// ty * tiles_x - sum_{y < ty} floor(y / EPW).
+__device__ __forceinline__ long long sym_prefix(int ty, int tiles_x, int epw) {
+  long long f;
+  if (epw == 1) {
+    f = (long long)ty * (ty - 1) / 2;
+  } else {
+    const long long a = ty / 2;
+    f = (ty % 2 == 0) ? a * (a - 1) : a * a;
+  }
+  return (long long)ty * tiles_x - f;
+}
+
 template <class Op, int BK, int TN>
 __global__ void __launch_bounds__(TileMap<128, 128, TN>::THREADS, 1)
     fw_phase3_tma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                   const __grid_constant__ CUtensorMap mapC, typename Op::elem *__restrict__ D, int64_t ld, int64_t n,
-                  int64_t p0, int64_t p1, int tiles_x, int tiles_total, int *err) {
+                  int64_t p0, int64_t p1, int tiles_x, int tiles_total, int *err, int sym, int tiles_y) {
   constexpr int BM = 128, BNW = 128;
   constexpr int P3T_STAGE_BYTES = P3T<BK>::STAGE_BYTES;
   using Map = TileMap<BM, BNW, TN>;
@@ -159,11 +232,24 @@ __global__ void __launch_bounds__(TileMap<128, 128, TN>::THREADS, 1)
   __syncthreads();
 
   // tile coordinates advance incrementally (row-major over the tile grid)
-  int cur_ty = t_begin / tiles_x, cur_tx = t_begin % tiles_x;
+  int cur_ty, cur_tx;
+  if (!sym) {
+    cur_ty = t_begin / tiles_x;
+    cur_tx = t_begin % tiles_x;
+  } else {
+    int lo = 0, hi = tiles_y - 1;  // last tile row whose prefix <= t_begin
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (sym_prefix(mid, tiles_x, Op::EPW) <= t_begin) lo = mid;
+      else hi = mid - 1;
+    }
+    cur_ty = lo;
+    cur_tx = lo / Op::EPW + (int)(t_begin - sym_prefix(lo, tiles_x, Op::EPW));
+  }
   auto issue_ab = [&](int ty_, int tx_, int s) {
     mbar_arrive_expect_tx(&bar_ab[s], P3T_STAGE_BYTES);
     tma_load_2d(stA(s), &mapA, &bar_ab[s], ty_ * BM, 0);
-    tma_load_2d(stB(s), &mapB, &bar_ab[s], tx_ * BNW * Op::EPW, (int)p0);
+    tma_load_2d(stB(s), &mapB, &bar_ab[s], tx_ * BNW * Op::EPW, sym ? 0 : (int)p0);
   };
   auto issue_c = [&](int ty_, int tx_) {
     mbar_arrive_expect_tx(&bar_c, P3T_C_BYTES);
@@ -179,8 +265,8 @@ __global__ void __launch_bounds__(TileMap<128, 128, TN>::THREADS, 1)
   uint32_t acc[8][TN];
   for (int t = t_begin; t < t_end; ++t) {
     const int s = (t - t_begin) & 1;
-    const int nxt_tx = (cur_tx + 1 == tiles_x) ? 0 : cur_tx + 1;
     const int nxt_ty = (cur_tx + 1 == tiles_x) ? cur_ty + 1 : cur_ty;
+    const int nxt_tx = (cur_tx + 1 == tiles_x) ? (sym ? nxt_ty / Op::EPW : 0) : cur_tx + 1;
     if (!mbar_wait_bounded(&bar_c, par & 1u, P3T_WAIT_LIMIT)) abort_flag = 1;
     par ^= 1u;
     pend &= ~1u;
@@ -441,8 +527,15 @@ static inline unsigned grid_cols(int64_t n, int threads) {
 
 template <class Op, int BK>
 static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int64_t ldT, bool vec, int variant,
-                               cudaStream_t s, int64_t *launches, PhaseTimer *tm, int *wait_err) {
+                               cudaStream_t s, int64_t *launches, PhaseTimer *tm, int *wait_err, bool sym,
+                               void *rowPv) {
   const bool use_tma = variant != 0;
+  using Elem = typename Op::elem;
+  // symmetric mode: the element panel (B operand of Phase 3) is colT itself
+  // for 32-bit elements, a separate BK x ldT buffer for packed 16-bit
+  Elem *rowP = sym ? (Op::EPW == 2 ? static_cast<Elem *>(rowPv) : nullptr) : nullptr;
+  const Elem *symB = sym ? (Op::EPW == 2 ? rowP : reinterpret_cast<const Elem *>(colTv)) : nullptr;
+  if (sym && Op::EPW == 2 && !rowP) return cudaErrorInvalidValue;
   using E = typename Op::elem;
   E *D = static_cast<E *>(Dv);
   uint32_t *colT = static_cast<uint32_t *>(colTv);
@@ -465,7 +558,8 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
                                                         : CU_TENSOR_MAP_DATA_TYPE_INT32;
     tma = make_map(&mA, CU_TENSOR_MAP_DATA_TYPE_UINT32, colT, (uint64_t)ldT, (uint64_t)BK, (uint64_t)ldT * 4, 128,
                    BK) &&
-          make_map(&mB, dt, D, (uint64_t)n, (uint64_t)n, (uint64_t)ld * sizeof(E), 128 * Op::EPW, BK) &&
+          (sym ? make_map(&mB, dt, symB, (uint64_t)ldT, (uint64_t)BK, (uint64_t)ldT * sizeof(E), 128 * Op::EPW, BK)
+               : make_map(&mB, dt, D, (uint64_t)n, (uint64_t)n, (uint64_t)ld * sizeof(E), 128 * Op::EPW, BK)) &&
           make_map(&mC, dt, D, (uint64_t)n, (uint64_t)n, (uint64_t)ld * sizeof(E), 128 * Op::EPW, 128);
     err = tma ? (wait_err ? wait_err : error_word()) : nullptr;
     tma = tma && err != nullptr;
@@ -478,7 +572,12 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
     }
   }
   const int tiles_x = (int)((n + 128 * Op::EPW - 1) / (128 * Op::EPW));
-  const int tiles_total = tiles_x * (int)((n + 127) / 128);
+  const int tiles_y = (int)((n + 127) / 128);
+  int tiles_total = tiles_x * tiles_y;
+  if (sym) {  // tiles with tx >= ty / EPW
+    tiles_total = 0;
+    for (int y = 0; y < tiles_y; ++y) tiles_total += tiles_x - std::min(tiles_x, y / Op::EPW);
+  }
   const int grid_tma = std::min(sm_count(), tiles_total);
   const int64_t q = (n + BK - 1) / BK;
   const int nrow = (int)((n + C2::ROW_BNW * Op::EPW - 1) / (C2::ROW_BNW * Op::EPW));
@@ -489,24 +588,43 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
     const int64_t p1 = (p0 + BK < n) ? p0 + BK : n;
     const double w = (double)(p1 - p0), rest = (double)(n - (p1 - p0));
     if (tm) tm->before(0, s);
-    fw_phase1<Op, BK><<<1, P1_THREADS, 0, s>>>(D, ld, n, p0, colT, ldT);
+    if (sym && rowP)
+      fw_phase1_sym<Op, BK><<<1, P1_THREADS, 0, s>>>(D, ld, n, p0, colT, ldT, rowP);
+    else
+      fw_phase1<Op, BK><<<1, P1_THREADS, 0, s>>>(D, ld, n, p0, colT, ldT);
     if (tm) tm->after(0, s, w * w * w);
     if (q > 1) {
       if (tm) tm->before(1, s);
-      fw_phase2<Op, BK><<<nrow + ncol, C2::THREADS, C2::SMEM, s>>>(D, ld, n, p0, p1, colT, ldT, nrow, vec ? 1 : 0);
-      if (tm) tm->after(1, s, 2.0 * rest * w * w);
+      SymPanel<Op> sp{rowP, (p0 / (128 * Op::EPW)) * (128 * Op::EPW) + 128 * Op::EPW};
+      int r_first = 0, r_count = nrow, c_count = ncol;
+      if (sym) {  // row chunks that reach columns >= p1; column chunks with rows < p0
+        r_first = (int)(p1 / (C2::ROW_BNW * Op::EPW));
+        r_count = std::max(0, nrow - r_first);
+        c_count = (int)((p0 + C2::COL_BM - 1) / C2::COL_BM);
+      }
+      if (r_count + c_count > 0)
+        fw_phase2<Op, BK><<<r_count + c_count, C2::THREADS, C2::SMEM, s>>>(D, ld, n, p0, p1, colT, ldT, r_count,
+                                                                          vec ? 1 : 0, r_first, sym ? 1 : 0, sp);
+      if (tm) tm->after(1, s, sym ? rest * w * w : 2.0 * rest * w * w);
       if (tm) tm->before(2, s);
       if (tma && variant == 2)
         fw_phase3_tma<Op, BK, 4><<<grid_tma, TileMap<128, 128, 4>::THREADS, P3T<BK>::SMEM, s>>>(
-            mA, mB, mC, D, ld, n, p0, p1, tiles_x, tiles_total, err);
+            mA, mB, mC, D, ld, n, p0, p1, tiles_x, tiles_total, err, sym ? 1 : 0, tiles_y);
       else if (tma)
         fw_phase3_tma<Op, BK, 8><<<grid_tma, TileMap<128, 128, 8>::THREADS, P3T<BK>::SMEM, s>>>(
-            mA, mB, mC, D, ld, n, p0, p1, tiles_x, tiles_total, err);
+            mA, mB, mC, D, ld, n, p0, p1, tiles_x, tiles_total, err, sym ? 1 : 0, tiles_y);
       else
-        fw_phase3<Op, BK><<<g3, C3::THREADS, SMEM3, s>>>(D, ld, n, p0, p1, colT, ldT, vec ? 1 : 0);
-      if (tm) tm->after(2, s, rest * rest * w);
+        fw_phase3<Op, BK><<<g3, C3::THREADS, SMEM3, s>>>(D, ld, n, p0, p1, colT, ldT, vec ? 1 : 0, symB);
+      // relaxations actually performed: the processed tiles' share of (n - w)^2 w
+      const double frac = sym ? (double)tiles_total / ((double)tiles_x * tiles_y) : 1.0;
+      if (tm) tm->after(2, s, rest * rest * w * frac);
     }
     if (launches) *launches += (q > 1) ? 3 : 1;
+  }
+  if (sym && q > 1) {  // the lower triangle from the upper
+    const dim3 gm((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
+    mirror_kernel<Op><<<gm, dim3(32, 8), 0, s>>>(D, n, ld);
+    if (launches) *launches += 1;
   }
   return cudaGetLastError();
 }
@@ -519,9 +637,23 @@ template <class Op>
 static cudaError_t rounds_bk(const RoundConfig &cfg, void *D, int64_t ld, int64_t n, void *colT, int64_t ldT,
                              cudaStream_t s, int64_t *launches, PhaseTimer *tm, int *wait_err) {
   const bool vec = aligned16(D, ld, sizeof(typename Op::elem));
-  if (cfg.bk == 32) return rounds_impl<Op, 32>(D, ld, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err);
-  if (cfg.bk == 64) return rounds_impl<Op, 64>(D, ld, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err);
+  if (cfg.bk == 32)
+    return rounds_impl<Op, 32>(D, ld, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err, cfg.sym, cfg.rowP);
+  if (cfg.bk == 64)
+    return rounds_impl<Op, 64>(D, ld, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err, cfg.sym, cfg.rowP);
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_symmetry_check(int dtype, const void *D, int64_t n, int64_t ld, int *flag, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const dim3 g((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
+  switch (dtype) {
+    case 0: symmetry_check_kernel<OpI32><<<g, dim3(32, 8), 0, s>>>(static_cast<const int32_t *>(D), n, ld, flag); break;
+    case 1: symmetry_check_kernel<OpU16><<<g, dim3(32, 8), 0, s>>>(static_cast<const uint16_t *>(D), n, ld, flag); break;
+    case 2: symmetry_check_kernel<OpF32><<<g, dim3(32, 8), 0, s>>>(static_cast<const float *>(D), n, ld, flag); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_rounds(int dtype, void *D, int64_t ld, int64_t n, void *colT, int64_t ldT, cudaStream_t s,

@@ -19,10 +19,19 @@ struct PhaseTimer {
 // threads (8 x 8 words each), 2 = persistent TMA kernel with 512 threads
 // (8 x 4 words each).  The TMA variants need a 16-byte addressable matrix and
 // fall back to variant 0 otherwise.
+// sym: symmetric mode for undirected (symmetric) inputs -- Phase 3 updates
+// only the tiles that touch the upper triangle, both of its operands come from
+// one symmetric panel, and a final pass mirrors the upper triangle into the
+// lower; rowP is the BK x ldT element panel that packed 16-bit needs for it.
 struct RoundConfig {
   int bk = 64;
   int p3 = 2;  // fastest on GB300 at n = 16384 (profiles/phase3_variants_gmm16k.md)
+  bool sym = false;
+  void *rowP = nullptr;
 };
+
+// flag |= 1 when D (n x n, leading dimension ld) is not symmetric.
+cudaError_t launch_symmetry_check(int dtype, const void *D, int64_t n, int64_t ld, int *flag, cudaStream_t s);
 constexpr int64_t kMaxRoundWidth = 64;  // panel buffers are sized for this
 
 // q rounds of Phase 1 -> Phase 2 -> Phase 3 on D (n x n, leading dimension ld).

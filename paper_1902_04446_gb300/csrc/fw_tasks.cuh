@@ -34,7 +34,8 @@ struct P1Smem {
 
 template <class Op, int BK, int NT, bool CG>
 __device__ __forceinline__ void phase1_body(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
-                                            uint32_t *__restrict__ colT, int64_t ldT, P1Smem<Op, BK> &sm, int tid) {
+                                            uint32_t *__restrict__ colT, int64_t ldT, P1Smem<Op, BK> &sm, int tid,
+                                            typename Op::elem *__restrict__ rowP = nullptr) {
   using S = typename Op::scalar;
   constexpr int G = 16;
   constexpr int PT = BK / G;
@@ -42,10 +43,21 @@ __device__ __forceinline__ void phase1_body(typename Op::elem *__restrict__ D, i
   auto &s = sm.s;
   const int by = tid / G, bx = tid % G;
   const S INF = Op::to_s(Op::inf_elem());
-  for (int idx = tid; idx < BK * BK; idx += NT) {
-    const int i = idx / BK, j = idx % BK;
-    const int64_t r = p0 + i, c = p0 + j;
-    s[i][j] = (r < n && c < n) ? Op::to_s(ld_elem<CG>(D + r * ld + c)) : INF;
+  {
+    // all of this thread's loads first, then the shared-memory stores
+    constexpr int IT = BK * BK / NT;
+    S tmp[IT];
+#pragma unroll
+    for (int k = 0; k < IT; ++k) {
+      const int idx = tid + k * NT;
+      const int64_t r = p0 + idx / BK, c = p0 + idx % BK;
+      tmp[k] = (r < n && c < n) ? Op::to_s(ld_elem<CG>(D + r * ld + c)) : INF;
+    }
+#pragma unroll
+    for (int k = 0; k < IT; ++k) {
+      const int idx = tid + k * NT;
+      s[idx / BK][idx % BK] = tmp[k];
+    }
   }
   __syncthreads();
   S v[PT][PT];
@@ -103,15 +115,33 @@ __device__ __forceinline__ void phase1_body(typename Op::elem *__restrict__ D, i
     const int t = idx / BK, i = idx % BK;
     colT[t * ldT + p0 + i] = Op::dup(Op::from_s(s[i][t]));
   }
+  if (rowP) {  // symmetric mode: the panel as elements (row t = D[p0 + t][.])
+    for (int idx = tid; idx < BK * BK; idx += NT) {
+      const int t = idx / BK, j = idx % BK;
+      rowP[t * ldT + p0 + j] = Op::from_s(s[t][j]);
+    }
+  }
 }
 
 // ---------------------------------------------------------------- Phase 2
 // Row panel chunk: output rows [p0, p0+BK), words [col0/EPW, col0/EPW + BNW).
 // A = D_kk (from colT), B = C = the chunk itself.  Shared memory: BK*BK + BK*BNW words.
+//
+// Symmetric mode (sym != nullptr, undirected input): only columns >= p1 are
+// updated (the upper triangle); the results also go to the symmetric panel
+// (colT words, and sym->rowP elements for packed 16-bit) and, for columns
+// below sym->band_end, to the lower-triangle column-panel element D[x][p0+t]
+// (those lie in diagonal-band Phase-3 tiles, which are updated in full).
+template <class Op>
+struct SymPanel {
+  typename Op::elem *rowP;  // BK x ldT elements (packed 16-bit only; nullptr otherwise)
+  int64_t band_end;         // end of the Phase-3 tile column band that holds the diagonal block
+};
+
 template <class Op, int BK, int BNW, int NT, bool CG>
 __device__ __forceinline__ void p2_row_task(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
-                                            int64_t p1, const uint32_t *__restrict__ colT, int64_t ldT, int64_t col0,
-                                            bool vec, uint32_t *smem, int tid) {
+                                            int64_t p1, uint32_t *__restrict__ colT, int64_t ldT, int64_t col0,
+                                            bool vec, uint32_t *smem, int tid, const SymPanel<Op> *sym = nullptr) {
   using Map = TileMap<BK, BNW>;
   static_assert(Map::THREADS == NT, "row tile");
   uint32_t *As = smem;
@@ -123,15 +153,40 @@ __device__ __forceinline__ void p2_row_task(typename Op::elem *__restrict__ D, i
   load_acc<Op, BK, BNW, CG>(D, ld, n, n, p0, col0, vec, acc, ty, tx);
   __syncthreads();
   tile_minplus<Op, BK, BNW, BK>(As, Bs, acc, ty, tx);
-  store_acc<Op, BK, BNW>(D, ld, n, n, p0, col0, 0, 0, p0, p1, vec, acc, ty, tx);
+  if (!sym) {
+    store_acc<Op, BK, BNW>(D, ld, n, n, p0, col0, 0, 0, p0, p1, vec, acc, ty, tx);
+    return;
+  }
+  store_acc<Op, BK, BNW>(D, ld, n, n, p0, col0, 0, 0, 0, p1, vec, acc, ty, tx);
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int t = Map::row(ty, r);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+      for (int cw = 0; cw < 4; ++cw) {
+        const uint32_t word = acc[r][4 * h + cw];
+#pragma unroll
+        for (int lane = 0; lane < Op::EPW; ++lane) {
+          const int64_t x = col0 + (int64_t)(Map::wcol(tx, h) + cw) * Op::EPW + lane;
+          if (x < p1 || x >= n) continue;
+          const typename Op::elem e = bits_elem<Op>(Op::EPW == 2 ? (lane ? (word >> 16) : (word & 0xFFFFu)) : word);
+          colT[(int64_t)t * ldT + x] = Op::dup(e);
+          if (sym->rowP) sym->rowP[(int64_t)t * ldT + x] = e;
+          if (x < sym->band_end && p0 + t < n) D[x * ld + p0 + t] = e;
+        }
+      }
+    }
+  }
 }
 
-// Column panel chunk: output rows [row0, row0+BM), element columns [p0, p0+BK).
-// A = C = the chunk (transposed load), B = D_kk.  Shared memory: BK*BM + BK*(BK/EPW) words.
+// Symmetric mode: only rows < p0 are updated (the upper triangle); the
+// results also go to the row panel's lower-triangle elements D[p0+t][x] and,
+// for packed 16-bit, to sym->rowP.
 template <class Op, int BK, int BM, int NT, bool CG>
 __device__ __forceinline__ void p2_col_task(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
                                             int64_t p1, uint32_t *__restrict__ colT, int64_t ldT, int64_t row0,
-                                            bool vec, uint32_t *smem, int tid) {
+                                            bool vec, uint32_t *smem, int tid, const SymPanel<Op> *sym = nullptr) {
   constexpr int BNW = BK / Op::EPW;
   using Map = TileMap<BM, BNW>;
   static_assert(Map::THREADS == NT, "col tile");
@@ -144,7 +199,9 @@ __device__ __forceinline__ void p2_col_task(typename Op::elem *__restrict__ D, i
   load_acc<Op, BM, BNW, CG>(D, ld, n, n, row0, p0, vec, acc, ty, tx);
   __syncthreads();
   tile_minplus<Op, BM, BNW, BK>(As, Bs, acc, ty, tx);
-  store_acc<Op, BM, BNW>(D, ld, n, n, row0, p0, p0, p1, 0, 0, vec, acc, ty, tx);
+  // symmetric mode stores rows < p0 only
+  const int64_t xr1 = sym ? INT64_MAX : p1;
+  store_acc<Op, BM, BNW>(D, ld, n, n, row0, p0, p0, xr1, 0, 0, vec, acc, ty, tx);
   // transposed copy: colT[t][row0 + i] = word(D_Ik[i][t]) for rows outside [p0, p1)
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
@@ -152,7 +209,7 @@ __device__ __forceinline__ void p2_col_task(typename Op::elem *__restrict__ D, i
     for (int g = 0; g < 2; ++g) {
       const int ib = Map::row(ty, 4 * g);  // 4 consecutive rows ib .. ib+3
       const int64_t rb = row0 + ib;
-      const bool all_out = (rb + 3 < p0) || (rb >= p1);
+      const bool all_out = (rb + 3 < p0) || (rb >= xr1);
 #pragma unroll
       for (int cw = 0; cw < 4; ++cw) {
         const int w = Map::wcol(tx, h) + cw;
@@ -171,7 +228,19 @@ __device__ __forceinline__ void p2_col_task(typename Op::elem *__restrict__ D, i
           } else {
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-              if (rb + q < p0 || rb + q >= p1) dst[q] = q4[q];
+              if (rb + q < p0 || rb + q >= xr1) dst[q] = q4[q];
+          }
+          if (sym && p0 + t < n) {
+            // row panel's lower part D[p0+t][x] = D[x][p0+t], and the element panel
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int64_t x = rb + q;
+              if (x >= p0 || x >= n) continue;
+              const typename Op::elem e =
+                  bits_elem<Op>(Op::EPW == 2 ? (q4[q] & 0xFFFFu) : q4[q]);
+              D[(p0 + t) * ld + x] = e;
+              if (sym->rowP) sym->rowP[(int64_t)t * ldT + x] = e;
+            }
           }
         }
       }
@@ -182,10 +251,13 @@ __device__ __forceinline__ void p2_col_task(typename Op::elem *__restrict__ D, i
 // ---------------------------------------------------------------- Phase 3 (one tile)
 // Output tile rows [row0, row0+128), words [col0/EPW, +128); 256 threads;
 // shared memory 2 * BK * 128 words.
+// symB (nullable): symmetric mode, B rows come from this BK x ldT panel of
+// elements instead of D's row panel.
 template <class Op, int BK, bool CG>
 __device__ __forceinline__ void p3_task(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
                                         int64_t p1, const uint32_t *__restrict__ colT, int64_t ldT, int64_t row0,
-                                        int64_t col0, bool vec, uint32_t *smem, int tid) {
+                                        int64_t col0, bool vec, uint32_t *smem, int tid,
+                                        const typename Op::elem *symB = nullptr) {
   constexpr int BM = 128, BNW = 128, NT = 256;
   using Map = TileMap<BM, BNW>;
   uint32_t *As = smem;
@@ -193,7 +265,10 @@ __device__ __forceinline__ void p3_task(typename Op::elem *__restrict__ D, int64
   const int tx = tid % Map::TX, ty = tid / Map::TX;
   uint32_t acc[8][8];
   load_As_colT<BM, BK, NT, CG>(As, colT, ldT, row0, tid);
-  load_Bs_rows<Op, BNW, BK, NT, CG>(Bs, D, ld, n, n, p0, col0, vec, tid);
+  if (symB)
+    load_Bs_rows<Op, BNW, BK, NT, CG>(Bs, symB, ldT, BK, ldT, 0, col0, true, tid);
+  else
+    load_Bs_rows<Op, BNW, BK, NT, CG>(Bs, D, ld, n, n, p0, col0, vec, tid);
   load_acc<Op, BM, BNW, CG>(D, ld, n, n, row0, col0, vec, acc, ty, tx);
   __syncthreads();
   tile_minplus<Op, BM, BNW, BK>(As, Bs, acc, ty, tx);

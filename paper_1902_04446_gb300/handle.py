@@ -58,7 +58,8 @@ class Handle:
     """Owns one ``apsp_handle`` (workspace, serving thread) on one device."""
 
     def __init__(self, device: int = 0, dtype="int32", max_batch: int = 64, queue_depth: int = 4096,
-                 memory_budget: int = 0, spin_limit: int = 0, block_k: int = 0, phase3_variant: int = 0):
+                 memory_budget: int = 0, spin_limit: int = 0, block_k: int = 0, phase3_variant: int = 0,
+                 symmetric: int = 0):
         cfg = apsp_config()
         _L().apsp_config_default(ctypes.byref(cfg))
         cfg.device = device
@@ -69,6 +70,7 @@ class Handle:
         cfg.spin_limit = spin_limit
         cfg.block_k = block_k
         cfg.phase3_variant = phase3_variant
+        cfg.symmetric = symmetric
         h = ctypes.c_void_p()
         st = _L().apsp_create(ctypes.byref(h), ctypes.byref(cfg))
         if st != 0:

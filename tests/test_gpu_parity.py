@@ -324,3 +324,44 @@ def test_every_round_shape_matches_oracle(lib, block_k, variant, dt):
             Df = h.solve_t(dt, dev(gen.dense_matrix(n, s, d, w, dtype=np.float32))).cpu().numpy()
             D = np.where(np.isinf(Df), INF, Df.astype(np.float64)).astype(np.int64)  # small integers: exact
         np.testing.assert_array_equal(D, E)
+
+
+# ------------------------------------------------------------------ symmetric mode
+@pytest.mark.parametrize("symmetric", [0, 1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("dt", ["int32", "u16", "fp32"])
+@pytest.mark.parametrize("n", [65, 300, 1000])
+def test_symmetric_mode_matches_oracle(lib, symmetric, variant, dt, n):
+    """Undirected inputs: the symmetric mode (upper-triangle tiles + mirror),
+    auto-detected (0), forced (1) or off (2), gives the oracle's matrix."""
+    s, d, w = er_edges(n, seed=n + variant, deg=3.0, wmax=40)
+    E = expect_fw(gen.dense_matrix(n, s, d, w, dtype=np.int32))
+    with lib.Handle(device=0, phase3_variant=variant, symmetric=symmetric) as h:
+        if dt == "int32":
+            D = h.solve_t(dt, dev(gen.dense_matrix(n, s, d, w, dtype=np.int32))).cpu().numpy().astype(np.int64)
+        elif dt == "u16":
+            D16 = h.solve_t(dt, dev(gen.dense_matrix(n, s, d, w, dtype=np.int16, inf=0x7FFF))).cpu().numpy()
+            D = oracle.unpack_u16(D16.view(np.uint16)).astype(np.int64)
+        else:
+            Df = h.solve_t(dt, dev(gen.dense_matrix(n, s, d, w, dtype=np.float32))).cpu().numpy()
+            D = np.where(np.isinf(Df), INF, Df.astype(np.float64)).astype(np.int64)
+        np.testing.assert_array_equal(D, E)
+
+
+@pytest.mark.parametrize("block_k", [32, 64])
+def test_symmetric_mode_block_k_and_ld(lib, block_k):
+    n, ld = 333, 340
+    s, d, w = er_edges(n, seed=block_k, deg=3.0, wmax=500)
+    W = gen.dense_matrix(n, s, d, w, dtype=np.int32, ld=ld)
+    with lib.Handle(device=0, block_k=block_k, symmetric=1) as h:
+        D = h.solve_t("int32", dev(W)).cpu().numpy()[:, :n]
+    np.testing.assert_array_equal(D.astype(np.int64), expect_fw(W))
+
+
+def test_auto_symmetric_detection_keeps_directed_exact(lib):
+    n = 500
+    s, d, w = er_edges(n, seed=99, deg=4.0, directed=True)
+    W = dense_directed(n, s, d, w)
+    with lib.Handle(device=0, symmetric=0) as h:
+        D = h.solve_t("int32", dev(W)).cpu().numpy()
+    np.testing.assert_array_equal(D.astype(np.int64), expect_fw(W))
