@@ -379,6 +379,14 @@ apsp_status apsp_create(apsp_handle **out, const apsp_config *cfg) {
   if (cudaSetDevice(c.device) != cudaSuccess) return APSP_E_CUDA;
   std::unique_ptr<apsp_handle> h(new apsp_handle());
   h->cfg = c;
+  {
+    // stream-ordered allocations (request loop, bound pass) stay in the pool
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, c.device) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+  }
   if (cudaMalloc(&h->d_status, 64) != cudaSuccess) return APSP_E_CUDA;
   if (cudaMemset(h->d_status, 0, 64) != cudaSuccess) return APSP_E_CUDA;
   if (cudaMallocHost(&h->h_status, 64) != cudaSuccess) {
@@ -1021,12 +1029,26 @@ apsp_status admit_group(apsp_handle *h, const std::vector<Request *> &rs) {
       return APSP_E_CUDA;
   }
   if (rs.size() == 1 && rs[0]->req.n >= kLargeN) {
-    // one large graph: per-round kernels on the group's stream
+    // one large graph: per-round kernels on the group's stream; an undirected
+    // (symmetric) matrix takes the symmetric mode, decided by a device check
     const int64_t rn = rs[0]->req.n;
     const int64_t ldT = panel_ld(rn);
     if (cudaMallocAsync(&g->ws, (size_t)apsp::kMaxRoundWidth * ldT * 4, s) != cudaSuccess) return APSP_E_CUDA;
-    if (apsp::launch_rounds(APSP_I32, rs[0]->D, rn, rn, g->ws, ldT, s, &l, nullptr, config_for(h, APSP_I32, rn),
-                            g->status + 1) != cudaSuccess)
+    apsp::RoundConfig rc = config_for(h, APSP_I32, rn);
+    if (h->cfg.symmetric != 2) {
+      int flag = 0;
+      int *dflag = g->status + 1;  // reused below as the wait-error word (reset first)
+      if (h->cfg.symmetric == 1) {
+        rc.sym = true;
+      } else if (apsp::launch_symmetry_check(APSP_I32, rs[0]->D, rn, rn, dflag, s) == cudaSuccess &&
+                 cudaMemcpyAsync(&flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+                 cudaStreamSynchronize(s) == cudaSuccess) {
+        rc.sym = flag == 0;
+      }
+      if (cudaMemsetAsync(dflag, 0, sizeof(int), s) != cudaSuccess) return APSP_E_CUDA;
+    }
+    if (apsp::launch_rounds(APSP_I32, rs[0]->D, rn, rn, g->ws, ldT, s, &l, nullptr, rc, g->status + 1) !=
+        cudaSuccess)
       return APSP_E_CUDA;
     h->launches += l;
     if (cudaEventRecord(g->done_ev, s) != cudaSuccess) return APSP_E_CUDA;

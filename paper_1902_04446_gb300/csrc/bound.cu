@@ -143,10 +143,16 @@ __global__ void fill_edges(const int32_t *__restrict__ W, int64_t n, int64_t ld,
   if (bad) *asym = 1;
 }
 
+// Stream-ordered scratch (cudaMallocAsync from the device's memory pool, which
+// the library keeps from returning memory to the system, so repeated solves
+// reuse it without synchronizing the device).
 struct DevBuf {
   void *p = nullptr;
+  cudaStream_t s = nullptr;
+  explicit DevBuf(cudaStream_t st) : s(st) {}
+  cudaError_t alloc(size_t bytes) { return cudaMallocAsync(&p, bytes, s); }
   ~DevBuf() {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, s);
   }
 };
 
@@ -156,10 +162,10 @@ cudaError_t run_bf(const int32_t *src, const int32_t *dst, const WT *w, int64_t 
   *bound = 0;
   *ok = 1;
   if (n <= 0) return cudaSuccess;
-  DevBuf keyb, aux;
-  cudaError_t e = cudaMalloc(&keyb.p, (size_t)n * sizeof(unsigned long long));
+  DevBuf keyb(s), aux(s);
+  cudaError_t e = keyb.alloc((size_t)n * sizeof(unsigned long long));
   if (e != cudaSuccess) return e;
-  e = cudaMalloc(&aux.p, 64);
+  e = aux.alloc(64);
   if (e != cudaSuccess) return e;
   unsigned long long *key = static_cast<unsigned long long *>(keyb.p);
   int *changed = static_cast<int *>(aux.p);
@@ -210,8 +216,8 @@ cudaError_t bound_from_dense(const int32_t *W, int64_t n, int64_t ld, int64_t ma
   *bound = 0;
   *ok = 1;
   if (n <= 0) return cudaSuccess;
-  DevBuf offb;
-  cudaError_t e = cudaMalloc(&offb.p, (size_t)(2 * n + 2) * sizeof(int64_t) + 64);
+  DevBuf offb(s);
+  cudaError_t e = offb.alloc((size_t)(2 * n + 2) * sizeof(int64_t) + 64);
   if (e != cudaSuccess) return e;
   int64_t *cnt = static_cast<int64_t *>(offb.p);
   int64_t *off = cnt + n;
@@ -230,8 +236,8 @@ cudaError_t bound_from_dense(const int32_t *W, int64_t n, int64_t ld, int64_t ma
     *ok = 0;
     return cudaSuccess;
   }
-  DevBuf eb;
-  e = cudaMalloc(&eb.p, (size_t)(m > 0 ? m : 1) * 3 * sizeof(int32_t));
+  DevBuf eb(s);
+  e = eb.alloc((size_t)(m > 0 ? m : 1) * 3 * sizeof(int32_t));
   if (e != cudaSuccess) return e;
   int32_t *src = static_cast<int32_t *>(eb.p);
   int32_t *dst = src + m;

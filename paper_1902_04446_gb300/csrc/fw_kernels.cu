@@ -53,13 +53,16 @@ __global__ void __launch_bounds__(P1_THREADS) fw_phase1(typename Op::elem *__res
 // ---------------------------------------------------------------- Phase 2
 // Row-panel CTAs: tile BK x 128 words; column-panel CTAs: tile
 // (128 * EPW) x (BK / EPW) words.  Both use 128 threads.
+// 8 x 4 words per thread (twice the warps of 8 x 8): Phase 2 has little work
+// per round and is latency-bound.
 template <class Op, int BK>
 struct P2Cfg {
+  static constexpr int TN = 4;
   static constexpr int ROW_BM = BK, ROW_BNW = 128;
   static constexpr int COL_BM = 128 * Op::EPW, COL_BNW = BK / Op::EPW;
-  static constexpr int THREADS = (BK / 8) * 16;
-  static_assert(TileMap<ROW_BM, ROW_BNW>::THREADS == THREADS, "row tile");
-  static_assert(TileMap<COL_BM, COL_BNW>::THREADS == THREADS, "col tile");
+  static constexpr int THREADS = (BK / 8) * (128 / TN);
+  static_assert(TileMap<ROW_BM, ROW_BNW, TN>::THREADS == THREADS, "row tile");
+  static_assert(TileMap<COL_BM, COL_BNW, TN>::THREADS == THREADS, "col tile");
   static constexpr int ROW_SMEM = (BK * ROW_BM + BK * ROW_BNW) * 4;
   static constexpr int COL_SMEM = (BK * COL_BM + BK * COL_BNW) * 4;
   static constexpr int SMEM = ROW_SMEM > COL_SMEM ? ROW_SMEM : COL_SMEM;
@@ -77,13 +80,13 @@ __global__ void __launch_bounds__(P2Cfg<Op, BK>::THREADS)
   extern __shared__ __align__(16) uint32_t smem[];
   const SymPanel<Op> *spp = sym ? &sp : nullptr;
   if ((int)blockIdx.x < nrow_ctas)
-    p2_row_task<Op, BK, C::ROW_BNW, C::THREADS, false>(
+    p2_row_task<Op, BK, C::ROW_BNW, C::THREADS, false, C::TN>(
         D, ld, n, p0, p1, colT, ldT, (int64_t)(row_chunk0 + (int)blockIdx.x) * C::ROW_BNW * Op::EPW, vec, smem,
         threadIdx.x, spp);
   else
-    p2_col_task<Op, BK, C::COL_BM, C::THREADS, false>(D, ld, n, p0, p1, colT, ldT,
-                                                      (int64_t)(blockIdx.x - nrow_ctas) * C::COL_BM, vec, smem,
-                                                      threadIdx.x, spp);
+    p2_col_task<Op, BK, C::COL_BM, C::THREADS, false, C::TN>(D, ld, n, p0, p1, colT, ldT,
+                                                             (int64_t)(blockIdx.x - nrow_ctas) * C::COL_BM, vec,
+                                                             smem, threadIdx.x, spp);
 }
 
 // Phase 1 kernel with the optional element panel (symmetric mode).

@@ -138,42 +138,60 @@ struct SymPanel {
   int64_t band_end;         // end of the Phase-3 tile column band that holds the diagonal block
 };
 
-template <class Op, int BK, int BNW, int NT, bool CG>
+template <class Op, int BK, int BNW, int NT, bool CG, int TN = 8>
 __device__ __forceinline__ void p2_row_task(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
                                             int64_t p1, uint32_t *__restrict__ colT, int64_t ldT, int64_t col0,
                                             bool vec, uint32_t *smem, int tid, const SymPanel<Op> *sym = nullptr) {
-  using Map = TileMap<BK, BNW>;
+  using Map = TileMap<BK, BNW, TN>;
   static_assert(Map::THREADS == NT, "row tile");
   uint32_t *As = smem;
   uint32_t *Bs = smem + BK * BK;
   const int tx = tid % Map::TX, ty = tid / Map::TX;
-  uint32_t acc[8][8];
+  uint32_t acc[8][TN];
   load_As_colT<BK, BK, NT, CG>(As, colT, ldT, p0, tid);
   load_Bs_rows<Op, BNW, BK, NT, CG>(Bs, D, ld, n, n, p0, col0, vec, tid);
-  load_acc<Op, BK, BNW, CG>(D, ld, n, n, p0, col0, vec, acc, ty, tx);
+  load_acc<Op, BK, BNW, CG, TN>(D, ld, n, n, p0, col0, vec, acc, ty, tx);
   __syncthreads();
-  tile_minplus<Op, BK, BNW, BK>(As, Bs, acc, ty, tx);
+  tile_minplus<Op, BK, BNW, BK, TN>(As, Bs, acc, ty, tx);
   if (!sym) {
-    store_acc<Op, BK, BNW>(D, ld, n, n, p0, col0, 0, 0, p0, p1, vec, acc, ty, tx);
+    store_acc<Op, BK, BNW, TN>(D, ld, n, n, p0, col0, 0, 0, p0, p1, vec, acc, ty, tx);
     return;
   }
-  store_acc<Op, BK, BNW>(D, ld, n, n, p0, col0, 0, 0, 0, p1, vec, acc, ty, tx);
+  store_acc<Op, BK, BNW, TN>(D, ld, n, n, p0, col0, 0, 0, 0, p1, vec, acc, ty, tx);
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
     const int t = Map::row(ty, r);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < Map::NH; ++h) {
+      const int64_t x0 = col0 + (int64_t)Map::wcol(tx, h) * Op::EPW;  // first element of these 4 words
+      constexpr int E = 4 * Op::EPW;
+      const uint4 w4 = make_uint4(acc[r][4 * h + 0], acc[r][4 * h + 1], acc[r][4 * h + 2], acc[r][4 * h + 3]);
+      if (x0 >= p1 && x0 + E <= n) {
+        // the whole chunk is right of the diagonal block: 16-byte panel stores
+        uint32_t *cw = colT + (int64_t)t * ldT + x0;
+        if constexpr (Op::EPW == 1) {
+          *reinterpret_cast<uint4 *>(cw) = w4;
+        } else {
+          *reinterpret_cast<uint4 *>(cw) = make_uint4(Op::dup(w4.x & 0xFFFFu), Op::dup(w4.x >> 16),
+                                                      Op::dup(w4.y & 0xFFFFu), Op::dup(w4.y >> 16));
+          *reinterpret_cast<uint4 *>(cw + 4) = make_uint4(Op::dup(w4.z & 0xFFFFu), Op::dup(w4.z >> 16),
+                                                          Op::dup(w4.w & 0xFFFFu), Op::dup(w4.w >> 16));
+          *reinterpret_cast<uint4 *>(sym->rowP + (int64_t)t * ldT + x0) = w4;
+        }
+        if (x0 < sym->band_end && p0 + t < n) {
 #pragma unroll
-      for (int cw = 0; cw < 4; ++cw) {
-        const uint32_t word = acc[r][4 * h + cw];
+          for (int e = 0; e < E; ++e)
+            if (x0 + e < sym->band_end) D[(x0 + e) * ld + p0 + t] = bits_elem<Op>(chunk_get<Op>(w4, e));
+        }
+      } else {
 #pragma unroll
-        for (int lane = 0; lane < Op::EPW; ++lane) {
-          const int64_t x = col0 + (int64_t)(Map::wcol(tx, h) + cw) * Op::EPW + lane;
+        for (int e = 0; e < E; ++e) {
+          const int64_t x = x0 + e;
           if (x < p1 || x >= n) continue;
-          const typename Op::elem e = bits_elem<Op>(Op::EPW == 2 ? (lane ? (word >> 16) : (word & 0xFFFFu)) : word);
-          colT[(int64_t)t * ldT + x] = Op::dup(e);
-          if (sym->rowP) sym->rowP[(int64_t)t * ldT + x] = e;
-          if (x < sym->band_end && p0 + t < n) D[x * ld + p0 + t] = e;
+          const typename Op::elem v = bits_elem<Op>(chunk_get<Op>(w4, e));
+          colT[(int64_t)t * ldT + x] = Op::dup(v);
+          if (sym->rowP) sym->rowP[(int64_t)t * ldT + x] = v;
+          if (x < sym->band_end && p0 + t < n) D[x * ld + p0 + t] = v;
         }
       }
     }
@@ -183,28 +201,28 @@ __device__ __forceinline__ void p2_row_task(typename Op::elem *__restrict__ D, i
 // Symmetric mode: only rows < p0 are updated (the upper triangle); the
 // results also go to the row panel's lower-triangle elements D[p0+t][x] and,
 // for packed 16-bit, to sym->rowP.
-template <class Op, int BK, int BM, int NT, bool CG>
+template <class Op, int BK, int BM, int NT, bool CG, int TN = 8>
 __device__ __forceinline__ void p2_col_task(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
                                             int64_t p1, uint32_t *__restrict__ colT, int64_t ldT, int64_t row0,
                                             bool vec, uint32_t *smem, int tid, const SymPanel<Op> *sym = nullptr) {
   constexpr int BNW = BK / Op::EPW;
-  using Map = TileMap<BM, BNW>;
+  using Map = TileMap<BM, BNW, TN>;
   static_assert(Map::THREADS == NT, "col tile");
   uint32_t *As = smem;
   uint32_t *Bs = smem + BK * BM;
   const int tx = tid % Map::TX, ty = tid / Map::TX;
-  uint32_t acc[8][8];
+  uint32_t acc[8][TN];
   load_As_transposed<Op, BM, BK, NT, CG>(As, D, ld, n, n, row0, p0, vec, tid);
   load_Bs_rows<Op, BNW, BK, NT, CG>(Bs, D, ld, n, n, p0, p0, vec, tid);
-  load_acc<Op, BM, BNW, CG>(D, ld, n, n, row0, p0, vec, acc, ty, tx);
+  load_acc<Op, BM, BNW, CG, TN>(D, ld, n, n, row0, p0, vec, acc, ty, tx);
   __syncthreads();
-  tile_minplus<Op, BM, BNW, BK>(As, Bs, acc, ty, tx);
+  tile_minplus<Op, BM, BNW, BK, TN>(As, Bs, acc, ty, tx);
   // symmetric mode stores rows < p0 only
   const int64_t xr1 = sym ? INT64_MAX : p1;
-  store_acc<Op, BM, BNW>(D, ld, n, n, row0, p0, p0, xr1, 0, 0, vec, acc, ty, tx);
+  store_acc<Op, BM, BNW, TN>(D, ld, n, n, row0, p0, p0, xr1, 0, 0, vec, acc, ty, tx);
   // transposed copy: colT[t][row0 + i] = word(D_Ik[i][t]) for rows outside [p0, p1)
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
+  for (int h = 0; h < Map::NH; ++h) {
 #pragma unroll
     for (int g = 0; g < 2; ++g) {
       const int ib = Map::row(ty, 4 * g);  // 4 consecutive rows ib .. ib+3
