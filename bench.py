@@ -442,6 +442,16 @@ def run_gpu(args):
                              "u16x2 rounds, unpack (all inside the timed region)",
                              "phase3_achieved": a16, "phase3_peak": 2 * peak,
                              "phase3_frac": (a16 / (2 * peak)) if a16 else None, "gpu_launches": int(l16)}
+        # structure-obliviousness (the paper's Sec. 5.1: runtime depends only on n):
+        # the same solve on an Erdos-Renyi graph with the same n
+        if n == 16384:
+            ge = load_graph("er16k")
+            We = dense_on_device(torch, ge, torch.int32, 1073741823, device)
+            mse, _, _ = timed_solves(torch, h, "int32", We, Dd, args.steps, args.warmup, dist)
+            out["structure_check"] = {"er16k_ms_per_step": mse / args.steps, "workload_ms_per_step": ms / args.steps,
+                                      "ratio": (mse / args.steps) / (ms / args.steps),
+                                      "graph": WORKLOAD_TEXT["er16k"]}
+            del We
         gf = gen.workload("gmm16k_f32") if args.workload == "gmm16k" else g
         gf = gen.graphs.Graph(gf.name, gf.n, gf.src, gf.dst, gf.w.astype(np.float32), "fp32")
         Wf = dense_on_device(torch, gf, torch.float32, float("inf"), device)

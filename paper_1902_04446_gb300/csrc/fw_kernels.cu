@@ -55,12 +55,15 @@ __global__ void __launch_bounds__(P1_THREADS) fw_phase1(typename Op::elem *__res
 // (128 * EPW) x (BK / EPW) words.  Both use 128 threads.
 // 8 x 4 words per thread (twice the warps of 8 x 8): Phase 2 has little work
 // per round and is latency-bound.
+// Chunks are 128 elements wide (row panel) and 128 rows tall (column panel)
+// for every element type, so a round has as many Phase-2 CTAs for packed
+// 16-bit as for int32.
 template <class Op, int BK>
 struct P2Cfg {
   static constexpr int TN = 4;
-  static constexpr int ROW_BM = BK, ROW_BNW = 128;
-  static constexpr int COL_BM = 128 * Op::EPW, COL_BNW = BK / Op::EPW;
-  static constexpr int THREADS = (BK / 8) * (128 / TN);
+  static constexpr int ROW_BM = BK, ROW_BNW = 128 / Op::EPW;
+  static constexpr int COL_BM = 128, COL_BNW = BK / Op::EPW;
+  static constexpr int THREADS = (BK / 8) * (ROW_BNW / TN);
   static_assert(TileMap<ROW_BM, ROW_BNW, TN>::THREADS == THREADS, "row tile");
   static_assert(TileMap<COL_BM, COL_BNW, TN>::THREADS == THREADS, "col tile");
   static constexpr int ROW_SMEM = (BK * ROW_BM + BK * ROW_BNW) * 4;
@@ -87,6 +90,27 @@ __global__ void __launch_bounds__(P2Cfg<Op, BK>::THREADS)
     p2_col_task<Op, BK, C::COL_BM, C::THREADS, false, C::TN>(D, ld, n, p0, p1, colT, ldT,
                                                              (int64_t)(blockIdx.x - nrow_ctas) * C::COL_BM, vec,
                                                              smem, threadIdx.x, spp);
+}
+
+// Symmetric mode, after Phase 2: for x < p0 (the column-panel part of the
+// symmetric panel, written by the column-panel CTAs as colT words), copy
+// row t of colT to the element panel rowP[t][x] (packed 16-bit only) and to
+// the row panel's lower-triangle elements D[p0 + t][x] inside the diagonal
+// tile band x >= band_start (the only ones that Phase-3 tiles read).
+// Coalesced: one block row per panel row t.
+template <class Op>
+__global__ void panel_finalize(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
+                               const uint32_t *__restrict__ colT, int64_t ldT, typename Op::elem *__restrict__ rowP,
+                               int64_t band_start) {
+  const int t = blockIdx.y;
+  const int64_t row = p0 + t;
+  const int64_t x0 = rowP ? 0 : band_start;  // without an element panel only the band is needed
+  for (int64_t x = x0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < p0; x += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t w = colT[(int64_t)t * ldT + x];
+    const typename Op::elem e = bits_elem<Op>(Op::EPW == 2 ? (w & 0xFFFFu) : w);
+    if (rowP) rowP[(int64_t)t * ldT + x] = e;
+    if (x >= band_start && row < n) D[row * ld + x] = e;
+  }
 }
 
 // Phase 1 kernel with the optional element panel (symmetric mode).
@@ -608,6 +632,15 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
       if (r_count + c_count > 0)
         fw_phase2<Op, BK><<<r_count + c_count, C2::THREADS, C2::SMEM, s>>>(D, ld, n, p0, p1, colT, ldT, r_count,
                                                                           vec ? 1 : 0, r_first, sym ? 1 : 0, sp);
+      if (sym && p0 > 0) {
+        const int64_t band_start = (p0 / (128 * Op::EPW)) * (128 * Op::EPW);
+        const int64_t xs = rowP ? p0 : p0 - band_start;  // elements to visit per row
+        const unsigned gx = (unsigned)std::min<int64_t>((xs + 255) / 256, 64);
+        if (xs > 0) {
+          panel_finalize<Op><<<dim3(gx, BK), 256, 0, s>>>(D, ld, n, p0, colT, ldT, rowP, band_start);
+          if (launches) *launches += 1;
+        }
+      }
       if (tm) tm->after(1, s, sym ? rest * w * w : 2.0 * rest * w * w);
       if (tm) tm->before(2, s);
       if (tma && variant == 2)

@@ -199,8 +199,8 @@ __device__ __forceinline__ void p2_row_task(typename Op::elem *__restrict__ D, i
 }
 
 // Symmetric mode: only rows < p0 are updated (the upper triangle); the
-// results also go to the row panel's lower-triangle elements D[p0+t][x] and,
-// for packed 16-bit, to sym->rowP.
+// panel_finalize pass then copies colT[t][x < p0] to the element panel and to
+// the row panel's lower-triangle elements in the diagonal band.
 template <class Op, int BK, int BM, int NT, bool CG, int TN = 8>
 __device__ __forceinline__ void p2_col_task(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
                                             int64_t p1, uint32_t *__restrict__ colT, int64_t ldT, int64_t row0,
@@ -248,18 +248,7 @@ __device__ __forceinline__ void p2_col_task(typename Op::elem *__restrict__ D, i
             for (int q = 0; q < 4; ++q)
               if (rb + q < p0 || rb + q >= xr1) dst[q] = q4[q];
           }
-          if (sym && p0 + t < n) {
-            // row panel's lower part D[p0+t][x] = D[x][p0+t], and the element panel
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const int64_t x = rb + q;
-              if (x >= p0 || x >= n) continue;
-              const typename Op::elem e =
-                  bits_elem<Op>(Op::EPW == 2 ? (q4[q] & 0xFFFFu) : q4[q]);
-              D[(p0 + t) * ld + x] = e;
-              if (sym->rowP) sym->rowP[(int64_t)t * ldT + x] = e;
-            }
-          }
+
         }
       }
     }

@@ -68,8 +68,9 @@ extern "C" apsp_status apsp_solve_i32_noalloc(const int32_t *W, int64_t n, int64
   // the flag must start at zero; the panel buffer is fully rewritten every round
   if (cudaMemsetAsync(wait_flag, 0, sizeof(int), s) != cudaSuccess) return APSP_E_CUDA;
   const int64_t ldT = (n + 255) / 256 * 256;
-  if (apsp::launch_rounds(APSP_I32, D, ld, n, panel, ldT, s, nullptr, nullptr, apsp::RoundConfig(), wait_flag) !=
-      cudaSuccess)
+  apsp::RoundConfig rc;
+  rc.bk = 64;  // the static panel holds 64 rows
+  if (apsp::launch_rounds(APSP_I32, D, ld, n, panel, ldT, s, nullptr, nullptr, rc, wait_flag) != cudaSuccess)
     return APSP_E_CUDA;
   return APSP_OK;
 }

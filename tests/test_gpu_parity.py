@@ -365,3 +365,44 @@ def test_auto_symmetric_detection_keeps_directed_exact(lib):
     with lib.Handle(device=0, symmetric=0) as h:
         D = h.solve_t("int32", dev(W)).cpu().numpy()
     np.testing.assert_array_equal(D.astype(np.int64), expect_fw(W))
+
+
+# ------------------------------------------------------------------ degenerate graphs
+def _solve_any(H, dt, n, s, d, w):
+    if dt == "int32":
+        return H.solve_t(dt, dev(gen.dense_matrix(n, s, d, w, dtype=np.int32))).cpu().numpy().astype(np.int64)
+    if dt == "u16":
+        D16 = H.solve_t(dt, dev(gen.dense_matrix(n, s, d, w, dtype=np.int16, inf=0x7FFF))).cpu().numpy()
+        return oracle.unpack_u16(D16.view(np.uint16)).astype(np.int64)
+    Df = H.solve_t(dt, dev(gen.dense_matrix(n, s, d, w, dtype=np.float32))).cpu().numpy()
+    return np.where(np.isinf(Df), INF, Df.astype(np.float64)).astype(np.int64)
+
+
+@pytest.mark.parametrize("dt", ["int32", "u16", "fp32"])
+def test_zero_weight_edges(H, dt):
+    n = 300
+    s, d, w = er_edges(n, seed=21, deg=3.0, wmax=5)
+    w = np.where(np.arange(w.shape[0]) % 3 == 0, 0, w)  # a third of the edges weigh 0
+    E = expect_fw(gen.dense_matrix(n, s, d, w, dtype=np.int32))
+    np.testing.assert_array_equal(_solve_any(H, dt, n, s, d, w), E)
+
+
+@pytest.mark.parametrize("dt", ["int32", "u16", "fp32"])
+def test_complete_graph_and_edgeless_graph(H, dt):
+    n = 260
+    iu, ju = np.triu_indices(n, 1)
+    rng = np.random.default_rng(4)
+    w = rng.integers(1, 50, size=iu.shape[0])
+    E = expect_fw(gen.dense_matrix(n, iu, ju, w, dtype=np.int32))
+    np.testing.assert_array_equal(_solve_any(H, dt, n, iu, ju, w), E)
+    z = np.zeros(0, dtype=np.int64)
+    E0 = np.full((n, n), INF, dtype=np.int64)
+    np.fill_diagonal(E0, 0)
+    np.testing.assert_array_equal(_solve_any(H, dt, n, z, z, z), E0)
+
+
+@pytest.mark.parametrize("dt", ["int32", "u16", "fp32", "auto"])
+def test_single_vertex(H, dt):
+    np_dt = {"int32": np.int32, "auto": np.int32, "u16": np.int16, "fp32": np.float32}[dt]
+    D = H.solve_t(dt, dev(np.zeros((1, 1), dtype=np_dt))).cpu().numpy()
+    assert D.shape == (1, 1) and D[0, 0] == 0
