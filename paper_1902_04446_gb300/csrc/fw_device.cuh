@@ -113,22 +113,20 @@ __device__ __forceinline__ uint4 ld16(const void *p) {
   else return __ldg(reinterpret_cast<const uint4 *>(p));
 }
 
-template <class Op, bool CG = false>
-__device__ __forceinline__ uint4 load_chunk(const typename Op::elem *M, int64_t ld, int64_t nrows, int64_t ncols,
-                                            int64_t r, int64_t c0, bool vec) {
+// Per-element path of load_chunk (a chunk that crosses the matrix edge, or an
+// unaligned matrix).  Kept out of line: it is rare, and inlining it into every
+// tile loop makes the kernels too large for the instruction cache.
+template <class Op, bool CG>
+__device__ __noinline__ uint4 load_chunk_slow(const typename Op::elem *M, int64_t ld, int64_t ncols, int64_t r,
+                                              int64_t c0, bool vec) {
   constexpr int E = 4 * Op::EPW;
   uint4 v = make_uint4(Op::INF_WORD, Op::INF_WORD, Op::INF_WORD, Op::INF_WORD);
-  if (r < 0 || r >= nrows || c0 >= ncols) return v;
   const typename Op::elem *p = M + r * ld + c0;
   if (vec && c0 + E <= ld) {
     v = ld16<CG>(p);
-    if (c0 + E > ncols) {
-#pragma unroll
-      for (int e = 0; e < E; ++e)
-        if (c0 + e >= ncols) chunk_set<Op>(v, e, elem_bits<Op>(Op::inf_elem()));
-    }
+    for (int e = 0; e < E; ++e)
+      if (c0 + e >= ncols) chunk_set<Op>(v, e, elem_bits<Op>(Op::inf_elem()));
   } else {
-#pragma unroll
     for (int e = 0; e < E; ++e)
       if (c0 + e < ncols) {
         if constexpr (CG) chunk_set<Op>(v, e, elem_bits<Op>(__ldcg(p + e)));
@@ -136,6 +134,24 @@ __device__ __forceinline__ uint4 load_chunk(const typename Op::elem *M, int64_t 
       }
   }
   return v;
+}
+
+template <class Op, bool CG = false>
+__device__ __forceinline__ uint4 load_chunk(const typename Op::elem *M, int64_t ld, int64_t nrows, int64_t ncols,
+                                            int64_t r, int64_t c0, bool vec) {
+  constexpr int E = 4 * Op::EPW;
+  if (r < 0 || r >= nrows || c0 >= ncols)
+    return make_uint4(Op::INF_WORD, Op::INF_WORD, Op::INF_WORD, Op::INF_WORD);
+  if (vec && c0 + E <= ncols) return ld16<CG>(M + r * ld + c0);  // the common case: one 16-byte load
+  return load_chunk_slow<Op, CG>(M, ld, ncols, r, c0, vec);
+}
+
+// Per-element path of store_chunk, out of line for the same reason.
+template <class Op>
+__device__ __noinline__ void store_chunk_slow(typename Op::elem *p, uint4 v, uint32_t mask) {
+  constexpr int E = 4 * Op::EPW;
+  for (int e = 0; e < E; ++e)
+    if (mask & (1u << e)) p[e] = bits_elem<Op>(chunk_get<Op>(v, e));
 }
 
 // Stores the elements of a 4-word chunk whose mask bit is set (bit e for
@@ -147,13 +163,8 @@ __device__ __forceinline__ void store_chunk(typename Op::elem *M, int64_t ld, in
   constexpr uint32_t FULL = (1u << E) - 1u;
   if (mask == 0) return;
   typename Op::elem *p = M + r * ld + c0;
-  if (vec && mask == FULL) {
-    *reinterpret_cast<uint4 *>(p) = v;
-  } else {
-#pragma unroll
-    for (int e = 0; e < E; ++e)
-      if (mask & (1u << e)) p[e] = bits_elem<Op>(chunk_get<Op>(v, e));
-  }
+  if (vec && mask == FULL) *reinterpret_cast<uint4 *>(p) = v;
+  else store_chunk_slow<Op>(p, v, mask);
 }
 
 // Mask of the elements c0 .. c0+E-1 that lie in [0, ncols) and outside the

@@ -138,6 +138,32 @@ struct SymPanel {
   int64_t band_end;         // end of the Phase-3 tile column band that holds the diagonal block
 };
 
+// Per-element publication of a chunk that straddles p1 or n (out of line: rare).
+template <class Op>
+__device__ __noinline__ void sym_publish_slow(typename Op::elem *D, int64_t ld, int64_t n, int64_t p0, int64_t p1,
+                                              uint32_t *colT, int64_t ldT, const SymPanel<Op> *sym, int t,
+                                              int64_t x0, uint4 w4) {
+  constexpr int E = 4 * Op::EPW;
+  for (int e = 0; e < E; ++e) {
+    const int64_t x = x0 + e;
+    if (x < p1 || x >= n) continue;
+    const typename Op::elem v = bits_elem<Op>(chunk_get<Op>(w4, e));
+    colT[(int64_t)t * ldT + x] = Op::dup(v);
+    if (sym->rowP) sym->rowP[(int64_t)t * ldT + x] = v;
+    if (x < sym->band_end && p0 + t < n) D[x * ld + p0 + t] = v;
+  }
+}
+
+// Lower-triangle band elements D[x][p0+t] of a full chunk (out of line: only
+// the chunks next to the diagonal block have any).
+template <class Op>
+__device__ __noinline__ void sym_band_store(typename Op::elem *D, int64_t ld, int64_t col, int64_t band_end, int64_t x0,
+                                            uint4 w4) {
+  constexpr int E = 4 * Op::EPW;
+  for (int e = 0; e < E; ++e)
+    if (x0 + e < band_end) D[(x0 + e) * ld + col] = bits_elem<Op>(chunk_get<Op>(w4, e));
+}
+
 template <class Op, int BK, int BNW, int NT, bool CG, int TN = 8>
 __device__ __forceinline__ void p2_row_task(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
                                             int64_t p1, uint32_t *__restrict__ colT, int64_t ldT, int64_t col0,
@@ -178,21 +204,9 @@ __device__ __forceinline__ void p2_row_task(typename Op::elem *__restrict__ D, i
                                                           Op::dup(w4.w & 0xFFFFu), Op::dup(w4.w >> 16));
           *reinterpret_cast<uint4 *>(sym->rowP + (int64_t)t * ldT + x0) = w4;
         }
-        if (x0 < sym->band_end && p0 + t < n) {
-#pragma unroll
-          for (int e = 0; e < E; ++e)
-            if (x0 + e < sym->band_end) D[(x0 + e) * ld + p0 + t] = bits_elem<Op>(chunk_get<Op>(w4, e));
-        }
-      } else {
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int64_t x = x0 + e;
-          if (x < p1 || x >= n) continue;
-          const typename Op::elem v = bits_elem<Op>(chunk_get<Op>(w4, e));
-          colT[(int64_t)t * ldT + x] = Op::dup(v);
-          if (sym->rowP) sym->rowP[(int64_t)t * ldT + x] = v;
-          if (x < sym->band_end && p0 + t < n) D[x * ld + p0 + t] = v;
-        }
+        if (x0 < sym->band_end && p0 + t < n) sym_band_store<Op>(D, ld, p0 + t, sym->band_end, x0, w4);
+      } else if (x0 + E > p1 && x0 < n) {
+        sym_publish_slow<Op>(D, ld, n, p0, p1, colT, ldT, sym, t, x0, w4);
       }
     }
   }
@@ -201,6 +215,14 @@ __device__ __forceinline__ void p2_row_task(typename Op::elem *__restrict__ D, i
 // Symmetric mode: only rows < p0 are updated (the upper triangle); the
 // panel_finalize pass then copies colT[t][x < p0] to the element panel and to
 // the row panel's lower-triangle elements in the diagonal band.
+// Transposed colT store of 4 rows of which some lie in the panel (out of line: rare).
+static __device__ __noinline__ void colT_store_partial(uint32_t *dst, int64_t rb, int64_t p0, int64_t xr1, uint32_t q0,
+                                                uint32_t q1, uint32_t q2, uint32_t q3) {
+  const uint32_t q4[4] = {q0, q1, q2, q3};
+  for (int q = 0; q < 4; ++q)
+    if (rb + q < p0 || rb + q >= xr1) dst[q] = q4[q];
+}
+
 template <class Op, int BK, int BM, int NT, bool CG, int TN = 8>
 __device__ __forceinline__ void p2_col_task(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
                                             int64_t p1, uint32_t *__restrict__ colT, int64_t ldT, int64_t row0,
@@ -241,13 +263,8 @@ __device__ __forceinline__ void p2_col_task(typename Op::elem *__restrict__ D, i
             q4[q] = (Op::EPW == 2) ? Op::dup(bits_elem<Op>(lane ? (word >> 16) : (word & 0xFFFFu))) : word;
           }
           uint32_t *dst = colT + (int64_t)t * ldT + rb;
-          if (all_out) {
-            *reinterpret_cast<uint4 *>(dst) = make_uint4(q4[0], q4[1], q4[2], q4[3]);
-          } else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-              if (rb + q < p0 || rb + q >= xr1) dst[q] = q4[q];
-          }
+          if (all_out) *reinterpret_cast<uint4 *>(dst) = make_uint4(q4[0], q4[1], q4[2], q4[3]);
+          else colT_store_partial(dst, rb, p0, xr1, q4[0], q4[1], q4[2], q4[3]);
 
         }
       }
