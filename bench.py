@@ -399,7 +399,7 @@ def run_gpu(args):
     achieved = (r3 / n3) / (ms3 / n3 / 1e3) / 1e9 if n3 else None
     peak = ADDMIN_LANES_PER_CLK_PER_SM * sms * sm_max_mhz * 1e6 / 1e9
     phase_ms = {f"phase{p}": round(prof[p][1] / args.steps, 3) for p in (1, 2, 3)}
-    roofline = {"bound": "alu", "kernel": "fw_phase3_tma<int32>", "achieved": achieved, "peak": peak, "unit": UNIT,
+    roofline = {"bound": "alu", "kernel": "fw_phase3_ws<int32>", "achieved": achieved, "peak": peak, "unit": UNIT,
                 "work": "relaxations actually performed by Phase 3 (in symmetric mode only the tiles touching "
                         "the upper triangle)",
                 "frac": (achieved / peak) if achieved else None,

@@ -81,7 +81,9 @@ typedef struct {
   int64_t memory_budget; /* serving: bytes of device memory for admitted requests (0 = free HBM - reserve) */
   int64_t spin_limit;    /* bounded device waits: iterations before APSP_E_TIMEOUT (0 = default) */
   int phase3_variant;    /* Phase-3 kernel: 0 = tuned or default, 1 = one CTA per tile, 2 = persistent
-                            TMA kernel with 256 threads, 3 = persistent TMA kernel with 512 threads */
+                            TMA kernel with 256 threads, 3 = persistent TMA kernel with 512 threads,
+                            4 = warp-specialized persistent kernel (TMA producer warp; int32 results
+                            leave by a TMA min-reduction) -- the default */
   int symmetric;         /* symmetric mode for undirected graphs (Sec. 3: A_ij = A_ji; the paper keeps
                             only the upper triangle): Phase 3 updates only the tiles touching the upper
                             triangle and the lower triangle is mirrored at the end -- same result, about
@@ -223,16 +225,17 @@ apsp_status apsp_cancel(apsp_handle *h, uint64_t ticket);
 /* The paper picks its block size b per problem size (Sec. 3 "user-provided
  * (or auto-tuned)", Sec. 5.2-5.4, Table 3).  For `dtype` and every n bucket
  * (powers of two from 128 up to n_max) this times the candidate round shapes
- * -- round width Bk in {32, 64} x Phase-3 variant (persistent TMA kernel or
- * one CTA per tile) -- on a synthetic matrix generated on the device (the
+ * -- round width Bk in {32, 64} x Phase-3 variant (the persistent TMA kernels
+ * or one CTA per tile) -- on a synthetic matrix generated on the device (the
  * kernels do the same work for any graph of a given n), and keeps the
  * fastest for later solves on this handle.  cache_path (nullable): a JSON
  * file keyed by GPU name; entries for this GPU are loaded instead of timing
  * when present, and new results are written back.  Synchronizes the device. */
 apsp_status apsp_autotune(apsp_handle *h, int dtype, int64_t n_max, const char *cache_path);
 
-/* The round shape the handle uses for (dtype, n): *block_k and *tma (1 =
- * persistent TMA Phase 3). */
+/* The round shape the handle uses for (dtype, n): *block_k and *tma, the
+ * Phase-3 kernel numbered as apsp_config.phase3_variant minus one (0 = one
+ * CTA per tile, 1-3 = the persistent TMA kernels). */
 apsp_status apsp_tuned_config(apsp_handle *h, int dtype, int64_t n, int *block_k, int *tma);
 
 /* ---- solve without allocation -------------------------------------------- */

@@ -224,7 +224,7 @@ apsp::RoundConfig config_for(apsp_handle *h, int dtype, int64_t n) {
       }
   }
   if (h->cfg.block_k == 32 || h->cfg.block_k == 64) c.bk = h->cfg.block_k;
-  if (h->cfg.phase3_variant >= 1 && h->cfg.phase3_variant <= 3) c.p3 = h->cfg.phase3_variant - 1;
+  if (h->cfg.phase3_variant >= 1 && h->cfg.phase3_variant <= 4) c.p3 = h->cfg.phase3_variant - 1;
   return c;
 }
 
@@ -370,7 +370,7 @@ apsp_status apsp_create(apsp_handle **out, const apsp_config *cfg) {
   if (cfg) c = *cfg;
   if (c.dtype != APSP_AUTO && !valid_dtype(c.dtype)) return APSP_E_INVALID;
   if (c.block_k != 0 && c.block_k != 32 && c.block_k != 64) return APSP_E_INVALID;
-  if (c.phase3_variant < 0 || c.phase3_variant > 3) return APSP_E_INVALID;
+  if (c.phase3_variant < 0 || c.phase3_variant > 4) return APSP_E_INVALID;
   if (c.symmetric < 0 || c.symmetric > 2) return APSP_E_INVALID;
   if (c.max_batch <= 0) c.max_batch = 64;
   if (c.queue_depth <= 0) c.queue_depth = 4096;
@@ -824,7 +824,7 @@ apsp_status apsp_autotune(apsp_handle *h, int dtype, int64_t n_max, const char *
     double best = 1e30;
     apsp::RoundConfig best_c;
     for (int bk : {32, 64})
-      for (int var : {1, 2, 0}) {
+      for (int var : {3, 2, 1, 0}) {
         apsp::RoundConfig c;
         c.bk = bk;
         c.p3 = var;

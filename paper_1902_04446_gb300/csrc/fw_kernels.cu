@@ -344,6 +344,220 @@ __global__ void __launch_bounds__(TileMap<128, 128, TN>::THREADS, 1)
   if (abort_flag && tid == 0) atomicOr(err, 4);
 }
 
+// Phase 3, warp-specialized persistent kernel: 8 consumer warps (8 x 8 words
+// each, one 128-row x 128-word tile per CTA at a time) and one producer warp
+// that moves all data with TMA.  The consumers never wait on each other:
+// full/empty mbarriers hand the two A/B stages back and forth, and the
+// accumulators start at INF, so C is needed only at the end of the tile:
+//   RED (int32): the consumers write acc into the C buffer and the producer
+//     applies it with a TMA min-reduction, D = min(D, acc), carried out in L2.
+//     C is never loaded.  Every tile is reduced, the panel rows and columns
+//     included: there the update reproduces the current values exactly (after
+//     Phase 2 the row panel R' = min(R, D_kk (x) R) with D_kk closed, so
+//     D_kk (x) R' >= R'; likewise for the column panel and D_kk itself), so
+//     other CTAs may read the row panel while it is rewritten.
+//   !RED (packed 16-bit, fp32): the producer loads C by TMA during the tile;
+//     the consumers merge it (min) at the end; interior tiles go back through
+//     the C buffer and a TMA store, edge tiles (panel rows or columns, ragged
+//     edge) by masked stores that leave the panels untouched.
+// Symmetric mode and the tile order are as in fw_phase3_tma.  Every wait is
+// bounded; a CTA that gives up waits (bounded) for its copies in flight and
+// ORs 4 into *err.
+constexpr int P3W_THREADS = 9 * 32;
+
+template <class Op, int BK, bool RED>
+__global__ void __launch_bounds__(P3W_THREADS, 1)
+    fw_phase3_ws(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                 const __grid_constant__ CUtensorMap mapC, typename Op::elem *__restrict__ D, int64_t ld, int64_t n,
+                 int64_t p0, int64_t p1, int tiles_x, int tiles_total, int *err, int sym, int tiles_y) {
+  constexpr int BM = 128, BNW = 128, TN = 8;
+  using Map = TileMap<BM, BNW, TN>;
+  constexpr int NCW = Map::THREADS / 32;  // consumer warps
+  static_assert(Map::THREADS + 32 == P3W_THREADS, "one producer warp after the consumers");
+  constexpr int STAGE = P3T<BK>::STAGE_BYTES;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_ab[2], empty_ab[2], full_c, cdone, cfree;
+  __shared__ int abort_flag;
+  uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  auto stA = [&](int s) { return reinterpret_cast<uint32_t *>(base + s * STAGE); };
+  auto stB = [&](int s) { return reinterpret_cast<uint32_t *>(base + s * STAGE) + BK * BM; };
+  uint32_t *Cs = reinterpret_cast<uint32_t *>(base + 2 * STAGE);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int per = tiles_total / (int)gridDim.x, extra = tiles_total % (int)gridDim.x;
+  const int t_begin = (int)blockIdx.x * per + min((int)blockIdx.x, extra);
+  const int t_end = t_begin + per + ((int)blockIdx.x < extra ? 1 : 0);
+  if (t_begin >= t_end) return;
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&full_ab[i], 1);
+      mbar_init(&empty_ab[i], NCW);
+    }
+    mbar_init(&full_c, 1);
+    mbar_init(&cdone, NCW);
+    mbar_init(&cfree, 1);
+    fence_barrier_init();
+    prefetch_tensormap(&mapA);
+    prefetch_tensormap(&mapB);
+    prefetch_tensormap(&mapC);
+    abort_flag = 0;
+  }
+  __syncthreads();
+
+  // first tile of this CTA and the row-major step over the (symmetric) tile set
+  int ty0, tx0;
+  if (!sym) {
+    ty0 = t_begin / tiles_x;
+    tx0 = t_begin % tiles_x;
+  } else {
+    int lo = 0, hi = tiles_y - 1;  // last tile row whose prefix <= t_begin
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (sym_prefix(mid, tiles_x, Op::EPW) <= t_begin) lo = mid;
+      else hi = mid - 1;
+    }
+    ty0 = lo;
+    tx0 = lo / Op::EPW + (int)(t_begin - sym_prefix(lo, tiles_x, Op::EPW));
+  }
+  auto step = [&](int &ty_, int &tx_) {
+    if (++tx_ == tiles_x) {
+      ++ty_;
+      tx_ = sym ? ty_ / Op::EPW : 0;
+    }
+  };
+  auto interior_of = [&](int64_t r0, int64_t c0) {
+    return r0 + BM <= n && c0 + BNW * Op::EPW <= n && (r0 + BM <= p0 || r0 >= p1) &&
+           (c0 + BNW * Op::EPW <= p0 || c0 >= p1);
+  };
+
+  if (warp == NCW) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int n_ab[2] = {0, 0}, n_c = 0;
+      bool ok = true;
+      auto issue_ab = [&](int ty_, int tx_, int s) {
+        mbar_arrive_expect_tx(&full_ab[s], STAGE);
+        tma_load_2d(stA(s), &mapA, &full_ab[s], ty_ * BM, 0);
+        tma_load_2d(stB(s), &mapB, &full_ab[s], tx_ * BNW * Op::EPW, sym ? 0 : (int)p0);
+        if (s == 0) ++n_ab[0];
+        else ++n_ab[1];
+      };
+      auto issue_c = [&](int ty_, int tx_) {
+        mbar_arrive_expect_tx(&full_c, P3T_C_BYTES);
+        tma_load_2d(Cs, &mapC, &full_c, tx_ * BNW * Op::EPW, ty_ * BM);
+        ++n_c;
+      };
+      int aty = ty0, atx = tx0;  // next A/B tile to load
+      int cty = ty0, ctx = tx0;  // tile whose result is written next
+      issue_ab(aty, atx, 0);
+      step(aty, atx);
+      if (t_begin + 1 < t_end) {
+        issue_ab(aty, atx, 1);
+        step(aty, atx);
+      }
+      if (!RED) issue_c(cty, ctx);
+      for (int t = t_begin; t < t_end; ++t) {
+        const int i = t - t_begin, s = i & 1;
+        if (!mbar_wait_bounded(&empty_ab[s], (uint32_t)(i >> 1) & 1u, P3T_WAIT_LIMIT)) {
+          ok = false;
+          break;
+        }
+        if (t + 2 < t_end) {
+          issue_ab(aty, atx, s);
+          step(aty, atx);
+        }
+        if (!mbar_wait_bounded(&cdone, (uint32_t)i & 1u, P3T_WAIT_LIMIT)) {
+          ok = false;
+          break;
+        }
+        const int r0 = cty * BM, c0 = ctx * BNW * Op::EPW;
+        if (RED) {
+          tma_reduce_min_2d(&mapC, Cs, c0, r0);
+          bulk_commit();
+          bulk_wait_read_all();
+          mbar_arrive(&cfree);
+        } else if (interior_of(r0, c0)) {
+          tma_store_2d(&mapC, Cs, c0, r0);
+          bulk_commit();
+          bulk_wait_read_all();
+        }
+        step(cty, ctx);
+        if (!RED && t + 1 < t_end) issue_c(cty, ctx);
+      }
+      bulk_wait_all();
+      if (!ok) {
+        abort_flag = 1;
+        for (int st = 0; st < 2; ++st)
+          if (n_ab[st] > 0) mbar_wait_bounded(&full_ab[st], (uint32_t)(n_ab[st] - 1) & 1u, P3T_WAIT_LIMIT);
+        if (n_c > 0) mbar_wait_bounded(&full_c, (uint32_t)(n_c - 1) & 1u, P3T_WAIT_LIMIT);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ consumers
+    const int tx = tid % Map::TX, ty = tid / Map::TX;
+    int cty = ty0, ctx = tx0;
+    uint32_t acc[8][TN];
+    for (int t = t_begin; t < t_end; ++t) {
+      const int i = t - t_begin, s = i & 1;
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < TN; ++c) acc[r][c] = Op::INF_WORD;
+      bool bad = !mbar_wait_bounded(&full_ab[s], (uint32_t)(i >> 1) & 1u, P3T_WAIT_LIMIT);
+      if (__any_sync(0xffffffffu, bad)) {
+        if (lane == 0) abort_flag = 1;
+        break;
+      }
+      tile_minplus<Op, BM, BNW, BK, TN>(stA(s), stB(s), acc, ty, tx);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty_ab[s]);
+      const int64_t r0 = (int64_t)cty * BM, c0 = (int64_t)ctx * BNW * Op::EPW;
+      if (RED) {
+        // the previous tile's reduction has finished reading the C buffer
+        bad = i > 0 && !mbar_wait_bounded(&cfree, (uint32_t)(i - 1) & 1u, P3T_WAIT_LIMIT);
+        if (__any_sync(0xffffffffu, bad)) {
+          if (lane == 0) abort_flag = 1;
+          break;
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+          for (int h = 0; h < Map::NH; ++h)
+            *reinterpret_cast<uint4 *>(Cs + Map::row(ty, r) * BNW + Map::wcol(tx, h)) =
+                make_uint4(acc[r][4 * h], acc[r][4 * h + 1], acc[r][4 * h + 2], acc[r][4 * h + 3]);
+        fence_proxy_async_smem();
+      } else {
+        bad = !mbar_wait_bounded(&full_c, (uint32_t)i & 1u, P3T_WAIT_LIMIT);
+        if (__any_sync(0xffffffffu, bad)) {
+          if (lane == 0) abort_flag = 1;
+          break;
+        }
+        const bool interior = interior_of(r0, c0);
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+          for (int h = 0; h < Map::NH; ++h) {
+            uint4 *cp = reinterpret_cast<uint4 *>(Cs + Map::row(ty, r) * BNW + Map::wcol(tx, h));
+            const uint4 v = *cp;
+            acc[r][4 * h + 0] = Op::addmin(acc[r][4 * h + 0], 0u, v.x);
+            acc[r][4 * h + 1] = Op::addmin(acc[r][4 * h + 1], 0u, v.y);
+            acc[r][4 * h + 2] = Op::addmin(acc[r][4 * h + 2], 0u, v.z);
+            acc[r][4 * h + 3] = Op::addmin(acc[r][4 * h + 3], 0u, v.w);
+            if (interior)
+              *cp = make_uint4(acc[r][4 * h], acc[r][4 * h + 1], acc[r][4 * h + 2], acc[r][4 * h + 3]);
+          }
+        if (interior) fence_proxy_async_smem();
+        else store_acc<Op, BM, BNW, TN>(D, ld, n, n, r0, c0, p0, p1, p0, p1, true, acc, ty, tx);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&cdone);
+      step(cty, ctx);
+    }
+  }
+  __syncthreads();
+  if (abort_flag && tid == 0) atomicOr(err, 4);
+}
+
 // ---------------------------------------------------------------- general min-plus
 // C = min(C, A (x) B) for A m x k, B k x n, C m x n (Table 1 MatProd + MatMin).
 template <class Op, int BK>
@@ -595,6 +809,9 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(fw_phase3_tma<Op, BK, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  P3T<BK>::SMEM);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fw_phase3_ws<Op, BK, Op::DTYPE == 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 P3T<BK>::SMEM);
       if (e != cudaSuccess) return e;
     }
   }
@@ -643,7 +860,10 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
       }
       if (tm) tm->after(1, s, sym ? rest * w * w : 2.0 * rest * w * w);
       if (tm) tm->before(2, s);
-      if (tma && variant == 2)
+      if (tma && variant == 3)
+        fw_phase3_ws<Op, BK, Op::DTYPE == 0><<<grid_tma, P3W_THREADS, P3T<BK>::SMEM, s>>>(
+            mA, mB, mC, D, ld, n, p0, p1, tiles_x, tiles_total, err, sym ? 1 : 0, tiles_y);
+      else if (tma && variant == 2)
         fw_phase3_tma<Op, BK, 4><<<grid_tma, TileMap<128, 128, 4>::THREADS, P3T<BK>::SMEM, s>>>(
             mA, mB, mC, D, ld, n, p0, p1, tiles_x, tiles_total, err, sym ? 1 : 0, tiles_y);
       else if (tma)

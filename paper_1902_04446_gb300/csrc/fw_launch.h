@@ -17,15 +17,17 @@ struct PhaseTimer {
 // Tunable shape of the per-round kernels: round width Bk (32 or 64) and the
 // Phase-3 variant: 0 = one CTA per tile, 1 = persistent TMA kernel with 256
 // threads (8 x 8 words each), 2 = persistent TMA kernel with 512 threads
-// (8 x 4 words each).  The TMA variants need a 16-byte addressable matrix and
-// fall back to variant 0 otherwise.
+// (8 x 4 words each), 3 = warp-specialized persistent kernel (8 consumer
+// warps with 8 x 8 words each and a TMA producer warp; int32 results leave by
+// a TMA min-reduction).  The TMA variants need a 16-byte addressable matrix
+// and fall back to variant 0 otherwise.
 // sym: symmetric mode for undirected (symmetric) inputs -- Phase 3 updates
 // only the tiles that touch the upper triangle, both of its operands come from
 // one symmetric panel, and a final pass mirrors the upper triangle into the
 // lower; rowP is the BK x ldT element panel that packed 16-bit needs for it.
 struct RoundConfig {
   int bk = 64;
-  int p3 = 2;  // fastest on GB300 at n = 16384 (profiles/phase3_variants_gmm16k.md)
+  int p3 = 3;  // fastest on GB300 at n = 16384 (profiles/phase3_variants_gmm16k.md)
   bool sym = false;
   void *rowP = nullptr;
 };

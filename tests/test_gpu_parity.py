@@ -308,7 +308,7 @@ def test_gmm16k_auto_equals_int32(H):
 
 # ------------------------------------------------------------------ every round shape
 @pytest.mark.parametrize("block_k", [32, 64])
-@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
 @pytest.mark.parametrize("dt", ["int32", "u16", "fp32"])
 def test_every_round_shape_matches_oracle(lib, block_k, variant, dt):
     n = 777
@@ -326,9 +326,31 @@ def test_every_round_shape_matches_oracle(lib, block_k, variant, dt):
         np.testing.assert_array_equal(D, E)
 
 
+@pytest.mark.parametrize("block_k", [32, 64])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("dt", ["int32", "u16", "fp32"])
+def test_directed_every_phase3_kernel(lib, block_k, variant, dt):
+    """Directed input (general mode) through every Phase-3 kernel.  The int32
+    warp-specialized kernel reduces into the panel rows while other CTAs read
+    them as operands; the result must still be exact."""
+    n = 700
+    s, d, w = er_edges(n, seed=block_k + variant, deg=3.0, wmax=60, directed=True)
+    E = expect_fw(dense_directed(n, s, d, w))
+    with lib.Handle(device=0, block_k=block_k, phase3_variant=variant) as h:
+        if dt == "int32":
+            D = h.solve_t(dt, dev(dense_directed(n, s, d, w))).cpu().numpy().astype(np.int64)
+        elif dt == "u16":
+            D16 = h.solve_t(dt, dev(dense_directed(n, s, d, w, dtype=np.int16, inf=0x7FFF))).cpu().numpy()
+            D = oracle.unpack_u16(D16.view(np.uint16)).astype(np.int64)
+        else:
+            Df = h.solve_t(dt, dev(dense_directed(n, s, d, w, dtype=np.float32, inf=np.inf))).cpu().numpy()
+            D = np.where(np.isinf(Df), INF, Df.astype(np.float64)).astype(np.int64)
+        np.testing.assert_array_equal(D, E)
+
+
 # ------------------------------------------------------------------ symmetric mode
 @pytest.mark.parametrize("symmetric", [0, 1, 2])
-@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
 @pytest.mark.parametrize("dt", ["int32", "u16", "fp32"])
 @pytest.mark.parametrize("n", [65, 300, 1000])
 def test_symmetric_mode_matches_oracle(lib, symmetric, variant, dt, n):
