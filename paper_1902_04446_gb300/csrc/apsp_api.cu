@@ -232,15 +232,14 @@ apsp::RoundConfig config_for(apsp_handle *h, int dtype, int64_t n) {
 // known_sym: D is symmetric by construction (edge-list input).
 apsp_status run_rounds_locked(apsp_handle *h, int dtype, void *D, int64_t n, int64_t ld, cudaStream_t s,
                               bool known_sym = false) {
-  const int64_t bk = apsp::kMaxRoundWidth;
   const int64_t ldT = panel_ld(n);
-  const size_t need = (size_t)bk * ldT * 4;  // panel buffer of 32-bit words
-  cudaError_t e = ensure(&h->colT, &h->colT_bytes, need);
+  apsp::RoundConfig rc = config_for(h, dtype, n);
+  rc.lookahead = rc.p3 == 3;
+  cudaError_t e = ensure(&h->colT, &h->colT_bytes, apsp::panel_buffer_bytes(n, ldT, rc.lookahead));
   if (e != cudaSuccess) {
     h->last_error = std::string("panel workspace: ") + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? APSP_E_NOMEM : APSP_E_CUDA;
   }
-  apsp::RoundConfig rc = config_for(h, dtype, n);
   if (h->cfg.symmetric == 1 || (h->cfg.symmetric == 0 && known_sym)) {
     rc.sym = true;
   } else if (h->cfg.symmetric == 0 && n > 1) {
@@ -258,7 +257,7 @@ apsp_status run_rounds_locked(apsp_handle *h, int dtype, void *D, int64_t n, int
     rc.sym = h->h_status[1] == 0;
   }
   if (rc.sym && dtype == APSP_U16) {
-    e = ensure(&h->rowP, &h->rowP_bytes, (size_t)bk * ldT * 2);
+    e = ensure(&h->rowP, &h->rowP_bytes, apsp::row_panel_bytes(ldT, rc.lookahead));
     if (e != cudaSuccess) {
       h->last_error = std::string("panel workspace: ") + cudaGetErrorString(e);
       return e == cudaErrorMemoryAllocation ? APSP_E_NOMEM : APSP_E_CUDA;
@@ -814,7 +813,7 @@ apsp_status apsp_autotune(apsp_handle *h, int dtype, int64_t n_max, const char *
     void *M = nullptr;
     if ((e = cudaMalloc(&M, (size_t)b * b * es)) != cudaSuccess) return cuda_fail(h, e, "autotune matrix");
     const int64_t ldT = panel_ld(b);
-    if ((e = ensure(&h->colT, &h->colT_bytes, (size_t)apsp::kMaxRoundWidth * ldT * 4)) != cudaSuccess) {
+    if ((e = ensure(&h->colT, &h->colT_bytes, apsp::panel_buffer_bytes(b, ldT, true))) != cudaSuccess) {
       cudaFree(M);
       return cuda_fail(h, e, "autotune panel");
     }
@@ -828,6 +827,7 @@ apsp_status apsp_autotune(apsp_handle *h, int dtype, int64_t n_max, const char *
         apsp::RoundConfig c;
         c.bk = bk;
         c.p3 = var;
+        c.lookahead = var == 3;
         double t_min = 1e30;
         for (int rep = 0; rep < 4; ++rep) {
           apsp::launch_synth(dtype, M, b, b, nullptr);
@@ -1033,8 +1033,10 @@ apsp_status admit_group(apsp_handle *h, const std::vector<Request *> &rs) {
     // (symmetric) matrix takes the symmetric mode, decided by a device check
     const int64_t rn = rs[0]->req.n;
     const int64_t ldT = panel_ld(rn);
-    if (cudaMallocAsync(&g->ws, (size_t)apsp::kMaxRoundWidth * ldT * 4, s) != cudaSuccess) return APSP_E_CUDA;
     apsp::RoundConfig rc = config_for(h, APSP_I32, rn);
+    rc.lookahead = rc.p3 == 3;
+    if (cudaMallocAsync(&g->ws, apsp::panel_buffer_bytes(rn, ldT, rc.lookahead), s) != cudaSuccess)
+      return APSP_E_CUDA;
     if (h->cfg.symmetric != 2) {
       int flag = 0;
       int *dflag = g->status + 1;  // reused below as the wait-error word (reset first)
@@ -1092,7 +1094,7 @@ void worker_loop(apsp_handle *h) {
         Request *r = h->reqs[h->queue.front()].get();
         const bool large = r->req.n >= kLargeN;
         if (large && !rs.empty()) break;  // a large request starts its own group
-        const int64_t b = r->bytes + panel_bytes(r->req.n) + (large ? 64 * panel_ld(r->req.n) * 4 : 0);
+        const int64_t b = r->bytes + panel_bytes(r->req.n) + (large ? (int64_t)apsp::panel_buffer_bytes(r->req.n, panel_ld(r->req.n), true) : 0);
         if (h->used + add + b > h->budget) break;  // wait for memory to free up
         h->queue.pop_front();
         r->transient = b - r->bytes;

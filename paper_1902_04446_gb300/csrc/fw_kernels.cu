@@ -365,6 +365,38 @@ __global__ void __launch_bounds__(TileMap<128, 128, TN>::THREADS, 1)
 // ORs 4 into *err.
 constexpr int P3W_THREADS = 9 * 32;
 
+// int32 results leave by a TMA min-reduction over a tensor map that ends at
+// n4 = n rounded down to 4 elements (16 bytes): at the tensor's x edge the
+// reduction writes whole 16-byte units, so the last n - n4 columns are merged
+// here instead, element by element, by the threads that own them (the tile's
+// other elements are never touched by this).
+__device__ __forceinline__ int64_t red_cols(int64_t n) { return n & ~(int64_t)3; }
+
+template <int BM, int BNW, int TN>
+__device__ __forceinline__ void red_tail_store(int32_t *D, int64_t ld, int64_t n, int64_t r0, int64_t c0,
+                                               const uint32_t (&acc)[8][TN], int ty, int tx) {
+  using Map = TileMap<BM, BNW, TN>;
+  const int64_t n4 = red_cols(n);
+#pragma unroll
+  for (int h = 0; h < Map::NH; ++h) {
+    const int64_t cw = c0 + Map::wcol(tx, h);
+    if (cw + 4 <= n4 || cw >= n) continue;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int64_t row = r0 + Map::row(ty, r);
+      if (row >= n) continue;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int64_t c = cw + e;
+        if (c >= n4 && c < n) {
+          int32_t *p = D + row * ld + c;
+          *p = (int32_t)OpI32::addmin(acc[r][4 * h + e], 0u, (uint32_t)*p);
+        }
+      }
+    }
+  }
+}
+
 template <class Op, int BK, bool RED>
 __global__ void __launch_bounds__(P3W_THREADS, 1)
     fw_phase3_ws(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
@@ -472,9 +504,11 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
         }
         const int r0 = cty * BM, c0 = ctx * BNW * Op::EPW;
         if (RED) {
-          tma_reduce_min_2d(&mapC, Cs, c0, r0);
-          bulk_commit();
-          bulk_wait_read_all();
+          if (c0 < red_cols(n)) {  // mapC ends at red_cols(n) in this mode
+            tma_reduce_min_2d(&mapC, Cs, c0, r0);
+            bulk_commit();
+            bulk_wait_read_all();
+          }
           mbar_arrive(&cfree);
         } else if (interior_of(r0, c0)) {
           tma_store_2d(&mapC, Cs, c0, r0);
@@ -526,6 +560,9 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
             *reinterpret_cast<uint4 *>(Cs + Map::row(ty, r) * BNW + Map::wcol(tx, h)) =
                 make_uint4(acc[r][4 * h], acc[r][4 * h + 1], acc[r][4 * h + 2], acc[r][4 * h + 3]);
         fence_proxy_async_smem();
+        if constexpr (Op::DTYPE == 0)
+          if (c0 + BNW > red_cols(n) && c0 < n)
+            red_tail_store<BM, BNW, TN>(reinterpret_cast<int32_t *>(D), ld, n, r0, c0, acc, ty, tx);
       } else {
         bad = !mbar_wait_bounded(&full_c, (uint32_t)i & 1u, P3T_WAIT_LIMIT);
         if (__any_sync(0xffffffffu, bad)) {
@@ -552,6 +589,529 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&cdone);
       step(cty, ctx);
+    }
+  }
+  __syncthreads();
+  if (abort_flag && tid == 0) atomicOr(err, 4);
+}
+
+// ---------------------------------------------------------------- lookahead rounds
+// Round k's Phase-3 launch also runs round k+1's Phase 1, Phase 2 and (in
+// symmetric mode) panel publication, so that the next round's diagonal
+// closure and panels are ready when its Phase 3 starts instead of running as
+// near-idle launches in between (the diagonal blocks are the critical path of
+// the method, Sec. 4.4, Fig. 2).
+//
+// Work items are taken from a device counter in this order:
+//   the Phase-3 tiles that the next round's tasks read or write (tile row R'
+//   and tile column C' of the next diagonal block: "priority" tiles), the
+//   rest of the tiles, with the next round's tasks inserted into the stream:
+//   P1 after b1 tiles, the Phase-2 chunks after b2, the publication tasks
+//   after b3.
+// P1 waits until every priority tile is written, the Phase-2 chunks wait for
+// P1, the publication tasks for every Phase-2 chunk; each only waits for items
+// with smaller ids, which running CTAs have already taken, so the launch
+// always makes progress.  The next round's panels go to the other half of the
+// double panel buffer, so this round's operands are never overwritten.
+//
+// A next-round task runs on the 256 consumer threads and uses both stage
+// buffers (the producer takes no new item until it is done).
+template <class Op>
+struct RoundLA {
+  int64_t p0n, p1n;           // the next round's vertices [p0n, p1n)
+  uint32_t *colTn;            // the next round's panel (BK x ldT words)
+  typename Op::elem *rowPn;   // the next round's element panel (symmetric packed 16-bit), or nullptr
+  int *cnt;                   // this launch's counters: items taken, priority tiles done, P1 done, P2 done
+  int prio_ty, prio_tx;       // tile row R' and tile column C'
+  int row_x0;                 // priority tiles in row R': x in [row_x0, tiles_x)
+  int col_y1;                 // priority tiles in column C': y in [0, col_y1), y != R'
+  int n_prio;
+  int b1, b2, b3;             // positions of the next-round tasks in the tile stream
+  int n_p2row, p2_row_first, n_p2col, n_fin;
+  int64_t band_start_n, band_end_n;
+  int vec;
+};
+
+// Phase-2 shape for 256 threads (the consumer warps).
+template <class Op, int BK>
+struct LaP2 {
+  static constexpr int TN = 4;
+  static constexpr int ROW_BNW = 8192 / BK;             // 64 x 128 words for BK = 64
+  static constexpr int COL_BNW = BK / Op::EPW;
+  static constexpr int COL_BM = 8192 * Op::EPW / BK;    // 128 rows (256 for packed 16-bit) for BK = 64
+  static_assert(TileMap<BK, ROW_BNW, TN>::THREADS == 256, "row chunk");
+  static_assert(TileMap<COL_BM, COL_BNW, TN>::THREADS == 256, "column chunk");
+  static constexpr int SMEM = (BK * BK + BK * ROW_BNW) > (BK * COL_BM + BK * COL_BNW) ? (BK * BK + BK * ROW_BNW) * 4
+                                                                                     : (BK * COL_BM + BK * COL_BNW) * 4;
+};
+// Lookahead rounds are built for round width 64 (the tasks of width 32 do not
+// fit the 256-thread chunk shapes and the two 32 KB stage buffers).
+template <int BK>
+constexpr bool kLookaheadWidth = BK == 64;
+
+constexpr int LA_TILE = 0, LA_P1 = 1, LA_P2 = 2, LA_FIN = 3, LA_END = -1, LA_SKIP = 5;
+constexpr int LA_FIN_ROWS = 8;  // panel rows per publication task (packed 16-bit element panel)
+
+// Consumer-warp barrier of the next-round tasks: an mbarrier that each of the 8
+// consumer warps arrives on once per sync, with a bounded wait.  Unlike a
+// hardware named barrier it cannot hang when a warp has left after a timeout:
+// the others give up, set la_grp_abort, and every later sync returns at once
+// (the launch then reports the timeout).
+__shared__ __align__(8) uint64_t la_grp_bar;
+__shared__ uint32_t la_grp_par[8];  // phase parity of each consumer warp's next sync
+__shared__ int la_grp_abort;
+
+struct GroupBar {
+  __device__ __forceinline__ static void sync() {
+    __syncwarp();
+    if (*reinterpret_cast<volatile int *>(&la_grp_abort)) return;
+    const int w = threadIdx.x >> 5;
+    const uint32_t par = la_grp_par[w];
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&la_grp_bar);
+    const bool ok = mbar_wait_bounded(&la_grp_bar, par, P3T_WAIT_LIMIT);
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) la_grp_par[w] = par ^ 1u;
+    if (!ok) la_grp_abort = 1;
+    __syncwarp();
+  }
+};
+
+template <class Op, int BK>
+__device__ __noinline__ void la_task_p1(typename Op::elem *D, int64_t ld, int64_t n, int64_t p0, uint32_t *colT,
+                                        int64_t ldT, typename Op::elem *rowP, uint32_t *smem, int tid) {
+  auto &sm = *reinterpret_cast<P1Smem<Op, BK> *>(smem);
+  phase1_body<Op, BK, 256, true, GroupBar>(D, ld, n, p0, colT, ldT, sm, tid, rowP);
+}
+
+template <class Op, int BK>
+__device__ __noinline__ void la_task_p2(typename Op::elem *D, int64_t ld, int64_t n, int64_t p0, int64_t p1,
+                                        uint32_t *colT, int64_t ldT, int idx, int n_row, int row_first, bool vec,
+                                        SymPanel<Op> sp, bool sym, uint32_t *smem, int tid) {
+  using F = LaP2<Op, BK>;
+  const SymPanel<Op> *spp = sym ? &sp : nullptr;
+  if (idx < n_row)
+    p2_row_task<Op, BK, F::ROW_BNW, 256, true, F::TN, GroupBar>(
+        D, ld, n, p0, p1, colT, ldT, (int64_t)(row_first + idx) * F::ROW_BNW * Op::EPW, vec, smem, tid, spp);
+  else
+    p2_col_task<Op, BK, F::COL_BM, 256, true, F::TN, GroupBar>(D, ld, n, p0, p1, colT, ldT,
+                                                                   (int64_t)(idx - n_row) * F::COL_BM, vec, smem,
+                                                                   tid, spp);
+}
+
+// Symmetric-mode publication (the panel_finalize pass) for panel rows [t0, t1):
+// 16-byte panel loads, four per thread in flight (p0 and band_start are
+// multiples of 4, and so is every x visited).
+template <class Op>
+__device__ __noinline__ void la_task_fin(typename Op::elem *D, int64_t ld, int64_t n, int64_t p0,
+                                         const uint32_t *colT, int64_t ldT, typename Op::elem *rowP,
+                                         int64_t band_start, int t0, int t1, int tid) {
+  using E = typename Op::elem;
+  constexpr int U = 4, STEP = 4 * 256;
+  const int64_t x0 = rowP ? 0 : band_start;
+  for (int t = t0; t < t1; ++t) {
+    const int64_t row = p0 + t;
+    const uint32_t *src = colT + (int64_t)t * ldT;
+    for (int64_t xb = x0 + 4 * tid; xb < p0; xb += (int64_t)U * STEP) {
+      uint4 v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t x = xb + (int64_t)u * STEP;
+        v[u] = x < p0 ? __ldcg(reinterpret_cast<const uint4 *>(src + x)) : make_uint4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t x = xb + (int64_t)u * STEP;
+        if (x >= p0) continue;
+        const uint32_t w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+        E e[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) e[j] = bits_elem<Op>(Op::EPW == 2 ? (w[j] & 0xFFFFu) : w[j]);
+        if constexpr (Op::EPW == 2) {
+          if (rowP)
+            *reinterpret_cast<uint2 *>(rowP + (int64_t)t * ldT + x) =
+                make_uint2((uint32_t)e[0] | ((uint32_t)e[1] << 16), (uint32_t)e[2] | ((uint32_t)e[3] << 16));
+        }
+        if (row < n && x + 4 > band_start) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (x + j >= band_start) D[row * ld + x + j] = e[j];
+        }
+      }
+    }
+  }
+}
+
+template <class Op, int BK, bool RED>
+__global__ void __launch_bounds__(P3W_THREADS, 1)
+    fw_round_la(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                const __grid_constant__ CUtensorMap mapC, typename Op::elem *__restrict__ D, int64_t ld, int64_t n,
+                int64_t p0, int64_t p1, int tiles_x, int tiles_y, int tiles_total, int *err, int sym, int64_t ldT,
+                const RoundLA<Op> la) {
+  constexpr int BM = 128, BNW = 128, TN = 8;
+  using Map = TileMap<BM, BNW, TN>;
+  constexpr int NCW = Map::THREADS / 32;
+  static_assert(Map::THREADS == 256 && Map::THREADS + 32 == P3W_THREADS, "8 consumer warps + producer");
+  constexpr int STAGE = P3T<BK>::STAGE_BYTES;
+  static_assert(LaP2<Op, BK>::SMEM <= 2 * STAGE && (int)sizeof(P1Smem<Op, BK>) <= 2 * STAGE, "task memory");
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_ab[2], empty_ab[2], full_c, cdone, cfree;
+  __shared__ int slot_kind[2], slot_info[2];
+  __shared__ int abort_flag;
+  uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  auto stA = [&](int s) { return reinterpret_cast<uint32_t *>(base + s * STAGE); };
+  auto stB = [&](int s) { return reinterpret_cast<uint32_t *>(base + s * STAGE) + BK * BM; };
+  uint32_t *Cs = reinterpret_cast<uint32_t *>(base + 2 * STAGE);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&full_ab[i], 1);
+      mbar_init(&empty_ab[i], NCW);
+    }
+    mbar_init(&full_c, 1);
+    mbar_init(&cdone, NCW);
+    mbar_init(&cfree, 1);
+    mbar_init(&la_grp_bar, NCW);
+    for (int w = 0; w < NCW; ++w) la_grp_par[w] = 0;
+    la_grp_abort = 0;
+    fence_barrier_init();
+    prefetch_tensormap(&mapA);
+    prefetch_tensormap(&mapB);
+    prefetch_tensormap(&mapC);
+    abort_flag = 0;
+  }
+  __syncthreads();
+  // int32: a next-round task runs in the C buffer (free once the previous
+  // tile's reduction has read it), so A/B prefetching goes on; otherwise it
+  // runs in the two stage buffers and the producer takes no item meanwhile
+  constexpr bool TASK_IN_C = RED && LaP2<Op, BK>::SMEM <= P3T_C_BYTES && (int)sizeof(P1Smem<Op, BK>) <= P3T_C_BYTES;
+  auto interior_of = [&](int64_t r0, int64_t c0) {
+    return r0 + BM <= n && c0 + BNW * Op::EPW <= n && (r0 + BM <= p0 || r0 >= p1) &&
+           (c0 + BNW * Op::EPW <= p0 || c0 >= p1);
+  };
+  auto is_prio = [&](int y, int x) {
+    return (y == la.prio_ty && x >= la.row_x0) || (x == la.prio_tx && y < la.col_y1);
+  };
+
+  if (warp == NCW) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      const int len_t = la.n_prio + tiles_total;
+      const int o1 = la.b1, o2 = la.b2 + 1, o3 = la.b3 + 1 + la.n_p2row + la.n_p2col;
+      const int n_p2 = la.n_p2row + la.n_p2col;
+      const int total = len_t + 1 + n_p2 + la.n_fin;
+      // tile-stream position -> packed tile (ty << 16 | tx), or -1 for a
+      // priority tile met again in the full list
+      auto stream_tile = [&](int j) -> int {
+        int y, x;
+        if (j < la.n_prio) {
+          const int nr = tiles_x - la.row_x0;
+          if (j < nr) {
+            y = la.prio_ty;
+            x = la.row_x0 + j;
+          } else {
+            y = j - nr;
+            if (y >= la.prio_ty) ++y;  // column C' without row R'
+            x = la.prio_tx;
+          }
+          return (y << 16) | x;
+        }
+        const int idx = j - la.n_prio;
+        if (!sym) {
+          y = idx / tiles_x;
+          x = idx % tiles_x;
+        } else {
+          int lo = 0, hi = tiles_y - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sym_prefix(mid, tiles_x, Op::EPW) <= idx) lo = mid;
+            else hi = mid - 1;
+          }
+          y = lo;
+          x = lo / Op::EPW + (int)(idx - sym_prefix(lo, tiles_x, Op::EPW));
+        }
+        return is_prio(y, x) ? -1 : ((y << 16) | x);
+      };
+      auto decode = [&](int item, int &kind, int &info) {
+        int j;
+        if (item >= total) {
+          kind = LA_END;
+          info = 0;
+          return;
+        }
+        if (item < o1) j = item;
+        else if (item == o1) { kind = LA_P1; info = 0; return; }
+        else if (item < o2) j = item - 1;
+        else if (item < o2 + n_p2) { kind = LA_P2; info = item - o2; return; }
+        else if (item < o3) j = item - 1 - n_p2;
+        else if (item < o3 + la.n_fin) { kind = LA_FIN; info = item - o3; return; }
+        else j = item - 1 - n_p2 - la.n_fin;
+        const int tpk = stream_tile(j);
+        kind = tpk < 0 ? LA_SKIP : LA_TILE;
+        info = tpk;
+      };
+      int rk[4], rt[4];  // kind and packed tile of the last four slots
+      int claimed = 0, hold = -1, c_next = 0;
+      int n_ab[2] = {0, 0}, n_c = 0;
+      bool stop = false, ok = true, cs_free = true;
+      // items already taken and not yet used, in increasing order (the launch
+      // starts by taking two at once); a CTA uses its items in increasing order
+      int q0 = -1, q1 = -1;
+      auto next_item = [&]() {
+        if (q0 < 0) return atomicAdd(la.cnt + 0, 1);
+        const int r = q0;
+        q0 = q1;
+        q1 = -1;
+        return r;
+      };
+      auto claim = [&]() {
+        const int slot = claimed, s = slot & 1;
+        int kind, info;
+        do {
+          decode(next_item(), kind, info);
+        } while (kind == LA_SKIP);
+        slot_kind[s] = kind;
+        slot_info[s] = info;
+        rk[slot & 3] = kind;
+        rt[slot & 3] = info;
+        if (kind == LA_TILE) {
+          mbar_arrive_expect_tx(&full_ab[s], STAGE);
+          tma_load_2d(stA(s), &mapA, &full_ab[s], (info >> 16) * BM, 0);
+          tma_load_2d(stB(s), &mapB, &full_ab[s], (info & 0xFFFF) * BNW * Op::EPW, sym ? 0 : (int)p0);
+        } else {
+          mbar_arrive(&full_ab[s]);  // a task or the end: no data
+        }
+        if (s == 0) ++n_ab[0];
+        else ++n_ab[1];
+        if (kind == LA_END) stop = true;
+        else if (kind != LA_TILE && !TASK_IN_C) hold = slot;
+        ++claimed;
+      };
+      auto issue_c = [&]() {  // !RED: the next tile's C once the C buffer is free
+        while (c_next < claimed && rk[c_next & 3] != LA_TILE) ++c_next;
+        if (!RED && cs_free && c_next < claimed) {
+          const int pk = rt[c_next & 3];
+          mbar_arrive_expect_tx(&full_c, P3T_C_BYTES);
+          tma_load_2d(Cs, &mapC, &full_c, (pk & 0xFFFF) * BNW * Op::EPW, (pk >> 16) * BM);
+          ++n_c;
+          cs_free = false;
+          ++c_next;
+        }
+      };
+      q0 = atomicAdd(la.cnt + 0, 2);
+      q1 = q0 + 1;
+      claim();
+      if (!stop && hold < 0) claim();
+      if (!RED) issue_c();
+      for (int i = 0;; ++i) {
+        const int kind = rk[i & 3], s = i & 1;
+        if (kind == LA_END) break;
+        if (!mbar_wait_bounded(&empty_ab[s], (uint32_t)(i >> 1) & 1u, P3T_WAIT_LIMIT)) {
+          ok = false;
+          break;
+        }
+        if (!stop && hold < 0 && claimed < i + 3) {
+          claim();
+          if (!RED) issue_c();
+        }
+        if (!mbar_wait_bounded(&cdone, (uint32_t)i & 1u, P3T_WAIT_LIMIT)) {
+          ok = false;
+          break;
+        }
+        if (kind == LA_TILE) {
+          const int pk = rt[i & 3];
+          const int ty_ = pk >> 16, tx_ = pk & 0xFFFF;
+          const int r0 = ty_ * BM, c0 = tx_ * BNW * Op::EPW;
+          const bool prio = is_prio(ty_, tx_);
+          if (RED) {
+            if (c0 < red_cols(n)) {  // mapC ends at red_cols(n) in this mode
+              tma_reduce_min_2d(&mapC, Cs, c0, r0);
+              bulk_commit();
+              if (prio) {
+                bulk_wait_all();
+                fence_proxy_async_global();
+              } else {
+                bulk_wait_read_all();
+              }
+            }
+            mbar_arrive(&cfree);
+          } else {
+            if (interior_of(r0, c0)) {
+              tma_store_2d(&mapC, Cs, c0, r0);
+              bulk_commit();
+              if (prio) {
+                bulk_wait_all();
+                fence_proxy_async_global();
+              } else {
+                bulk_wait_read_all();
+              }
+            }
+            cs_free = true;
+            issue_c();
+          }
+          if (prio) {
+            __threadfence();
+            atomicAdd(la.cnt + 1, 1);
+          }
+        } else if (!TASK_IN_C) {
+          // a next-round task finished: both stage buffers are free again
+          hold = -1;
+          while (!stop && hold < 0 && claimed < i + 3) claim();
+          if (!RED) issue_c();
+        }
+      }
+      bulk_wait_all();
+      if (!ok) {
+        abort_flag = 1;
+        for (int st = 0; st < 2; ++st)
+          if (n_ab[st] > 0) mbar_wait_bounded(&full_ab[st], (uint32_t)(n_ab[st] - 1) & 1u, P3T_WAIT_LIMIT);
+        if (n_c > 0) mbar_wait_bounded(&full_c, (uint32_t)(n_c - 1) & 1u, P3T_WAIT_LIMIT);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ consumers
+    const int tx = tid % Map::TX, ty = tid / Map::TX;
+    const int n_p2 = la.n_p2row + la.n_p2col;
+    uint32_t acc[8][TN];
+    int ct = 0;  // tiles done by this CTA
+    for (int i = 0;; ++i) {
+      const int s = i & 1;
+      // warps go on independently; a warp that gives up leaves, and the
+      // next-round tasks synchronize only through bounded waits (GroupBar)
+      const bool bad = !mbar_wait_bounded(&full_ab[s], (uint32_t)(i >> 1) & 1u, P3T_WAIT_LIMIT);
+      if (__any_sync(0xffffffffu, bad)) {
+        if (lane == 0) abort_flag = 1;
+        break;
+      }
+      const int kind = slot_kind[s], info = slot_info[s];
+      if (kind == LA_END) break;
+      if (kind == LA_TILE) {
+        const int cty = info >> 16, ctx = info & 0xFFFF;
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+          for (int c = 0; c < TN; ++c) acc[r][c] = Op::INF_WORD;
+        tile_minplus<Op, BM, BNW, BK, TN>(stA(s), stB(s), acc, ty, tx);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty_ab[s]);
+        const int64_t r0 = (int64_t)cty * BM, c0 = (int64_t)ctx * BNW * Op::EPW;
+        bool ebad;
+        if (RED) {
+          ebad = ct > 0 && !mbar_wait_bounded(&cfree, (uint32_t)(ct - 1) & 1u, P3T_WAIT_LIMIT);
+          if (!__any_sync(0xffffffffu, ebad)) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+              for (int h = 0; h < Map::NH; ++h)
+                *reinterpret_cast<uint4 *>(Cs + Map::row(ty, r) * BNW + Map::wcol(tx, h)) =
+                    make_uint4(acc[r][4 * h], acc[r][4 * h + 1], acc[r][4 * h + 2], acc[r][4 * h + 3]);
+            fence_proxy_async_smem();
+            if constexpr (Op::DTYPE == 0)
+              if (c0 + BNW > red_cols(n) && c0 < n)
+                red_tail_store<BM, BNW, TN>(reinterpret_cast<int32_t *>(D), ld, n, r0, c0, acc, ty, tx);
+          }
+        } else {
+          ebad = !mbar_wait_bounded(&full_c, (uint32_t)ct & 1u, P3T_WAIT_LIMIT);
+          if (!__any_sync(0xffffffffu, ebad)) {
+            const bool interior = interior_of(r0, c0);
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+              for (int h = 0; h < Map::NH; ++h) {
+                uint4 *cp = reinterpret_cast<uint4 *>(Cs + Map::row(ty, r) * BNW + Map::wcol(tx, h));
+                const uint4 v = *cp;
+                acc[r][4 * h + 0] = Op::addmin(acc[r][4 * h + 0], 0u, v.x);
+                acc[r][4 * h + 1] = Op::addmin(acc[r][4 * h + 1], 0u, v.y);
+                acc[r][4 * h + 2] = Op::addmin(acc[r][4 * h + 2], 0u, v.z);
+                acc[r][4 * h + 3] = Op::addmin(acc[r][4 * h + 3], 0u, v.w);
+                if (interior)
+                  *cp = make_uint4(acc[r][4 * h], acc[r][4 * h + 1], acc[r][4 * h + 2], acc[r][4 * h + 3]);
+              }
+            if (interior) fence_proxy_async_smem();
+            else store_acc<Op, BM, BNW, TN>(D, ld, n, n, r0, c0, p0, p1, p0, p1, true, acc, ty, tx);
+          }
+        }
+        ++ct;
+        if (__any_sync(0xffffffffu, ebad)) {
+          if (lane == 0) abort_flag = 1;
+          break;
+        }
+      } else {
+        // a next-round task
+        if (TASK_IN_C) {
+          // the stage is not used: hand it back at once; the task needs the
+          // C buffer, free once the previous tile's reduction has read it
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&empty_ab[s]);
+          const bool cb = ct > 0 && !mbar_wait_bounded(&cfree, (uint32_t)(ct - 1) & 1u, P3T_WAIT_LIMIT);
+          if (__any_sync(0xffffffffu, cb)) {
+            if (lane == 0) abort_flag = 1;
+            break;
+          }
+        }
+        int *dep = nullptr;
+        int target = 0;
+        if (kind == LA_P1) {
+          dep = la.cnt + 1;
+          target = la.n_prio;
+        } else if (kind == LA_P2) {
+          dep = la.cnt + 2;
+          target = 1;
+        } else {
+          dep = la.cnt + 3;
+          target = n_p2;
+        }
+        // each warp waits (bounded) for the task's inputs
+        bool dbad = false;
+        if (lane == 0) {
+          uint32_t spins = 0;
+          while (*reinterpret_cast<volatile int *>(dep) < target) {
+            if (++spins > P3T_WAIT_LIMIT / 4) {
+              dbad = true;
+              break;
+            }
+            __nanosleep(64);
+          }
+          __threadfence();
+        }
+        if (__any_sync(0xffffffffu, dbad)) {
+          la_grp_abort = 1;
+          if (lane == 0) abort_flag = 1;
+          break;
+        }
+        GroupBar::sync();  // every consumer warp is here: the task's memory is no longer read
+        if (*reinterpret_cast<volatile int *>(&la_grp_abort)) {
+          if (lane == 0) abort_flag = 1;
+          break;
+        }
+        uint32_t *tsm = TASK_IN_C ? Cs : reinterpret_cast<uint32_t *>(base);
+        if (kind == LA_P1) {
+          la_task_p1<Op, BK>(D, ld, n, la.p0n, la.colTn, ldT, la.rowPn, tsm, tid);
+        } else if (kind == LA_P2) {
+          la_task_p2<Op, BK>(D, ld, n, la.p0n, la.p1n, la.colTn, ldT, info, la.n_p2row, la.p2_row_first,
+                             la.vec != 0, SymPanel<Op>{la.rowPn, la.band_end_n}, sym != 0, tsm, tid);
+        } else {
+          const int rows = la.rowPn ? LA_FIN_ROWS : BK;
+          la_task_fin<Op>(D, ld, n, la.p0n, la.colTn, ldT, la.rowPn, la.band_start_n, info * rows,
+                          min((int)(la.p1n - la.p0n), (info + 1) * rows), tid);
+        }
+        fence_proxy_async_smem();  // the task's shared memory is refilled by TMA next
+        GroupBar::sync();          // every consumer's writes of the task are done
+        if (*reinterpret_cast<volatile int *>(&la_grp_abort)) {
+          if (lane == 0) abort_flag = 1;
+          break;
+        }
+        if (tid == 0 && kind != LA_FIN) {
+          __threadfence();
+          atomicAdd(la.cnt + (kind == LA_P1 ? 2 : 3), 1);
+        }
+        if (!TASK_IN_C) {
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&empty_ab[s]);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&cdone);
     }
   }
   __syncthreads();
@@ -769,17 +1329,28 @@ static inline unsigned grid_cols(int64_t n, int threads) {
 template <class Op, int BK>
 static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int64_t ldT, bool vec, int variant,
                                cudaStream_t s, int64_t *launches, PhaseTimer *tm, int *wait_err, bool sym,
-                               void *rowPv) {
+                               void *rowPv, bool lookahead) {
   const bool use_tma = variant != 0;
   using Elem = typename Op::elem;
+  using E = Elem;
+  E *D = static_cast<E *>(Dv);
+  const int64_t q = (n + BK - 1) / BK;
+  // lookahead rounds (the warp-specialized Phase 3 with the TMA path and more
+  // than one round): two panel buffers used by round parity, then 4 counters
+  // per round
+  bool la_on = kLookaheadWidth<BK> && lookahead && use_tma && vec && variant == 3 && q > 1;
+  uint32_t *colTb[2], *colT = static_cast<uint32_t *>(colTv);
+  colTb[0] = colT;
+  colTb[1] = la_on ? colT + (int64_t)kMaxRoundWidth * ldT : colT;
+  int *cnt = la_on ? reinterpret_cast<int *>(colT + 2 * (int64_t)kMaxRoundWidth * ldT) : nullptr;
   // symmetric mode: the element panel (B operand of Phase 3) is colT itself
   // for 32-bit elements, a separate BK x ldT buffer for packed 16-bit
   Elem *rowP = sym ? (Op::EPW == 2 ? static_cast<Elem *>(rowPv) : nullptr) : nullptr;
-  const Elem *symB = sym ? (Op::EPW == 2 ? rowP : reinterpret_cast<const Elem *>(colTv)) : nullptr;
   if (sym && Op::EPW == 2 && !rowP) return cudaErrorInvalidValue;
-  using E = typename Op::elem;
-  E *D = static_cast<E *>(Dv);
-  uint32_t *colT = static_cast<uint32_t *>(colTv);
+  Elem *rowPb[2] = {rowP, (la_on && rowP) ? rowP + (int64_t)kMaxRoundWidth * ldT : rowP};
+  auto symB_of = [&](int b) -> const Elem * {
+    return sym ? (Op::EPW == 2 ? rowPb[b] : reinterpret_cast<const Elem *>(colTb[b])) : nullptr;
+  };
   using C2 = P2Cfg<Op, BK>;
   using C3 = P3Cfg<Op>;
   constexpr int SMEM3 = (BK * C3::BM + BK * C3::BNW) * 4;
@@ -789,19 +1360,25 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
   e = cudaFuncSetAttribute(fw_phase3<Op, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM3);
   if (e != cudaSuccess) return e;
   // persistent TMA Phase 3 when D is 16-byte addressable (otherwise the
-  // per-tile kernel with scalar edge handling)
-  CUtensorMap mA, mB, mC;
+  // per-tile kernel with scalar edge handling); A (and B in symmetric mode)
+  // maps for each panel buffer
+  CUtensorMap mA[2], mB[2], mC;
   bool tma = vec && use_tma;
   int *err = nullptr;
   if (tma) {
     constexpr CUtensorMapDataType dt = Op::DTYPE == 1   ? CU_TENSOR_MAP_DATA_TYPE_UINT16
                                        : Op::DTYPE == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                                         : CU_TENSOR_MAP_DATA_TYPE_INT32;
-    tma = make_map(&mA, CU_TENSOR_MAP_DATA_TYPE_UINT32, colT, (uint64_t)ldT, (uint64_t)BK, (uint64_t)ldT * 4, 128,
-                   BK) &&
-          (sym ? make_map(&mB, dt, symB, (uint64_t)ldT, (uint64_t)BK, (uint64_t)ldT * sizeof(E), 128 * Op::EPW, BK)
-               : make_map(&mB, dt, D, (uint64_t)n, (uint64_t)n, (uint64_t)ld * sizeof(E), 128 * Op::EPW, BK)) &&
-          make_map(&mC, dt, D, (uint64_t)n, (uint64_t)n, (uint64_t)ld * sizeof(E), 128 * Op::EPW, 128);
+    for (int b = 0; b < (la_on ? 2 : 1) && tma; ++b)
+      tma = make_map(&mA[b], CU_TENSOR_MAP_DATA_TYPE_UINT32, colTb[b], (uint64_t)ldT, (uint64_t)BK,
+                     (uint64_t)ldT * 4, 128, BK) &&
+            (sym ? make_map(&mB[b], dt, symB_of(b), (uint64_t)ldT, (uint64_t)BK, (uint64_t)ldT * sizeof(E),
+                            128 * Op::EPW, BK)
+                 : make_map(&mB[b], dt, D, (uint64_t)n, (uint64_t)n, (uint64_t)ld * sizeof(E), 128 * Op::EPW, BK));
+    // int32 (TMA min-reduction epilogue of variant 3): x extent red_cols(n)
+    const uint64_t cx = (Op::DTYPE == 0 && variant == 3) ? (uint64_t)(n & ~(int64_t)3) : (uint64_t)n;
+    tma = tma && cx > 0 &&
+          make_map(&mC, dt, D, cx, (uint64_t)n, (uint64_t)ld * sizeof(E), 128 * Op::EPW, 128);
     err = tma ? (wait_err ? wait_err : error_word()) : nullptr;
     tma = tma && err != nullptr;
     if (tma) {
@@ -812,8 +1389,17 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(fw_phase3_ws<Op, BK, Op::DTYPE == 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  P3T<BK>::SMEM);
+      if constexpr (kLookaheadWidth<BK>)
+        if (e == cudaSuccess && la_on)
+          e = cudaFuncSetAttribute(fw_round_la<Op, BK, Op::DTYPE == 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   P3T<BK>::SMEM);
       if (e != cudaSuccess) return e;
     }
+  }
+  la_on = la_on && tma;
+  if (!la_on) {
+    colTb[1] = colT;
+    rowPb[1] = rowP;
   }
   const int tiles_x = (int)((n + 128 * Op::EPW - 1) / (128 * Op::EPW));
   const int tiles_y = (int)((n + 127) / 128);
@@ -823,59 +1409,137 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
     for (int y = 0; y < tiles_y; ++y) tiles_total += tiles_x - std::min(tiles_x, y / Op::EPW);
   }
   const int grid_tma = std::min(sm_count(), tiles_total);
-  const int64_t q = (n + BK - 1) / BK;
   const int nrow = (int)((n + C2::ROW_BNW * Op::EPW - 1) / (C2::ROW_BNW * Op::EPW));
   const int ncol = (int)((n + C2::COL_BM - 1) / C2::COL_BM);
   const dim3 g3((unsigned)((n + C3::BNW * Op::EPW - 1) / (C3::BNW * Op::EPW)), (unsigned)((n + C3::BM - 1) / C3::BM));
-  for (int64_t k = 0; k < q; ++k) {
-    const int64_t p0 = k * BK;
-    const int64_t p1 = (p0 + BK < n) ? p0 + BK : n;
+  auto span = [&](int64_t k, int64_t &p0, int64_t &p1) {
+    p0 = k * BK;
+    p1 = (p0 + BK < n) ? p0 + BK : n;
+  };
+  // Phase 1 and Phase 2 of round k as their own launches, into panel cT / rP
+  auto panels = [&](int64_t k, uint32_t *cT, Elem *rP) {
+    int64_t p0, p1;
+    span(k, p0, p1);
     const double w = (double)(p1 - p0), rest = (double)(n - (p1 - p0));
     if (tm) tm->before(0, s);
-    if (sym && rowP)
-      fw_phase1_sym<Op, BK><<<1, P1_THREADS, 0, s>>>(D, ld, n, p0, colT, ldT, rowP);
+    if (sym && rP)
+      fw_phase1_sym<Op, BK><<<1, P1_THREADS, 0, s>>>(D, ld, n, p0, cT, ldT, rP);
     else
-      fw_phase1<Op, BK><<<1, P1_THREADS, 0, s>>>(D, ld, n, p0, colT, ldT);
+      fw_phase1<Op, BK><<<1, P1_THREADS, 0, s>>>(D, ld, n, p0, cT, ldT);
+    if (launches) *launches += 1;
     if (tm) tm->after(0, s, w * w * w);
-    if (q > 1) {
-      if (tm) tm->before(1, s);
-      SymPanel<Op> sp{rowP, (p0 / (128 * Op::EPW)) * (128 * Op::EPW) + 128 * Op::EPW};
-      int r_first = 0, r_count = nrow, c_count = ncol;
-      if (sym) {  // row chunks that reach columns >= p1; column chunks with rows < p0
-        r_first = (int)(p1 / (C2::ROW_BNW * Op::EPW));
-        r_count = std::max(0, nrow - r_first);
-        c_count = (int)((p0 + C2::COL_BM - 1) / C2::COL_BM);
+    if (q == 1) return;
+    if (tm) tm->before(1, s);
+    SymPanel<Op> sp{rP, (p0 / (128 * Op::EPW)) * (128 * Op::EPW) + 128 * Op::EPW};
+    int r_first = 0, r_count = nrow, c_count = ncol;
+    if (sym) {  // row chunks that reach columns >= p1; column chunks with rows < p0
+      r_first = (int)(p1 / (C2::ROW_BNW * Op::EPW));
+      r_count = std::max(0, nrow - r_first);
+      c_count = (int)((p0 + C2::COL_BM - 1) / C2::COL_BM);
+    }
+    if (r_count + c_count > 0) {
+      fw_phase2<Op, BK><<<r_count + c_count, C2::THREADS, C2::SMEM, s>>>(D, ld, n, p0, p1, cT, ldT, r_count,
+                                                                        vec ? 1 : 0, r_first, sym ? 1 : 0, sp);
+      if (launches) *launches += 1;
+    }
+    if (sym && p0 > 0) {
+      const int64_t band_start = (p0 / (128 * Op::EPW)) * (128 * Op::EPW);
+      const int64_t xs = rP ? p0 : p0 - band_start;  // elements to visit per row
+      const unsigned gx = (unsigned)std::min<int64_t>((xs + 255) / 256, 64);
+      if (xs > 0) {
+        panel_finalize<Op><<<dim3(gx, BK), 256, 0, s>>>(D, ld, n, p0, cT, ldT, rP, band_start);
+        if (launches) *launches += 1;
       }
-      if (r_count + c_count > 0)
-        fw_phase2<Op, BK><<<r_count + c_count, C2::THREADS, C2::SMEM, s>>>(D, ld, n, p0, p1, colT, ldT, r_count,
-                                                                          vec ? 1 : 0, r_first, sym ? 1 : 0, sp);
-      if (sym && p0 > 0) {
-        const int64_t band_start = (p0 / (128 * Op::EPW)) * (128 * Op::EPW);
-        const int64_t xs = rowP ? p0 : p0 - band_start;  // elements to visit per row
-        const unsigned gx = (unsigned)std::min<int64_t>((xs + 255) / 256, 64);
-        if (xs > 0) {
-          panel_finalize<Op><<<dim3(gx, BK), 256, 0, s>>>(D, ld, n, p0, colT, ldT, rowP, band_start);
-          if (launches) *launches += 1;
-        }
-      }
-      if (tm) tm->after(1, s, sym ? rest * w * w : 2.0 * rest * w * w);
+    }
+    if (tm) tm->after(1, s, sym ? rest * w * w : 2.0 * rest * w * w);
+  };
+  // relaxations of round k's Phase 3 actually performed: the processed tiles' share of (n - w)^2 w
+  auto p3_work = [&](int64_t k) {
+    int64_t p0, p1;
+    span(k, p0, p1);
+    const double w = (double)(p1 - p0), rest = (double)(n - (p1 - p0));
+    const double frac = sym ? (double)tiles_total / ((double)tiles_x * tiles_y) : 1.0;
+    return rest * rest * w * frac;
+  };
+  if (!la_on) {
+    for (int64_t k = 0; k < q; ++k) {
+      int64_t p0, p1;
+      span(k, p0, p1);
+      panels(k, colT, rowP);
+      if (q == 1) break;
       if (tm) tm->before(2, s);
       if (tma && variant == 3)
         fw_phase3_ws<Op, BK, Op::DTYPE == 0><<<grid_tma, P3W_THREADS, P3T<BK>::SMEM, s>>>(
-            mA, mB, mC, D, ld, n, p0, p1, tiles_x, tiles_total, err, sym ? 1 : 0, tiles_y);
+            mA[0], mB[0], mC, D, ld, n, p0, p1, tiles_x, tiles_total, err, sym ? 1 : 0, tiles_y);
       else if (tma && variant == 2)
         fw_phase3_tma<Op, BK, 4><<<grid_tma, TileMap<128, 128, 4>::THREADS, P3T<BK>::SMEM, s>>>(
-            mA, mB, mC, D, ld, n, p0, p1, tiles_x, tiles_total, err, sym ? 1 : 0, tiles_y);
+            mA[0], mB[0], mC, D, ld, n, p0, p1, tiles_x, tiles_total, err, sym ? 1 : 0, tiles_y);
       else if (tma)
         fw_phase3_tma<Op, BK, 8><<<grid_tma, TileMap<128, 128, 8>::THREADS, P3T<BK>::SMEM, s>>>(
-            mA, mB, mC, D, ld, n, p0, p1, tiles_x, tiles_total, err, sym ? 1 : 0, tiles_y);
+            mA[0], mB[0], mC, D, ld, n, p0, p1, tiles_x, tiles_total, err, sym ? 1 : 0, tiles_y);
       else
-        fw_phase3<Op, BK><<<g3, C3::THREADS, SMEM3, s>>>(D, ld, n, p0, p1, colT, ldT, vec ? 1 : 0, symB);
-      // relaxations actually performed: the processed tiles' share of (n - w)^2 w
-      const double frac = sym ? (double)tiles_total / ((double)tiles_x * tiles_y) : 1.0;
-      if (tm) tm->after(2, s, rest * rest * w * frac);
+        fw_phase3<Op, BK><<<g3, C3::THREADS, SMEM3, s>>>(D, ld, n, p0, p1, colT, ldT, vec ? 1 : 0, symB_of(0));
+      if (launches) *launches += 1;
+      if (tm) tm->after(2, s, p3_work(k));
     }
-    if (launches) *launches += (q > 1) ? 3 : 1;
+  } else if constexpr (kLookaheadWidth<BK>) {
+    using F = LaP2<Op, BK>;
+    e = cudaMemsetAsync(cnt, 0, sizeof(int) * 4 * (size_t)q, s);
+    if (e != cudaSuccess) return e;
+    panels(0, colTb[0], rowPb[0]);
+    const int nrow_la = (int)((n + F::ROW_BNW * Op::EPW - 1) / (F::ROW_BNW * Op::EPW));
+    const int ncol_la = (int)((n + F::COL_BM - 1) / F::COL_BM);
+    for (int64_t k = 0; k < q; ++k) {
+      const int b = (int)(k & 1);
+      int64_t p0, p1;
+      span(k, p0, p1);
+      if (tm) tm->before(2, s);
+      double work = p3_work(k);
+      if (k + 1 == q) {
+        fw_phase3_ws<Op, BK, Op::DTYPE == 0><<<grid_tma, P3W_THREADS, P3T<BK>::SMEM, s>>>(
+            mA[b], mB[b], mC, D, ld, n, p0, p1, tiles_x, tiles_total, err, sym ? 1 : 0, tiles_y);
+      } else {
+        RoundLA<Op> la{};
+        span(k + 1, la.p0n, la.p1n);
+        la.colTn = colTb[b ^ 1];
+        la.rowPn = rowPb[b ^ 1];
+        la.cnt = cnt + 4 * k;
+        la.prio_ty = (int)(la.p0n / 128);
+        la.prio_tx = (int)(la.p0n / (128 * Op::EPW));
+        la.row_x0 = sym ? la.prio_tx : 0;
+        la.col_y1 = sym ? std::min(tiles_y, la.prio_tx * Op::EPW + Op::EPW) : tiles_y;
+        la.n_prio = (tiles_x - la.row_x0) + (la.col_y1 - (la.prio_ty < la.col_y1 ? 1 : 0));
+        if (sym) {
+          la.p2_row_first = (int)(la.p1n / (F::ROW_BNW * Op::EPW));
+          la.n_p2row = std::max(0, nrow_la - la.p2_row_first);
+          la.n_p2col = (int)((la.p0n + F::COL_BM - 1) / F::COL_BM);
+        } else {
+          la.p2_row_first = 0;
+          la.n_p2row = nrow_la;
+          la.n_p2col = ncol_la;
+        }
+        la.band_start_n = (la.p0n / (128 * Op::EPW)) * (128 * Op::EPW);
+        la.band_end_n = la.band_start_n + 128 * Op::EPW;
+        const int wn = (int)(la.p1n - la.p0n);
+        la.n_fin = 0;
+        if (sym && la.p0n > 0)
+          la.n_fin = la.rowPn ? (wn + LA_FIN_ROWS - 1) / LA_FIN_ROWS : (la.p0n > la.band_start_n ? 1 : 0);
+        const int len_t = la.n_prio + tiles_total;
+        // items are taken about grid_tma per tile time: P1 two tile times after
+        // the priority tiles (which are written by then), the Phase-2 chunks four
+        // more (P1 done), the publication three more (the chunks done)
+        la.b1 = std::min(len_t, la.n_prio + 2 * grid_tma);
+        la.b2 = std::min(len_t, la.b1 + 4 * grid_tma);
+        la.b3 = std::min(len_t, la.b2 + 3 * grid_tma);
+        la.vec = vec ? 1 : 0;
+        fw_round_la<Op, BK, Op::DTYPE == 0><<<grid_tma, P3W_THREADS, P3T<BK>::SMEM, s>>>(
+            mA[b], mB[b], mC, D, ld, n, p0, p1, tiles_x, tiles_y, tiles_total, err, sym ? 1 : 0, ldT, la);
+        const double w1 = (double)wn, rest1 = (double)(n - wn);
+        work += w1 * w1 * w1 + (sym ? rest1 * w1 * w1 : 2.0 * rest1 * w1 * w1);
+      }
+      if (launches) *launches += 1;
+      if (tm) tm->after(2, s, work);
+    }
   }
   if (sym && q > 1) {  // the lower triangle from the upper
     const dim3 gm((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
@@ -894,9 +1558,11 @@ static cudaError_t rounds_bk(const RoundConfig &cfg, void *D, int64_t ld, int64_
                              cudaStream_t s, int64_t *launches, PhaseTimer *tm, int *wait_err) {
   const bool vec = aligned16(D, ld, sizeof(typename Op::elem));
   if (cfg.bk == 32)
-    return rounds_impl<Op, 32>(D, ld, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err, cfg.sym, cfg.rowP);
+    return rounds_impl<Op, 32>(D, ld, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err, cfg.sym, cfg.rowP,
+                               cfg.lookahead);
   if (cfg.bk == 64)
-    return rounds_impl<Op, 64>(D, ld, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err, cfg.sym, cfg.rowP);
+    return rounds_impl<Op, 64>(D, ld, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err, cfg.sym, cfg.rowP,
+                               cfg.lookahead);
   return cudaErrorInvalidValue;
 }
 

@@ -25,20 +25,38 @@ struct PhaseTimer {
 // only the tiles that touch the upper triangle, both of its operands come from
 // one symmetric panel, and a final pass mirrors the upper triangle into the
 // lower; rowP is the BK x ldT element panel that packed 16-bit needs for it.
+// lookahead: with variant 3, round k's Phase-3 launch also runs round k+1's
+// Phase 1 and Phase 2 (one launch per round); needs the double panel buffers
+// of panel_buffer_bytes / row_panel_bytes(..., true).
 struct RoundConfig {
   int bk = 64;
   int p3 = 3;  // fastest on GB300 at n = 16384 (profiles/phase3_variants_gmm16k.md)
   bool sym = false;
   void *rowP = nullptr;
+  bool lookahead = false;
 };
 
 // flag |= 1 when D (n x n, leading dimension ld) is not symmetric.
 cudaError_t launch_symmetry_check(int dtype, const void *D, int64_t n, int64_t ld, int *flag, cudaStream_t s);
 constexpr int64_t kMaxRoundWidth = 64;  // panel buffers are sized for this
 
+// Bytes of the colT panel buffer launch_rounds needs for n (ldT = its row
+// pitch in words): one kMaxRoundWidth x ldT panel of 32-bit words, or with
+// lookahead two of them and 4 counters per round (round width >= 32).
+inline size_t panel_buffer_bytes(int64_t n, int64_t ldT, bool lookahead) {
+  const size_t one = (size_t)kMaxRoundWidth * (size_t)ldT * 4;
+  if (!lookahead) return one;
+  const size_t rounds = (size_t)((n + 31) / 32) + 1;
+  return 2 * one + 4 * sizeof(int) * rounds;
+}
+// Bytes of the element panel (symmetric mode, packed 16-bit).
+inline size_t row_panel_bytes(int64_t ldT, bool lookahead) {
+  return (lookahead ? 2 : 1) * (size_t)kMaxRoundWidth * (size_t)ldT * 2;
+}
+
 // q rounds of Phase 1 -> Phase 2 -> Phase 3 on D (n x n, leading dimension ld).
-// colT is a kMaxRoundWidth x ldT panel buffer of 32-bit words, ldT a multiple
-// of 256 and >= n.
+// colT is the panel buffer (panel_buffer_bytes(n, ldT, cfg.lookahead) bytes),
+// ldT a multiple of 256 and >= n; cfg.rowP the element panel when needed.
 // wait_err: device word that the persistent Phase-3 kernel ORs 4 into when a
 // bounded wait gives up; nullptr = a per-device word the library allocates on
 // first use.

@@ -17,6 +17,14 @@
 
 namespace apsp {
 
+// Barrier policy of the phase bodies: the whole CTA (the per-round and batch
+// kernels), or, in the warp-specialized Phase-3 kernel that runs next-round
+// tasks on its consumer warps while the producer warp goes on, a bounded
+// barrier over those warps (GroupBar in fw_kernels.cu).
+struct CtaBar {
+  __device__ __forceinline__ static void sync() { __syncthreads(); }
+};
+
 template <bool CG, class T>
 __device__ __forceinline__ T ld_elem(const T *p) {
   if constexpr (CG) return __ldcg(p);
@@ -32,7 +40,7 @@ struct P1Smem {
   typename Op::scalar s[BK][BK + 4];
 };
 
-template <class Op, int BK, int NT, bool CG>
+template <class Op, int BK, int NT, bool CG, class Bar = CtaBar>
 __device__ __forceinline__ void phase1_body(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
                                             uint32_t *__restrict__ colT, int64_t ldT, P1Smem<Op, BK> &sm, int tid,
                                             typename Op::elem *__restrict__ rowP = nullptr) {
@@ -59,7 +67,7 @@ __device__ __forceinline__ void phase1_body(typename Op::elem *__restrict__ D, i
       s[idx / BK][idx % BK] = tmp[k];
     }
   }
-  __syncthreads();
+  Bar::sync();
   S v[PT][PT];
 #pragma unroll
   for (int r = 0; r < PT; ++r)
@@ -98,14 +106,14 @@ __device__ __forceinline__ void phase1_body(typename Op::elem *__restrict__ D, i
           for (int r = 0; r < PT; ++r) s[by * PT + r][t + 1] = v[r][q];
         }
       }
-      __syncthreads();
+      Bar::sync();
     }
   }
 #pragma unroll
   for (int r = 0; r < PT; ++r)
 #pragma unroll
     for (int c = 0; c < PT; ++c) s[by * PT + r][bx * PT + c] = v[r][c];
-  __syncthreads();
+  Bar::sync();
   for (int idx = tid; idx < BK * BK; idx += NT) {
     const int i = idx / BK, j = idx % BK;
     const int64_t r = p0 + i, c = p0 + j;
@@ -164,7 +172,7 @@ __device__ __noinline__ void sym_band_store(typename Op::elem *D, int64_t ld, in
     if (x0 + e < band_end) D[(x0 + e) * ld + col] = bits_elem<Op>(chunk_get<Op>(w4, e));
 }
 
-template <class Op, int BK, int BNW, int NT, bool CG, int TN = 8>
+template <class Op, int BK, int BNW, int NT, bool CG, int TN = 8, class Bar = CtaBar>
 __device__ __forceinline__ void p2_row_task(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
                                             int64_t p1, uint32_t *__restrict__ colT, int64_t ldT, int64_t col0,
                                             bool vec, uint32_t *smem, int tid, const SymPanel<Op> *sym = nullptr) {
@@ -177,7 +185,7 @@ __device__ __forceinline__ void p2_row_task(typename Op::elem *__restrict__ D, i
   load_As_colT<BK, BK, NT, CG>(As, colT, ldT, p0, tid);
   load_Bs_rows<Op, BNW, BK, NT, CG>(Bs, D, ld, n, n, p0, col0, vec, tid);
   load_acc<Op, BK, BNW, CG, TN>(D, ld, n, n, p0, col0, vec, acc, ty, tx);
-  __syncthreads();
+  Bar::sync();
   tile_minplus<Op, BK, BNW, BK, TN>(As, Bs, acc, ty, tx);
   if (!sym) {
     store_acc<Op, BK, BNW, TN>(D, ld, n, n, p0, col0, 0, 0, p0, p1, vec, acc, ty, tx);
@@ -223,7 +231,7 @@ static __device__ __noinline__ void colT_store_partial(uint32_t *dst, int64_t rb
     if (rb + q < p0 || rb + q >= xr1) dst[q] = q4[q];
 }
 
-template <class Op, int BK, int BM, int NT, bool CG, int TN = 8>
+template <class Op, int BK, int BM, int NT, bool CG, int TN = 8, class Bar = CtaBar>
 __device__ __forceinline__ void p2_col_task(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
                                             int64_t p1, uint32_t *__restrict__ colT, int64_t ldT, int64_t row0,
                                             bool vec, uint32_t *smem, int tid, const SymPanel<Op> *sym = nullptr) {
@@ -237,7 +245,7 @@ __device__ __forceinline__ void p2_col_task(typename Op::elem *__restrict__ D, i
   load_As_transposed<Op, BM, BK, NT, CG>(As, D, ld, n, n, row0, p0, vec, tid);
   load_Bs_rows<Op, BNW, BK, NT, CG>(Bs, D, ld, n, n, p0, p0, vec, tid);
   load_acc<Op, BM, BNW, CG, TN>(D, ld, n, n, row0, p0, vec, acc, ty, tx);
-  __syncthreads();
+  Bar::sync();
   tile_minplus<Op, BM, BNW, BK, TN>(As, Bs, acc, ty, tx);
   // symmetric mode stores rows < p0 only
   const int64_t xr1 = sym ? INT64_MAX : p1;
