@@ -399,13 +399,15 @@ def run_gpu(args):
     achieved = (r3 / n3) / (ms3 / n3 / 1e3) / 1e9 if n3 else None
     peak = ADDMIN_LANES_PER_CLK_PER_SM * sms * sm_max_mhz * 1e6 / 1e9
     phase_ms = {f"phase{p}": round(prof[p][1] / args.steps, 3) for p in (1, 2, 3)}
-    roofline = {"bound": "alu", "kernel": "fw_phase3_ws<int32>", "achieved": achieved, "peak": peak, "unit": UNIT,
-                "work": "relaxations actually performed by Phase 3 (in symmetric mode only the tiles touching "
-                        "the upper triangle)",
+    roofline = {"bound": "alu",
+                "kernel": "fw_round_la<int32> (Phase 3 of round k with round k+1's Phase 1 and Phase 2 as tasks)",
+                "achieved": achieved, "peak": peak, "unit": UNIT,
+                "work": "relaxations performed in the launches: Phase 3 (in symmetric mode only the tiles touching "
+                        "the upper triangle) plus the next round's Phase 1 and Phase 2",
                 "frac": (achieved / peak) if achieved else None,
                 "peak_basis": f"{ADDMIN_LANES_PER_CLK_PER_SM} add-min lanes/clk/SM (measured) x {sms} SMs x "
                               f"{sm_max_mhz:.0f} MHz (max SM clock)",
-                "traffic": ncu_traffic("fw_phase3_int32_gmm16k"),
+                "traffic": ncu_traffic(f"fw_round_la_int32_{args.workload}"),
                 "phase_ms_per_step": phase_ms,
                 "phase3_share_of_step": prof[3][1] / ms if ms else None}
     if clocks and achieved:
@@ -529,6 +531,35 @@ def run_reference(args, n_s: int = 2048):
     print(json.dumps(out), flush=True)
 
 
+def run_round_shapes(args):
+    """Every round shape (round width x Phase-3 kernel) on the workload, int32, one JSON line each (not the
+    contract line): the table the autotuner chooses from, with per-phase times."""
+    import torch
+
+    import paper_1902_04446_gb300 as apsp
+
+    g = load_graph(args.workload)
+    n = g.n
+    Wd = dense_on_device(torch, g, torch.int32, 1073741823, 0)
+    Dd = torch.empty_like(Wd)
+    names = {1: "one CTA per tile", 2: "TMA, 256 threads", 3: "TMA, 512 threads",
+             4: "warp-specialized (lookahead rounds at width 64)"}
+    peak = ADDMIN_LANES_PER_CLK_PER_SM * torch.cuda.get_device_properties(0).multi_processor_count * 2070.0 / 1e3
+    for bk in (32, 64):
+        for v in (1, 2, 3, 4):
+            with apsp.Handle(device=0, block_k=bk, phase3_variant=v) as h:
+                ms, launches, prof = timed_solves(torch, h, "int32", Wd, Dd, args.steps, args.warmup, None,
+                                                  profile=True)
+            ms /= args.steps
+            n3, ms3, r3 = prof[3]
+            print(json.dumps({"workload": args.workload, "round_width": bk, "phase3_variant": v,
+                              "phase3_kernel": names[v], "ms_per_solve": round(ms, 2),
+                              "grelax_per_s": float(n) ** 3 / (ms / 1e3) / 1e9,
+                              "phase_ms": {f"phase{p}": round(prof[p][1] / args.steps, 2) for p in (1, 2, 3)},
+                              "phase3_frac_of_addmin_peak_2070mhz": (r3 / (ms3 / 1e3) / 1e9 / peak) if ms3 else None,
+                              "launches_per_solve": launches // args.steps}), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -540,8 +571,12 @@ def main(argv=None):
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=2000)
+    ap.add_argument("--round-shapes", action="store_true",
+                    help="time every round shape (round width x Phase-3 kernel) instead of the benchmark line")
     args = ap.parse_args(argv)
-    if args.impl == "reference":
+    if args.round_shapes:
+        run_round_shapes(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

@@ -348,6 +348,36 @@ def test_directed_every_phase3_kernel(lib, block_k, variant, dt):
         np.testing.assert_array_equal(D, E)
 
 
+# ------------------------------------------------------------------ lookahead task placement
+# Round k's Phase-3 launch also runs round k+1's Phase 1 / Phase 2 tasks, placed
+# in its work stream a few tile waves after the tiles they depend on; below
+# ~2000 vertices they all fall at the end of the stream, so these sizes are
+# needed to run them between tiles (general and symmetric, directed too).
+@pytest.mark.parametrize("symmetric,directed", [(2, False), (0, False), (0, True)])
+def test_lookahead_midstream_int32_full_matrix(lib, symmetric, directed):
+    n = 4100
+    s, d, w = er_edges(n, seed=41 + symmetric + directed, deg=4.0, wmax=200, directed=directed)
+    W = dense_directed(n, s, d, w) if directed else gen.dense_matrix(n, s, d, w, dtype=np.int32)
+    E = oracle.dijkstra(n, s, d, w, np.arange(n), directed=directed)
+    with lib.Handle(device=0, symmetric=symmetric) as h:
+        D = h.solve_t("int32", dev(W)).cpu().numpy().astype(np.int64)
+        assert h.last_status() == 0
+    np.testing.assert_array_equal(D, E)
+
+
+def test_lookahead_midstream_u16_sampled_rows(lib):
+    n = 8200
+    s, d, w = er_edges(n, seed=82, deg=4.0, wmax=60)
+    W = gen.dense_matrix(n, s, d, w, dtype=np.int16, inf=0x7FFF)
+    rows = np.sort(np.random.default_rng(8200).choice(n, size=512, replace=False))
+    E = oracle.dijkstra(n, s, d, w, rows)
+    with lib.Handle(device=0) as h:
+        D = h.solve_t("u16", dev(W))
+        assert h.last_status() == 0
+        got = D[torch.from_numpy(rows).cuda().long()].cpu().numpy()
+    np.testing.assert_array_equal(oracle.unpack_u16(got.view(np.uint16)).astype(np.int64), E)
+
+
 # ------------------------------------------------------------------ symmetric mode
 @pytest.mark.parametrize("symmetric", [0, 1, 2])
 @pytest.mark.parametrize("variant", [1, 2, 3, 4])
