@@ -53,6 +53,7 @@ WORKLOAD_TEXT = {
     "roll512": "n=512 symmetric k=8 kNN Swiss-roll graph (seed 0), int32 weights max(1, rint(100 d))",
     "er8k": "n=8192 Erdos-Renyi graph, average degree 16 plus a spanning path (seed 8), int32 weights U{1..1000}",
     "er16k": "n=16384 Erdos-Renyi graph, average degree 16 plus a spanning path (seed 16), int32 weights U{1..1000}",
+    "er4k": "n=4096 Erdos-Renyi graph, average degree 16 plus a spanning path (seed 4), int32 weights U{1..1000}",
 }
 PAPER_CONTEXT = {
     "source": "paper Table 3 (Blocked-CB, Spark, 64 Xeon Gold 6130 cores, n=16384 Erdos-Renyi): 2m50s",
@@ -145,7 +146,7 @@ def ncu_traffic(kernel_key: str):
 
 def load_graph(name):
     if name.startswith("er"):
-        n = {"er8k": 8192, "er16k": 16384}[name]
+        n = {"er4k": 4096, "er8k": 8192, "er16k": 16384}[name]
         s, d, w = gen.er_graph(n, n // 1024)
         return gen.graphs.Graph(name, n, s, d, w, "int32")
     return gen.workload(name)
@@ -465,6 +466,47 @@ def run_gpu(args):
                        "weights": "raw Euclidean distances as fp32 (same points)", "gpu_launches": int(lf)}
         del Wf, Df
 
+        # the min-plus product as a library primitive (Table 1 MatProd + MatMin)
+        # and repeated squaring (Alg. 1) as a second workload
+        mk = 8192
+        gmp = torch.Generator(device="cuda").manual_seed(8192)
+        A = torch.randint(0, 1000, (mk, mk), dtype=torch.int32, device="cuda", generator=gmp)
+        B = torch.randint(0, 1000, (mk, mk), dtype=torch.int32, device="cuda", generator=gmp)
+        C = torch.full((mk, mk), 1073741823, dtype=torch.int32, device="cuda")
+        for _ in range(max(1, args.warmup)):
+            h.minplus(A, B, C)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            h.minplus(A, B, C)
+        e1.record()
+        torch.cuda.synchronize()
+        msmp = e0.elapsed_time(e1) / args.steps
+        gr = float(mk) ** 3 / (msmp / 1e3) / 1e9
+        out["minplus"] = {"m": mk, "k": mk, "n": mk, "dtype": "int32", "ms": msmp, "value": gr, "unit": UNIT,
+                          "frac_of_addmin_peak": gr / peak, "inputs": "uniform U{0..999} (torch generator seed 8192)"}
+        del A, B, C
+        gs = load_graph("er4k")
+        Ws = dense_on_device(torch, gs, torch.int32, 1073741823, device)
+        Ds = torch.empty_like(Ws)
+        h.solve_squaring("int32", Ws, Ds)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            h.solve_squaring("int32", Ws, Ds)
+        e1.record()
+        torch.cuda.synchronize()
+        mss = e0.elapsed_time(e1) / args.steps
+        msfw, _, _ = timed_solves(torch, h, "int32", Ws, Ds, args.steps, 1, None)
+        nsq = gs.n
+        prods = int(np.ceil(np.log2(nsq - 1)))
+        out["squaring"] = {"graph": WORKLOAD_TEXT["er4k"], "n": nsq, "products": prods,
+                           "ms_per_solve": mss, "products_grelax_per_s": prods * float(nsq) ** 3 / (mss / 1e3) / 1e9,
+                           "floyd_warshall_ms_per_solve": msfw / args.steps,
+                           "path": "apsp_solve_squaring (Alg. 1): ceil(log2(n-1)) in-place min-plus products"}
+        del Ws, Ds
+
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     Wh = Wd.cpu().pin_memory()
     Dh = torch.empty_like(Wh).pin_memory()
@@ -520,7 +562,8 @@ def run_reference(args, n_s: int = 2048):
     value = args.steps * float(n_s) ** 3 / dt / 1e9
     sample = (f"each step = the oracle's complete int64 Floyd-Warshall on the workload's generator recipe at "
               f"n={n_s} (one host core); value = n^3 / t")
-    n = {"gmm16k": 16384, "er8k": 8192, "er16k": 16384, "roll64k": 65536, "roll512": 512}.get(args.workload)
+    n = {"gmm16k": 16384, "er4k": 4096, "er8k": 8192, "er16k": 16384, "roll64k": 65536,
+         "roll512": 512}.get(args.workload)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "int64", "data": "synthetic",

@@ -169,9 +169,23 @@ apsp_status apsp_check_bounded_wait(apsp_handle *h, int64_t spin_limit);
 /* C = min(C, A (x) B): the min-plus product ("MatProd") followed by the
  * element-wise minimum ("MatMin").  A is m x k (lda), B is k x n (ldb), C is
  * m x n (ldc), all device, row-major, of the given dtype (APSP_I32, APSP_U16 or
- * APSP_F32).  C must not overlap A or B.  Errors: APSP_E_INVALID. */
+ * APSP_F32).  C must not overlap A or B.  Uses a handle-owned workspace of
+ * about 4*m*k bytes (A transposed) for the TMA-fed kernel when it can be
+ * allocated and B and C are 16-byte addressable; otherwise a kernel without
+ * workspace.  Asynchronous on `stream`; a device wait that gave up is reported
+ * by apsp_last_status (bit 4).  Errors: APSP_E_INVALID, APSP_E_CUDA. */
 apsp_status apsp_minplus(apsp_handle *h, int dtype, const void *A, int64_t lda, const void *B, int64_t ldb,
                          void *C, int64_t ldc, int64_t m, int64_t k, int64_t n, void *stream);
+
+/* All-pairs shortest paths by repeated min-plus squaring (Alg. 1): D = W, then
+ * ceil(log2(n - 1)) times D = min(D, D (x) D), in place.  The same matrix as
+ * apsp_solve_t (exact for APSP_I32 and APSP_U16; fp32 within rounding), for
+ * about log2(n) times the work of Floyd-Warshall: the paper's first method, kept
+ * as a second workload of the min-plus product.  Arguments, layout, input
+ * checks and status as apsp_solve_t with an explicit dtype (no APSP_AUTO);
+ * uses the apsp_minplus workspace (about 4*n*n bytes). */
+apsp_status apsp_solve_squaring(apsp_handle *h, int dtype, const void *W, int64_t n, int64_t ld, void *D,
+                                void *stream);
 
 /* int32 -> packed u16 (INF32 -> INF16) and back, n x n with separate leading
  * dimensions; the caller guarantees every finite entry is < APSP_INF_U16. */

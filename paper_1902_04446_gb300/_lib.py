@@ -51,6 +51,7 @@ def _load():
         "apsp_last_status": (st, [H, vp]),
         "apsp_int16_bound": (st, [H, vp, i64, i64, ctypes.POINTER(i64), ctypes.POINTER(i32), vp]),
         "apsp_minplus": (st, [H, i32, vp, i64, vp, i64, vp, i64, i64, i64, i64, vp]),
+        "apsp_solve_squaring": (st, [H, i32, vp, i64, i64, vp, vp]),
         "apsp_pack_u16": (st, [vp, i64, vp, i64, i64, vp]),
         "apsp_unpack_u16": (st, [vp, i64, vp, i64, i64, vp]),
         "apsp_submit": (st, [H, ctypes.POINTER(apsp_request), ctypes.POINTER(ctypes.c_uint64)]),
@@ -95,4 +96,4 @@ ENTRY_POINTS = sorted(["apsp_config_default", "apsp_create", "apsp_destroy", "ap
                        "apsp_unpack_u16", "apsp_submit", "apsp_poll", "apsp_wait", "apsp_fetch", "apsp_release",
                        "apsp_cancel", "apsp_strerror", "apsp_last_error", "apsp_launch_count",
                        "apsp_profile", "apsp_profile_read", "apsp_solve_batch", "apsp_check_bounded_wait",
-                       "apsp_autotune", "apsp_tuned_config", "apsp_solve_i32_noalloc"])
+                       "apsp_autotune", "apsp_tuned_config", "apsp_solve_i32_noalloc", "apsp_solve_squaring"])

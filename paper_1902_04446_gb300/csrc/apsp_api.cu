@@ -134,6 +134,8 @@ struct apsp_handle {
   size_t wsb_bytes = 0;
   void *rowP = nullptr;  // symmetric mode, packed 16-bit: element panel
   size_t rowP_bytes = 0;
+  void *mpT = nullptr;  // min-plus product: A^T (32-bit words)
+  size_t mpT_bytes = 0;
   int *d_status = nullptr;
   int *h_status = nullptr;  // pinned
   std::string last_error;
@@ -425,6 +427,7 @@ apsp_status apsp_destroy(apsp_handle *h) {
   if (h->ws16) cudaFree(h->ws16);
   if (h->wsb) cudaFree(h->wsb);
   if (h->rowP) cudaFree(h->rowP);
+  if (h->mpT) cudaFree(h->mpT);
   if (h->d_status) cudaFree(h->d_status);
   if (h->h_status) cudaFreeHost(h->h_status);
   delete h;
@@ -551,6 +554,23 @@ apsp_status apsp_int16_bound(apsp_handle *h, const int32_t *W, int64_t n, int64_
   return APSP_OK;
 }
 
+// The product into C with the library's A^T workspace (the warp-specialized
+// kernel) when it can be had, else the one-CTA-per-tile kernel.  h->mu held.
+static cudaError_t minplus_locked(apsp_handle *h, int dtype, const void *A, int64_t lda, const void *B, int64_t ldb,
+                                  void *C, int64_t ldc, int64_t m, int64_t k, int64_t n, cudaStream_t s) {
+  const size_t need = apsp::minplus_scratch_bytes(m, k);
+  void *scr = nullptr;
+  if (need > 0) {
+    if (ensure(&h->mpT, &h->mpT_bytes, need) == cudaSuccess) scr = h->mpT;
+    else cudaGetLastError();  // out of memory: the kernel without workspace
+  }
+  int64_t l = 0;
+  cudaError_t e = apsp::launch_minplus(dtype, A, lda, B, ldb, C, ldc, m, k, n, s, &l, scr, scr ? h->mpT_bytes : 0,
+                                       h->d_status);
+  h->launches += l;
+  return e;
+}
+
 apsp_status apsp_minplus(apsp_handle *h, int dtype, const void *A, int64_t lda, const void *B, int64_t ldb, void *C,
                          int64_t ldc, int64_t m, int64_t k, int64_t n, void *stream) {
   if (!h || !valid_dtype(dtype)) return APSP_E_INVALID;
@@ -559,10 +579,39 @@ apsp_status apsp_minplus(apsp_handle *h, int dtype, const void *A, int64_t lda, 
   if ((m + 127) / 128 > 65535) return set_err(h, APSP_E_INVALID, "m too large");
   cudaError_t e = cudaSetDevice(h->cfg.device);
   if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
-  int64_t l = 0;
-  e = apsp::launch_minplus(dtype, A, lda, B, ldb, C, ldc, m, k, n, static_cast<cudaStream_t>(stream), &l);
-  h->launches += l;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> g(h->mu);
+  if ((e = cudaMemsetAsync(h->d_status, 0, sizeof(int), s)) != cudaSuccess) return cuda_fail(h, e, "status reset");
+  e = minplus_locked(h, dtype, A, lda, B, ldb, C, ldc, m, k, n, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "minplus");
+  return APSP_OK;
+}
+
+apsp_status apsp_solve_squaring(apsp_handle *h, int dtype, const void *W, int64_t n, int64_t ld, void *D,
+                                void *stream) {
+  if (!h) return APSP_E_INVALID;
+  if (!valid_dtype(dtype)) return set_err(h, APSP_E_INVALID, "dtype must be APSP_I32, APSP_U16 or APSP_F32");
+  if (n < 0 || ld < n || (n > 0 && (!W || !D))) return set_err(h, APSP_E_INVALID, "need n >= 0, ld >= n, W and D");
+  if ((n + 127) / 128 > 65535) return set_err(h, APSP_E_INVALID, "n too large");
+  cudaError_t e = cudaSetDevice(h->cfg.device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> g(h->mu);
+  if ((e = cudaMemsetAsync(h->d_status, 0, sizeof(int), s)) != cudaSuccess) return cuda_fail(h, e, "status reset");
+  if (n == 0) return APSP_OK;
+  int64_t l = 0;
+  e = apsp::launch_ingest(dtype, W, D, n, ld, h->d_status, s, &l);
+  h->launches += l;
+  if (e != cudaSuccess) return cuda_fail(h, e, "ingest");
+  // a shortest path has at most n - 1 edges; after i squarings every path of
+  // up to 2^i edges is accounted for (Alg. 1).  In place: each value read
+  // during a product is already a valid upper bound, so it converges no later
+  int rounds = 0;
+  while ((int64_t(1) << rounds) < n - 1) ++rounds;
+  for (int i = 0; i < rounds; ++i) {
+    e = minplus_locked(h, dtype, D, ld, D, ld, D, ld, n, n, n, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "squaring");
+  }
   return APSP_OK;
 }
 

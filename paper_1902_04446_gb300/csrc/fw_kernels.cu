@@ -373,22 +373,22 @@ constexpr int P3W_THREADS = 9 * 32;
 __device__ __forceinline__ int64_t red_cols(int64_t n) { return n & ~(int64_t)3; }
 
 template <int BM, int BNW, int TN>
-__device__ __forceinline__ void red_tail_store(int32_t *D, int64_t ld, int64_t n, int64_t r0, int64_t c0,
-                                               const uint32_t (&acc)[8][TN], int ty, int tx) {
+__device__ __forceinline__ void red_tail_store(int32_t *D, int64_t ld, int64_t nrows, int64_t ncols, int64_t r0,
+                                               int64_t c0, const uint32_t (&acc)[8][TN], int ty, int tx) {
   using Map = TileMap<BM, BNW, TN>;
-  const int64_t n4 = red_cols(n);
+  const int64_t n4 = red_cols(ncols);
 #pragma unroll
   for (int h = 0; h < Map::NH; ++h) {
     const int64_t cw = c0 + Map::wcol(tx, h);
-    if (cw + 4 <= n4 || cw >= n) continue;
+    if (cw + 4 <= n4 || cw >= ncols) continue;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       const int64_t row = r0 + Map::row(ty, r);
-      if (row >= n) continue;
+      if (row >= nrows) continue;
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int64_t c = cw + e;
-        if (c >= n4 && c < n) {
+        if (c >= n4 && c < ncols) {
           int32_t *p = D + row * ld + c;
           *p = (int32_t)OpI32::addmin(acc[r][4 * h + e], 0u, (uint32_t)*p);
         }
@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
         fence_proxy_async_smem();
         if constexpr (Op::DTYPE == 0)
           if (c0 + BNW > red_cols(n) && c0 < n)
-            red_tail_store<BM, BNW, TN>(reinterpret_cast<int32_t *>(D), ld, n, r0, c0, acc, ty, tx);
+            red_tail_store<BM, BNW, TN>(reinterpret_cast<int32_t *>(D), ld, n, n, r0, c0, acc, ty, tx);
       } else {
         bad = !mbar_wait_bounded(&full_c, (uint32_t)i & 1u, P3T_WAIT_LIMIT);
         if (__any_sync(0xffffffffu, bad)) {
@@ -1008,7 +1008,7 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
             fence_proxy_async_smem();
             if constexpr (Op::DTYPE == 0)
               if (c0 + BNW > red_cols(n) && c0 < n)
-                red_tail_store<BM, BNW, TN>(reinterpret_cast<int32_t *>(D), ld, n, r0, c0, acc, ty, tx);
+                red_tail_store<BM, BNW, TN>(reinterpret_cast<int32_t *>(D), ld, n, n, r0, c0, acc, ty, tx);
           }
         } else {
           ebad = !mbar_wait_bounded(&full_c, (uint32_t)ct & 1u, P3T_WAIT_LIMIT);
@@ -1144,6 +1144,203 @@ __global__ void __launch_bounds__(256, 2) minplus_kernel(const typename Op::elem
     __syncthreads();
   }
   store_acc<Op, Cfg::BM, Cfg::BNW>(Cm, ldc, m, nn, row0, col0, 0, 0, 0, 0, vecc, acc, ty, tx);
+}
+
+// A^T as the k-major operand of the warp-specialized product: AT[t][i] =
+// word(A[i][t]) (the value in both halves for packed 16-bit) for t < k, i < m;
+// the padding rows t in [k, k_pad) and columns i >= m hold INF words, so
+// TMA's zero fill of B's missing rows (t >= k) never meets a finite A.
+template <class Op>
+__global__ void transpose_dup_kernel(const typename Op::elem *__restrict__ A, int64_t lda, int64_t m, int64_t k,
+                                     uint32_t *__restrict__ AT, int64_t ldat, int64_t k_pad) {
+  __shared__ uint32_t tile[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32, t0 = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int r = ty; r < 32; r += 8) {             // read A[i0 + r][t0 + tx]
+    const int64_t i = i0 + r, t = t0 + tx;
+    tile[r][tx] = (i < m && t < k) ? Op::dup(A[i * lda + t]) : Op::INF_WORD;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {  // write AT[t0 + r][i0 + tx]
+    const int64_t t = t0 + r, i = i0 + tx;
+    if (t < k_pad && i < ldat) AT[t * ldat + i] = tile[tx][r];
+  }
+}
+
+// C = min(C, A (x) B) for general shapes, warp-specialized like fw_phase3_ws:
+// 8 consumer warps own 8 x 8 words of a 128 x 128-word output tile and walk
+// its k in chunks of 64 (one work slot per chunk; the accumulators start at INF
+// with the first chunk); a producer warp moves A^T and B chunks by TMA and
+// applies the tile after its last chunk: TMA min-reduction for int32 (the map
+// ends at ncols rounded down to 4 elements, the tail merged by its owners),
+// merge with a TMA-loaded C and TMA store (interior) or masked stores (edge)
+// otherwise.  Static contiguous tile ranges per CTA; bounded waits.
+template <class Op, bool RED>
+__global__ void __launch_bounds__(P3W_THREADS, 1)
+    fw_minplus_ws(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                  const __grid_constant__ CUtensorMap mapC, typename Op::elem *__restrict__ C, int64_t ldc, int64_t m,
+                  int64_t ncols, int nk, int tiles_x, int tiles_total, int *err) {
+  constexpr int BK = 64, BM = 128, BNW = 128, TN = 8;
+  using Map = TileMap<BM, BNW, TN>;
+  constexpr int NCW = Map::THREADS / 32;
+  constexpr int STAGE = P3T<BK>::STAGE_BYTES;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_ab[2], empty_ab[2], full_c, cdone, cfree;
+  __shared__ int abort_flag;
+  uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  auto stA = [&](int s) { return reinterpret_cast<uint32_t *>(base + s * STAGE); };
+  auto stB = [&](int s) { return reinterpret_cast<uint32_t *>(base + s * STAGE) + BK * BM; };
+  uint32_t *Cs = reinterpret_cast<uint32_t *>(base + 2 * STAGE);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int per = tiles_total / (int)gridDim.x, extra = tiles_total % (int)gridDim.x;
+  const int t_begin = (int)blockIdx.x * per + min((int)blockIdx.x, extra);
+  const int t_end = t_begin + per + ((int)blockIdx.x < extra ? 1 : 0);
+  if (t_begin >= t_end) return;
+  const long long n_slots = (long long)(t_end - t_begin) * nk;
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&full_ab[i], 1);
+      mbar_init(&empty_ab[i], NCW);
+    }
+    mbar_init(&full_c, 1);
+    mbar_init(&cdone, NCW);
+    mbar_init(&cfree, 1);
+    fence_barrier_init();
+    prefetch_tensormap(&mapA);
+    prefetch_tensormap(&mapB);
+    prefetch_tensormap(&mapC);
+    abort_flag = 0;
+  }
+  __syncthreads();
+  auto interior_of = [&](int64_t r0, int64_t c0) { return r0 + BM <= m && c0 + BNW * Op::EPW <= ncols; };
+
+  if (warp == NCW) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int n_ab[2] = {0, 0}, n_c = 0;
+      bool ok = true;
+      auto issue_ab = [&](long long j) {
+        const int s = (int)(j & 1);
+        const int t = t_begin + (int)(j / nk), c = (int)(j % nk);
+        mbar_arrive_expect_tx(&full_ab[s], STAGE);
+        tma_load_2d(stA(s), &mapA, &full_ab[s], (t / tiles_x) * BM, c * BK);
+        tma_load_2d(stB(s), &mapB, &full_ab[s], (t % tiles_x) * BNW * Op::EPW, c * BK);
+        if (s == 0) ++n_ab[0];
+        else ++n_ab[1];
+      };
+      auto issue_c = [&](int t) {
+        mbar_arrive_expect_tx(&full_c, P3T_C_BYTES);
+        tma_load_2d(Cs, &mapC, &full_c, (t % tiles_x) * BNW * Op::EPW, (t / tiles_x) * BM);
+        ++n_c;
+      };
+      issue_ab(0);
+      if (n_slots > 1) issue_ab(1);
+      if (!RED) issue_c(t_begin);
+      for (long long j = 0; j < n_slots; ++j) {
+        const int s = (int)(j & 1);
+        if (!mbar_wait_bounded(&empty_ab[s], (uint32_t)(j >> 1) & 1u, P3T_WAIT_LIMIT)) {
+          ok = false;
+          break;
+        }
+        if (j + 2 < n_slots) issue_ab(j + 2);
+        if (j % nk != nk - 1) continue;
+        const int ti = (int)(j / nk), t = t_begin + ti;  // the tile's last chunk: write it back
+        if (!mbar_wait_bounded(&cdone, (uint32_t)ti & 1u, P3T_WAIT_LIMIT)) {
+          ok = false;
+          break;
+        }
+        const int r0 = (t / tiles_x) * BM, c0 = (t % tiles_x) * BNW * Op::EPW;
+        if (RED) {
+          if (c0 < red_cols(ncols)) {  // mapC ends at red_cols(ncols) in this mode
+            tma_reduce_min_2d(&mapC, Cs, c0, r0);
+            bulk_commit();
+            bulk_wait_read_all();
+          }
+          mbar_arrive(&cfree);
+        } else {
+          if (interior_of(r0, c0)) {
+            tma_store_2d(&mapC, Cs, c0, r0);
+            bulk_commit();
+            bulk_wait_read_all();
+          }
+          if (t + 1 < t_end) issue_c(t + 1);
+        }
+      }
+      bulk_wait_all();
+      if (!ok) {
+        abort_flag = 1;
+        for (int st = 0; st < 2; ++st)
+          if (n_ab[st] > 0) mbar_wait_bounded(&full_ab[st], (uint32_t)(n_ab[st] - 1) & 1u, P3T_WAIT_LIMIT);
+        if (n_c > 0) mbar_wait_bounded(&full_c, (uint32_t)(n_c - 1) & 1u, P3T_WAIT_LIMIT);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ consumers
+    const int tx = tid % Map::TX, ty = tid / Map::TX;
+    uint32_t acc[8][TN];
+    for (long long j = 0; j < n_slots; ++j) {
+      const int s = (int)(j & 1), c = (int)(j % nk);
+      if (c == 0) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+          for (int q = 0; q < TN; ++q) acc[r][q] = Op::INF_WORD;
+      }
+      bool bad = !mbar_wait_bounded(&full_ab[s], (uint32_t)(j >> 1) & 1u, P3T_WAIT_LIMIT);
+      if (__any_sync(0xffffffffu, bad)) {
+        if (lane == 0) abort_flag = 1;
+        break;
+      }
+      tile_minplus<Op, BM, BNW, BK, TN>(stA(s), stB(s), acc, ty, tx);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty_ab[s]);
+      if (c != nk - 1) continue;
+      const int ti = (int)(j / nk), t = t_begin + ti;
+      const int64_t r0 = (int64_t)(t / tiles_x) * BM, c0 = (int64_t)(t % tiles_x) * BNW * Op::EPW;
+      if (RED) {
+        bad = ti > 0 && !mbar_wait_bounded(&cfree, (uint32_t)(ti - 1) & 1u, P3T_WAIT_LIMIT);
+        if (__any_sync(0xffffffffu, bad)) {
+          if (lane == 0) abort_flag = 1;
+          break;
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+          for (int h = 0; h < Map::NH; ++h)
+            *reinterpret_cast<uint4 *>(Cs + Map::row(ty, r) * BNW + Map::wcol(tx, h)) =
+                make_uint4(acc[r][4 * h], acc[r][4 * h + 1], acc[r][4 * h + 2], acc[r][4 * h + 3]);
+        fence_proxy_async_smem();
+        if constexpr (Op::DTYPE == 0)
+          if (c0 + BNW > red_cols(ncols) && c0 < ncols)
+            red_tail_store<BM, BNW, TN>(reinterpret_cast<int32_t *>(C), ldc, m, ncols, r0, c0, acc, ty, tx);
+      } else {
+        bad = !mbar_wait_bounded(&full_c, (uint32_t)ti & 1u, P3T_WAIT_LIMIT);
+        if (__any_sync(0xffffffffu, bad)) {
+          if (lane == 0) abort_flag = 1;
+          break;
+        }
+        const bool interior = interior_of(r0, c0);
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+          for (int h = 0; h < Map::NH; ++h) {
+            uint4 *cp = reinterpret_cast<uint4 *>(Cs + Map::row(ty, r) * BNW + Map::wcol(tx, h));
+            const uint4 v = *cp;
+            acc[r][4 * h + 0] = Op::addmin(acc[r][4 * h + 0], 0u, v.x);
+            acc[r][4 * h + 1] = Op::addmin(acc[r][4 * h + 1], 0u, v.y);
+            acc[r][4 * h + 2] = Op::addmin(acc[r][4 * h + 2], 0u, v.z);
+            acc[r][4 * h + 3] = Op::addmin(acc[r][4 * h + 3], 0u, v.w);
+            if (interior) *cp = make_uint4(acc[r][4 * h], acc[r][4 * h + 1], acc[r][4 * h + 2], acc[r][4 * h + 3]);
+          }
+        if (interior) fence_proxy_async_smem();
+        else store_acc<Op, BM, BNW, TN>(C, ldc, m, ncols, r0, c0, 0, 0, 0, 0, true, acc, ty, tx);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&cdone);
+    }
+  }
+  __syncthreads();
+  if (abort_flag && tid == 0) atomicOr(err, 4);
 }
 
 // ---------------------------------------------------------------- ingest / checks
@@ -1687,9 +1884,63 @@ static cudaError_t minplus_impl(const void *A, int64_t lda, const void *B, int64
   return cudaGetLastError();
 }
 
+// The warp-specialized product (A^T in `scratch`); returns cudaErrorNotSupported
+// when its preconditions do not hold (the caller then uses minplus_kernel).
+template <class Op>
+static cudaError_t minplus_ws_impl(const void *A, int64_t lda, const void *B, int64_t ldb, void *Cm, int64_t ldc,
+                                   int64_t m, int64_t k, int64_t nn, cudaStream_t s, int64_t *launches,
+                                   void *scratch, size_t scratch_bytes, int *wait_err) {
+  using E = typename Op::elem;
+  constexpr bool RED = Op::DTYPE == 0;
+  const size_t es = sizeof(E);
+  if (k <= 0 || !scratch || scratch_bytes < minplus_scratch_bytes(m, k)) return cudaErrorNotSupported;
+  if (!aligned16(B, ldb, es) || !aligned16(Cm, ldc, es)) return cudaErrorNotSupported;
+  const uint64_t cx = RED ? (uint64_t)(nn & ~(int64_t)3) : (uint64_t)nn;
+  if (cx == 0) return cudaErrorNotSupported;
+  int *err = wait_err ? wait_err : error_word();
+  if (!err) return cudaErrorNotSupported;
+  const int64_t k_pad = (k + 63) / 64 * 64, ldat = (m + 255) / 256 * 256;
+  uint32_t *AT = static_cast<uint32_t *>(scratch);
+  constexpr CUtensorMapDataType dt = Op::DTYPE == 1   ? CU_TENSOR_MAP_DATA_TYPE_UINT16
+                                     : Op::DTYPE == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                      : CU_TENSOR_MAP_DATA_TYPE_INT32;
+  CUtensorMap mA, mB, mC;
+  if (!make_map(&mA, CU_TENSOR_MAP_DATA_TYPE_UINT32, AT, (uint64_t)ldat, (uint64_t)k_pad, (uint64_t)ldat * 4, 128,
+                64) ||
+      !make_map(&mB, dt, B, (uint64_t)nn, (uint64_t)k, (uint64_t)ldb * es, 128 * Op::EPW, 64) ||
+      !make_map(&mC, dt, Cm, cx, (uint64_t)m, (uint64_t)ldc * es, 128 * Op::EPW, 128))
+    return cudaErrorNotSupported;
+  cudaError_t e = cudaFuncSetAttribute(fw_minplus_ws<Op, RED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       P3T<64>::SMEM);
+  if (e != cudaSuccess) return e;
+  const dim3 gt((unsigned)(ldat / 32), (unsigned)(k_pad / 32));
+  transpose_dup_kernel<Op><<<gt, dim3(32, 8), 0, s>>>(static_cast<const E *>(A), lda, m, k, AT, ldat, k_pad);
+  const int tiles_x = (int)((nn + 128 * Op::EPW - 1) / (128 * Op::EPW));
+  const int tiles_total = tiles_x * (int)((m + 127) / 128);
+  const int grid = std::min(sm_count(), tiles_total);
+  fw_minplus_ws<Op, RED><<<grid, P3W_THREADS, P3T<64>::SMEM, s>>>(mA, mB, mC, static_cast<E *>(Cm), ldc, m, nn,
+                                                                   (int)(k_pad / 64), tiles_x, tiles_total, err);
+  if (launches) *launches += 2;
+  return cudaGetLastError();
+}
+
+size_t minplus_scratch_bytes(int64_t m, int64_t k) {
+  if (m <= 0 || k <= 0) return 0;
+  return (size_t)((k + 63) / 64 * 64) * (size_t)((m + 255) / 256 * 256) * 4;
+}
+
 cudaError_t launch_minplus(int dtype, const void *A, int64_t lda, const void *B, int64_t ldb, void *Cm, int64_t ldc,
-                           int64_t m, int64_t k, int64_t nn, cudaStream_t s, int64_t *launches) {
+                           int64_t m, int64_t k, int64_t nn, cudaStream_t s, int64_t *launches, void *scratch,
+                           size_t scratch_bytes, int *wait_err) {
   if (m <= 0 || nn <= 0) return cudaSuccess;
+  cudaError_t e = cudaErrorNotSupported;
+  switch (dtype) {
+    case 0: e = minplus_ws_impl<OpI32>(A, lda, B, ldb, Cm, ldc, m, k, nn, s, launches, scratch, scratch_bytes, wait_err); break;
+    case 1: e = minplus_ws_impl<OpU16>(A, lda, B, ldb, Cm, ldc, m, k, nn, s, launches, scratch, scratch_bytes, wait_err); break;
+    case 2: e = minplus_ws_impl<OpF32>(A, lda, B, ldb, Cm, ldc, m, k, nn, s, launches, scratch, scratch_bytes, wait_err); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaErrorNotSupported) return e;
   switch (dtype) {
     case 0: return minplus_impl<OpI32>(A, lda, B, ldb, Cm, ldc, m, k, nn, s, launches);
     case 1: return minplus_impl<OpU16>(A, lda, B, ldb, Cm, ldc, m, k, nn, s, launches);

@@ -74,8 +74,15 @@ cudaError_t launch_unpack(const uint16_t *src, int64_t lds, int32_t *dst, int64_
                           int64_t *launches);
 cudaError_t launch_densify(int dtype, const int32_t *src, const int32_t *dst, const void *w, int64_t m, void *D,
                            int64_t n, int64_t ld, int *status, cudaStream_t s, int64_t *launches);
+// C = min(C, A (x) B).  With scratch (>= minplus_scratch_bytes(m, k)) and
+// 16-byte addressable B and C: A^T into scratch, then the warp-specialized TMA
+// kernel (C may then alias A and B: every value read is a valid upper bound,
+// so an in-place product only converges faster); otherwise one CTA per tile.
+// wait_err as for launch_rounds.
+size_t minplus_scratch_bytes(int64_t m, int64_t k);
 cudaError_t launch_minplus(int dtype, const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc,
-                           int64_t m, int64_t k, int64_t nn, cudaStream_t s, int64_t *launches);
+                           int64_t m, int64_t k, int64_t nn, cudaStream_t s, int64_t *launches,
+                           void *scratch = nullptr, size_t scratch_bytes = 0, int *wait_err = nullptr);
 
 // 16-bit enable test.  *bound = max over components of 2 * ecc(smallest vertex);
 // *ok = bound < 0x7FFF.  Both synchronize `s`.

@@ -135,6 +135,22 @@ class Handle:
                     "apsp_solve_t")
         return D
 
+    def solve_squaring(self, dtype, W, D=None, stream=None):
+        """apsp_solve_squaring: D (allocated like W when None) <- APSP of W by repeated min-plus squaring
+        (Alg. 1); returns D."""
+        import torch
+        code = dtype_code(dtype)
+        n, ld = _mat(W, "W")
+        _elem_ok(W, code)
+        if D is None:
+            D = torch.empty_like(W)
+        nd, ldd = _mat(D, "D")
+        if nd != n or ldd != ld or D.dtype != W.dtype:
+            raise ValueError("D must have W's shape, leading dimension and dtype")
+        self._check(_L().apsp_solve_squaring(self._h, code, W.data_ptr(), n, ld, D.data_ptr(),
+                                             _stream(stream, W.device)), "apsp_solve_squaring")
+        return D
+
     def solve(self, W, D=None, stream=None):
         """apsp_solve with the handle's dtype."""
         return self.solve_t(self.dtype, W, D, stream)

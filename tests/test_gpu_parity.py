@@ -80,6 +80,88 @@ def test_minplus_matches_oracle(H, m, k, n, dt):
     np.testing.assert_array_equal(got, exp)
 
 
+def _minplus_inputs(rng, m, k, n, dt):
+    """A, B, C of the given dtype (INF entries included) and the oracle's C = min(C, A (x) B)."""
+    if dt == "fp32":
+        A = rng.random((m, k), dtype=np.float32) * 50
+        B = rng.random((k, n), dtype=np.float32) * 50
+        C = rng.random((m, n), dtype=np.float32) * 120
+        A[rng.random(A.shape) < 0.2] = np.inf
+        B[rng.random(B.shape) < 0.2] = np.inf
+        return A, B, C, oracle.minplus(A.astype(np.float64), B.astype(np.float64), C.astype(np.float64))
+    inf = INF if dt == "int32" else 0x7FFF
+    hi = 5000 if dt == "int32" else 16000
+    npdt = np.int32 if dt == "int32" else np.int16
+    A = rng.integers(0, hi, size=(m, k)); B = rng.integers(0, hi, size=(k, n)); C = rng.integers(0, 2 * hi, size=(m, n))
+    A[rng.random(A.shape) < 0.2] = inf
+    B[rng.random(B.shape) < 0.2] = inf
+    C[rng.random(C.shape) < 0.2] = inf
+    A64, B64, C64 = (np.where(x == inf, INF, x).astype(np.int64) for x in (A, B, C))
+    exp = oracle.minplus(A64, B64, C64)
+    if dt == "u16":
+        exp = np.where(exp >= 0x7FFF, 0x7FFF, exp)
+    return A.astype(npdt), B.astype(npdt), C.astype(npdt), exp
+
+
+@pytest.mark.parametrize("m,k,n", [(128, 64, 128), (333, 130, 261), (129, 64, 5), (70, 700, 300),
+                                   (1024, 1024, 1024)])
+@pytest.mark.parametrize("dt", ["int32", "u16", "fp32"])
+def test_minplus_tma_path_padded_ld(H, m, k, n, dt):
+    """B and C 16-byte addressable (leading dimensions padded to 8 elements): the TMA-fed product, with k in
+    several 64-wide chunks, ragged m, n not a multiple of 4 (the columns after the last 16-byte unit are merged
+    outside the int32 TMA reduction), and the padding columns of C left untouched."""
+    rng = np.random.default_rng(m * 7 + k * 3 + n)
+    A, B, C, exp = _minplus_inputs(rng, m, k, n, dt)
+    pad = lambda x: (x + 7) // 8 * 8
+    sentinel = 7
+    bufs = []
+    for X in (A, B, C):
+        P = np.full((X.shape[0], pad(X.shape[1])), sentinel, dtype=X.dtype)
+        P[:, :X.shape[1]] = X
+        bufs.append(dev(P))
+    Av, Bv, Cv = bufs[0][:, :k], bufs[1][:, :n], bufs[2][:, :n]
+    H.minplus(Av, Bv, Cv)
+    assert H.last_status() == 0
+    out = bufs[2].cpu().numpy()
+    assert (out[:, n:] == sentinel).all()
+    got = out[:, :n]
+    if dt == "fp32":
+        got = got.astype(np.float64)
+        np.testing.assert_array_equal(np.isinf(got), np.isinf(exp))
+        f = np.isfinite(exp)
+        np.testing.assert_allclose(got[f], exp[f], rtol=REL_TOL, atol=0)
+    else:
+        np.testing.assert_array_equal(got.astype(np.int64), exp)
+
+
+# ------------------------------------------------------------------ repeated squaring (Alg. 1)
+@pytest.mark.parametrize("n", [1, 2, 3, 65, 129, 300])
+@pytest.mark.parametrize("dt", ["int32", "u16", "fp32"])
+def test_squaring_solver_matches_oracle(H, n, dt):
+    s, d, w = er_edges(n, seed=n + 5, deg=3.0, wmax=40)
+    E = expect_fw(gen.dense_matrix(n, s, d, w, dtype=np.int32))
+    if dt == "int32":
+        D = H.solve_squaring(dt, dev(gen.dense_matrix(n, s, d, w, dtype=np.int32))).cpu().numpy().astype(np.int64)
+    elif dt == "u16":
+        D16 = H.solve_squaring(dt, dev(gen.dense_matrix(n, s, d, w, dtype=np.int16, inf=0x7FFF))).cpu().numpy()
+        D = oracle.unpack_u16(D16.view(np.uint16)).astype(np.int64)
+    else:
+        Df = H.solve_squaring(dt, dev(gen.dense_matrix(n, s, d, w, dtype=np.float32))).cpu().numpy()
+        D = np.where(np.isinf(Df), INF, Df.astype(np.float64)).astype(np.int64)  # small integers: exact
+    assert H.last_status() == 0
+    np.testing.assert_array_equal(D, E)
+
+
+@pytest.mark.parametrize("n,ld", [(130, 136), (200, 201)])
+def test_squaring_solver_directed_and_ld(H, n, ld):
+    """Directed input; a 16-byte addressable ld (TMA-fed product) and an odd one (the kernel without workspace)."""
+    s, d, w = er_edges(n, seed=ld, deg=3.0, wmax=90, directed=True)
+    W = dense_directed(n, s, d, w, ld=ld)
+    D = H.solve_squaring("int32", dev(W)).cpu().numpy()[:, :n]
+    assert H.last_status() == 0
+    np.testing.assert_array_equal(D.astype(np.int64), expect_fw(W))
+
+
 # ------------------------------------------------------------------ int32 solves, odd sizes
 @pytest.mark.parametrize("n", [1, 2, 3, 31, 33, 63, 64, 65, 127, 129, 200, 257, 513, 1000])
 def test_int32_solve_odd_sizes_bit_exact(H, n):
