@@ -596,42 +596,11 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
 }
 
 // ---------------------------------------------------------------- lookahead rounds
-// Round k's Phase-3 launch also runs round k+1's Phase 1, Phase 2 and (in
-// symmetric mode) panel publication, so that the next round's diagonal
-// closure and panels are ready when its Phase 3 starts instead of running as
-// near-idle launches in between (the diagonal blocks are the critical path of
-// the method, Sec. 4.4, Fig. 2).
-//
-// Work items are taken from a device counter in this order:
-//   the Phase-3 tiles that the next round's tasks read or write (tile row R'
-//   and tile column C' of the next diagonal block: "priority" tiles), the
-//   rest of the tiles, with the next round's tasks inserted into the stream:
-//   P1 after b1 tiles, the Phase-2 chunks after b2, the publication tasks
-//   after b3.
-// P1 waits until every priority tile is written, the Phase-2 chunks wait for
-// P1, the publication tasks for every Phase-2 chunk; each only waits for items
-// with smaller ids, which running CTAs have already taken, so the launch
-// always makes progress.  The next round's panels go to the other half of the
-// double panel buffer, so this round's operands are never overwritten.
-//
-// A next-round task runs on the 256 consumer threads and uses both stage
-// buffers (the producer takes no new item until it is done).
-template <class Op>
-struct RoundLA {
-  int64_t p0n, p1n;           // the next round's vertices [p0n, p1n)
-  uint32_t *colTn;            // the next round's panel (BK x ldT words)
-  typename Op::elem *rowPn;   // the next round's element panel (symmetric packed 16-bit), or nullptr
-  int *cnt;                   // this launch's counters: items taken, priority tiles done, P1 done, P2 done
-  int prio_ty, prio_tx;       // tile row R' and tile column C'
-  int row_x0;                 // priority tiles in row R': x in [row_x0, tiles_x)
-  int col_y1;                 // priority tiles in column C': y in [0, col_y1), y != R'
-  int n_prio;
-  int b1, b2, b3;             // positions of the next-round tasks in the tile stream
-  int n_p2row, p2_row_first, n_p2col, n_fin;
-  int64_t band_start_n, band_end_n;
-  int vec;
-};
-
+// Pieces of the next-round tasks that the Phase-3 kernel runs on its consumer
+// warps (fw_solve_ws): Phase 1, Phase-2 chunks shaped for 256 threads, and the
+// symmetric-mode panel publication.  A task runs on the 256 consumer threads
+// with the bounded group barrier below, in the C buffer (int32) or in the two
+// stage buffers (the producer takes no new item meanwhile).
 // Phase-2 shape for 256 threads (the consumer warps).
 template <class Op, int BK>
 struct LaP2 {
@@ -742,27 +711,132 @@ __device__ __noinline__ void la_task_fin(typename Op::elem *D, int64_t ld, int64
   }
 }
 
+// ---------------------------------------------------------------- all rounds in one launch
+// The lookahead scheme carried across the whole solve: one persistent launch
+// takes work items from one device counter, so round k+1's tiles start while
+// round k's last tiles finish, with no launch boundary between rounds.  Items
+// come in blocks: block 0 = round 0's Phase 1 and Phase-2 chunks; block j >= 1
+// = round j-1's Phase-3 tiles (first the priority tiles that round j's tasks
+// read or write: tile row R' and tile column C' of round j's diagonal block)
+// with round j's tasks inserted a few tile waves later (P1 two waves after the
+// priority tiles, the Phase-2 chunks four more, the publication three more),
+// padded to a common size (padding items are skipped).  Each item waits only for items
+// with smaller ids:
+//   tile of round k        <- every task of round k done (P1, P2 chunks,
+//                             publication); packed 16-bit / fp32 also the same
+//                             tile of round k-1 written (its C is loaded, merged
+//                             and stored, which must not overlap)
+//   P1 of round j          <- round j-1's priority tiles written, and every
+//                             tile of round j-2 written (those read the panel
+//                             buffer that round j overwrites, and carry the last
+//                             contributions the diagonal block needs)
+//   P2 chunks of round j   <- P1 of round j
+//   publication, round j   <- every P2 chunk of round j
+// int32 tiles of rounds k and k+1 may overlap on the same tile: both are TMA
+// min-reductions, which commute; and a tile of round k may read a row-panel
+// value that round k+1 has already lowered.  Every value is always a real path
+// length no larger than the one the sequential order would hold at that point,
+// so the result is the same exact matrix.
+template <class Op>
+struct SolvePlan {
+  int64_t n, ld, ldT;
+  int q, tiles_x, tiles_y, tiles_total, grid, sym, vec;
+  int block, base1;  // items per block j >= 1 (padded), items of block 0
+  uint32_t *colT[2];
+  typename Op::elem *rowP[2];
+  unsigned long long *items;  // work items taken (64-bit: blocks x block size can pass 2^31)
+  int *cnt;          // 6 per round r: [0] priority tiles for round r, [1] P1(r), [2] P2(r), [3] all tasks of r,
+                     // [4] tiles of round r written
+  int *tile_round;   // packed 16-bit / fp32: rounds written per tile
+};
+
+// Round j's tasks and the priority tiles (of round j-1) they depend on.
+struct SolveRound {
+  int64_t p0, p1, band_start, band_end;
+  int R, C, row_x0, col_y1, n_prio, n_p2row, p2_row_first, n_p2col, n_fin;
+  int b1, b2, b3, len_t, total;  // positions in block j, tile-stream length, items of block j
+};
+
+template <class Op, int BK>
+__host__ __device__ inline SolveRound solve_round(int64_t n, int q, int tiles_x, int tiles_y, int tiles_total, int grid,
+                                                  int sym, bool has_rowP, int j) {
+  using F = LaP2<Op, BK>;
+  SolveRound r{};
+  r.p0 = (int64_t)j * BK;
+  r.p1 = r.p0 + BK < n ? r.p0 + BK : n;
+  if (j >= q) {  // the last block: the final round's tiles, no tasks
+    r.len_t = tiles_total;
+    r.total = tiles_total;
+    r.R = -1;
+    r.C = -1;
+    r.b1 = r.b2 = r.b3 = tiles_total;
+    return r;
+  }
+  const int E = Op::EPW;
+  r.R = (int)(r.p0 / 128);
+  r.C = (int)(r.p0 / (128 * E));
+  r.row_x0 = sym ? r.C : 0;
+  r.col_y1 = sym ? (r.C * E + E < tiles_y ? r.C * E + E : tiles_y) : tiles_y;
+  r.n_prio = j == 0 ? 0 : (tiles_x - r.row_x0) + (r.col_y1 - (r.R < r.col_y1 ? 1 : 0));
+  const int nrow = (int)((n + F::ROW_BNW * E - 1) / (F::ROW_BNW * E));
+  const int ncol = (int)((n + F::COL_BM - 1) / F::COL_BM);
+  if (sym) {
+    r.p2_row_first = (int)(r.p1 / (F::ROW_BNW * E));
+    r.n_p2row = nrow - r.p2_row_first > 0 ? nrow - r.p2_row_first : 0;
+    r.n_p2col = (int)((r.p0 + F::COL_BM - 1) / F::COL_BM);
+  } else {
+    r.p2_row_first = 0;
+    r.n_p2row = nrow;
+    r.n_p2col = ncol;
+  }
+  r.band_start = (r.p0 / (128 * E)) * (128 * E);
+  r.band_end = r.band_start + 128 * E;
+  const int w = (int)(r.p1 - r.p0);
+  r.n_fin = 0;
+  if (sym && r.p0 > 0) r.n_fin = has_rowP ? (w + LA_FIN_ROWS - 1) / LA_FIN_ROWS : (r.p0 > r.band_start ? 1 : 0);
+  if (j == 0) {  // block 0: round 0's tasks only
+    r.len_t = 0;
+    r.b1 = r.b2 = r.b3 = 0;
+    r.total = 1 + r.n_p2row + r.n_p2col + r.n_fin;
+    return r;
+  }
+  r.len_t = r.n_prio + tiles_total;
+  r.b1 = r.n_prio + 2 * grid < r.len_t ? r.n_prio + 2 * grid : r.len_t;
+  r.b2 = r.b1 + 4 * grid < r.len_t ? r.b1 + 4 * grid : r.len_t;
+  r.b3 = r.b2 + 3 * grid < r.len_t ? r.b2 + 3 * grid : r.len_t;
+  r.total = r.len_t + 1 + r.n_p2row + r.n_p2col + r.n_fin;
+  return r;
+}
+
 template <class Op, int BK, bool RED>
 __global__ void __launch_bounds__(P3W_THREADS, 1)
-    fw_round_la(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                const __grid_constant__ CUtensorMap mapC, typename Op::elem *__restrict__ D, int64_t ld, int64_t n,
-                int64_t p0, int64_t p1, int tiles_x, int tiles_y, int tiles_total, int *err, int sym, int64_t ldT,
-                const RoundLA<Op> la) {
+    fw_solve_ws(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
+                const __grid_constant__ CUtensorMap mapB0, const __grid_constant__ CUtensorMap mapB1,
+                const __grid_constant__ CUtensorMap mapC, typename Op::elem *__restrict__ D, int *err,
+                const SolvePlan<Op> P) {
   constexpr int BM = 128, BNW = 128, TN = 8;
   using Map = TileMap<BM, BNW, TN>;
   constexpr int NCW = Map::THREADS / 32;
   static_assert(Map::THREADS == 256 && Map::THREADS + 32 == P3W_THREADS, "8 consumer warps + producer");
   constexpr int STAGE = P3T<BK>::STAGE_BYTES;
   static_assert(LaP2<Op, BK>::SMEM <= 2 * STAGE && (int)sizeof(P1Smem<Op, BK>) <= 2 * STAGE, "task memory");
+  constexpr bool TASK_IN_C = RED && LaP2<Op, BK>::SMEM <= P3T_C_BYTES && (int)sizeof(P1Smem<Op, BK>) <= P3T_C_BYTES;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_ab[2], empty_ab[2], full_c, cdone, cfree;
-  __shared__ int slot_kind[2], slot_info[2];
+  __shared__ int slot_kind[2], slot_info[2], slot_round[2];
   __shared__ int abort_flag;
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   auto stA = [&](int s) { return reinterpret_cast<uint32_t *>(base + s * STAGE); };
   auto stB = [&](int s) { return reinterpret_cast<uint32_t *>(base + s * STAGE) + BK * BM; };
   uint32_t *Cs = reinterpret_cast<uint32_t *>(base + 2 * STAGE);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t n = P.n, ld = P.ld;
+  const bool has_rowP = P.rowP[0] != nullptr;
+  auto cnt = [&](int r, int f) { return P.cnt + 6 * r + f; };
+  auto vload = [](const int *p) { return *reinterpret_cast<const volatile int *>(p); };
+  auto round_info = [&](int j) {
+    return solve_round<Op, BK>(n, P.q, P.tiles_x, P.tiles_y, P.tiles_total, P.grid, P.sym, has_rowP, j);
+  };
   if (tid == 0) {
     for (int i = 0; i < 2; ++i) {
       mbar_init(&full_ab[i], 1);
@@ -775,189 +849,255 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
     for (int w = 0; w < NCW; ++w) la_grp_par[w] = 0;
     la_grp_abort = 0;
     fence_barrier_init();
-    prefetch_tensormap(&mapA);
-    prefetch_tensormap(&mapB);
+    prefetch_tensormap(&mapA0);
+    prefetch_tensormap(&mapA1);
+    prefetch_tensormap(&mapB0);
+    prefetch_tensormap(&mapB1);
     prefetch_tensormap(&mapC);
     abort_flag = 0;
   }
   __syncthreads();
-  // int32: a next-round task runs in the C buffer (free once the previous
-  // tile's reduction has read it), so A/B prefetching goes on; otherwise it
-  // runs in the two stage buffers and the producer takes no item meanwhile
-  constexpr bool TASK_IN_C = RED && LaP2<Op, BK>::SMEM <= P3T_C_BYTES && (int)sizeof(P1Smem<Op, BK>) <= P3T_C_BYTES;
-  auto interior_of = [&](int64_t r0, int64_t c0) {
+  auto span = [&](int k, int64_t &p0, int64_t &p1) {
+    p0 = (int64_t)k * BK;
+    p1 = p0 + BK < n ? p0 + BK : n;
+  };
+  auto interior_of = [&](int k, int64_t r0, int64_t c0) {
+    int64_t p0, p1;
+    span(k, p0, p1);
     return r0 + BM <= n && c0 + BNW * Op::EPW <= n && (r0 + BM <= p0 || r0 >= p1) &&
            (c0 + BNW * Op::EPW <= p0 || c0 >= p1);
   };
-  auto is_prio = [&](int y, int x) {
-    return (y == la.prio_ty && x >= la.row_x0) || (x == la.prio_tx && y < la.col_y1);
+  // a bounded wait for a counter, by one thread; false: gave up
+  auto wait_count = [&](const int *c, int target) {
+    uint32_t spins = 0;
+    while (vload(c) < target) {
+      if (++spins > P3T_WAIT_LIMIT / 4) return false;
+      __nanosleep(64);
+    }
+    __threadfence();
+    return true;
   };
 
   if (warp == NCW) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
-      const int len_t = la.n_prio + tiles_total;
-      const int o1 = la.b1, o2 = la.b2 + 1, o3 = la.b3 + 1 + la.n_p2row + la.n_p2col;
-      const int n_p2 = la.n_p2row + la.n_p2col;
-      const int total = len_t + 1 + n_p2 + la.n_fin;
-      // tile-stream position -> packed tile (ty << 16 | tx), or -1 for a
-      // priority tile met again in the full list
-      auto stream_tile = [&](int j) -> int {
+      // tile-stream position -> packed tile, or -1 for a priority tile met again
+      auto stream_tile = [&](const SolveRound &r, int j) -> int {
         int y, x;
-        if (j < la.n_prio) {
-          const int nr = tiles_x - la.row_x0;
+        if (j < r.n_prio) {
+          const int nr = P.tiles_x - r.row_x0;
           if (j < nr) {
-            y = la.prio_ty;
-            x = la.row_x0 + j;
+            y = r.R;
+            x = r.row_x0 + j;
           } else {
             y = j - nr;
-            if (y >= la.prio_ty) ++y;  // column C' without row R'
-            x = la.prio_tx;
+            if (y >= r.R) ++y;
+            x = r.C;
           }
           return (y << 16) | x;
         }
-        const int idx = j - la.n_prio;
-        if (!sym) {
-          y = idx / tiles_x;
-          x = idx % tiles_x;
+        const int idx = j - r.n_prio;
+        if (!P.sym) {
+          y = idx / P.tiles_x;
+          x = idx % P.tiles_x;
         } else {
-          int lo = 0, hi = tiles_y - 1;
+          int lo = 0, hi = P.tiles_y - 1;
           while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (sym_prefix(mid, tiles_x, Op::EPW) <= idx) lo = mid;
+            if (sym_prefix(mid, P.tiles_x, Op::EPW) <= idx) lo = mid;
             else hi = mid - 1;
           }
           y = lo;
-          x = lo / Op::EPW + (int)(idx - sym_prefix(lo, tiles_x, Op::EPW));
+          x = lo / Op::EPW + (int)(idx - sym_prefix(lo, P.tiles_x, Op::EPW));
         }
-        return is_prio(y, x) ? -1 : ((y << 16) | x);
+        const bool prio = r.n_prio > 0 && ((y == r.R && x >= r.row_x0) || (x == r.C && y < r.col_y1));
+        return prio ? -1 : ((y << 16) | x);
       };
-      auto decode = [&](int item, int &kind, int &info) {
-        int j;
-        if (item >= total) {
-          kind = LA_END;
-          info = 0;
+      // item -> kind, round (tiles: their round; tasks: the round they build), info
+      auto decode = [&](long long item, int &kind, int &rnd, int &info) {
+        if (item < P.base1) {
+          const SolveRound r0 = round_info(0);
+          rnd = 0;
+          if (item == 0) { kind = LA_P1; info = 0; }
+          else if (item < 1 + r0.n_p2row + r0.n_p2col) { kind = LA_P2; info = (int)item - 1; }
+          else { kind = LA_SKIP; info = 0; }
           return;
         }
-        if (item < o1) j = item;
-        else if (item == o1) { kind = LA_P1; info = 0; return; }
-        else if (item < o2) j = item - 1;
-        else if (item < o2 + n_p2) { kind = LA_P2; info = item - o2; return; }
-        else if (item < o3) j = item - 1 - n_p2;
-        else if (item < o3 + la.n_fin) { kind = LA_FIN; info = item - o3; return; }
-        else j = item - 1 - n_p2 - la.n_fin;
-        const int tpk = stream_tile(j);
-        kind = tpk < 0 ? LA_SKIP : LA_TILE;
-        info = tpk;
+        const long long rel = item - P.base1;
+        const int j = 1 + (int)(rel / P.block), pos = (int)(rel % P.block);
+        if (j > P.q) { kind = LA_END; rnd = P.q; info = 0; return; }
+        const SolveRound r = round_info(j);
+        if (pos >= r.total) { kind = LA_SKIP; rnd = j; info = 0; return; }
+        const int n_p2 = r.n_p2row + r.n_p2col;
+        if (j < P.q) {
+          const int o1 = r.b1, o2 = r.b2 + 1, o3 = r.b3 + 1 + n_p2;
+          int t;
+          if (pos < o1) t = pos;
+          else if (pos == o1) { kind = LA_P1; rnd = j; info = 0; return; }
+          else if (pos < o2) t = pos - 1;
+          else if (pos < o2 + n_p2) { kind = LA_P2; rnd = j; info = pos - o2; return; }
+          else if (pos < o3) t = pos - 1 - n_p2;
+          else if (pos < o3 + r.n_fin) { kind = LA_FIN; rnd = j; info = pos - o3; return; }
+          else t = pos - 1 - n_p2 - r.n_fin;
+          const int pk = stream_tile(r, t);
+          kind = pk < 0 ? LA_SKIP : LA_TILE;
+          rnd = j - 1;
+          info = pk;
+        } else {
+          kind = LA_TILE;
+          rnd = j - 1;
+          info = stream_tile(r, pos);
+        }
       };
-      int rk[4], rt[4];  // kind and packed tile of the last four slots
-      int claimed = 0, hold = -1, c_next = 0;
+      // The producer never blocks on another item: a claimed tile whose round's
+      // panels are not complete yet waits in the queue [issued, claimed) (slots
+      // are issued strictly in order, as the stage barriers require), and so does
+      // a C load whose tile has not been written by the previous round; both are
+      // retried inside every wait below.  Blocking on them could wait for a tile
+      // this producer has not published yet.
+      int rk[4], rt[4], rr[4];  // kind, packed tile / task index and round of the last four slots
+      int claimed = 0, issued = 0, hold = -1, c_next = 0;
       int n_ab[2] = {0, 0}, n_c = 0;
+      int ready = -1;  // rounds up to this one have every task done
       bool stop = false, ok = true, cs_free = true;
-      // items already taken and not yet used, in increasing order (the launch
-      // starts by taking two at once); a CTA uses its items in increasing order
-      int q0 = -1, q1 = -1;
-      auto next_item = [&]() {
-        if (q0 < 0) return atomicAdd(la.cnt + 0, 1);
-        const int r = q0;
+      long long q0 = -1, q1 = -1;  // items taken and not yet used, in increasing order
+      auto next_item = [&]() -> long long {
+        if (q0 < 0) return (long long)atomicAdd(P.items, 1ull);
+        const long long r = q0;
         q0 = q1;
         q1 = -1;
         return r;
       };
+      auto panels_ready = [&](int k) {  // non-blocking
+        if (k <= ready) return true;
+        const SolveRound r = round_info(k);
+        if (vload(cnt(k, 3)) < 1 + r.n_p2row + r.n_p2col + r.n_fin) return false;
+        __threadfence();
+        fence_proxy_async_global();  // the panels written by other CTAs are read by TMA next
+        ready = k;
+        return true;
+      };
+      auto issue_slots = [&]() {  // non-blocking, in slot order
+        while (issued < claimed) {
+          const int slot = issued, s = slot & 1, kind = rk[slot & 3], info = rt[slot & 3], rnd = rr[slot & 3];
+          if (kind == LA_TILE) {
+            if (!panels_ready(rnd)) return;
+            int64_t p0, p1;
+            span(rnd, p0, p1);
+            const CUtensorMap *mA = (rnd & 1) ? &mapA1 : &mapA0;
+            const CUtensorMap *mB = (rnd & 1) ? &mapB1 : &mapB0;
+            mbar_arrive_expect_tx(&full_ab[s], STAGE);
+            tma_load_2d(stA(s), mA, &full_ab[s], (info >> 16) * BM, 0);
+            tma_load_2d(stB(s), mB, &full_ab[s], (info & 0xFFFF) * BNW * Op::EPW, P.sym ? 0 : (int)p0);
+          } else {
+            mbar_arrive(&full_ab[s]);  // a task or the end: no data
+          }
+          if (s == 0) ++n_ab[0];
+          else ++n_ab[1];
+          ++issued;
+        }
+      };
+      auto issue_c = [&]() {  // !RED, non-blocking: the next tile's C once the C buffer is free and the tile's
+                              // previous round is written
+        if (RED) return;
+        while (c_next < claimed && rk[c_next & 3] != LA_TILE) ++c_next;
+        if (!cs_free || c_next >= claimed) return;
+        const int pk = rt[c_next & 3], k = rr[c_next & 3];
+        if (vload(P.tile_round + (pk >> 16) * P.tiles_x + (pk & 0xFFFF)) < k) return;
+        __threadfence();
+        fence_proxy_async_global();
+        mbar_arrive_expect_tx(&full_c, P3T_C_BYTES);
+        tma_load_2d(Cs, &mapC, &full_c, (pk & 0xFFFF) * BNW * Op::EPW, (pk >> 16) * BM);
+        ++n_c;
+        cs_free = false;
+        ++c_next;
+      };
+      auto progress = [&]() {
+        issue_slots();
+        issue_c();
+      };
+      auto wait_bar = [&](uint64_t *bar, uint32_t parity) {  // bounded, making progress meanwhile
+        for (uint32_t it = 0; it < P3T_WAIT_LIMIT; ++it) {
+          if (mbar_try_wait(bar, parity)) return true;
+          progress();
+        }
+        return false;
+      };
       auto claim = [&]() {
-        const int slot = claimed, s = slot & 1;
-        int kind, info;
+        const int slot = claimed;
+        int kind, rnd, info;
         do {
-          decode(next_item(), kind, info);
+          decode(next_item(), kind, rnd, info);
         } while (kind == LA_SKIP);
-        slot_kind[s] = kind;
-        slot_info[s] = info;
         rk[slot & 3] = kind;
         rt[slot & 3] = info;
-        if (kind == LA_TILE) {
-          mbar_arrive_expect_tx(&full_ab[s], STAGE);
-          tma_load_2d(stA(s), &mapA, &full_ab[s], (info >> 16) * BM, 0);
-          tma_load_2d(stB(s), &mapB, &full_ab[s], (info & 0xFFFF) * BNW * Op::EPW, sym ? 0 : (int)p0);
-        } else {
-          mbar_arrive(&full_ab[s]);  // a task or the end: no data
-        }
-        if (s == 0) ++n_ab[0];
-        else ++n_ab[1];
+        rr[slot & 3] = rnd;
         if (kind == LA_END) stop = true;
         else if (kind != LA_TILE && !TASK_IN_C) hold = slot;
         ++claimed;
+        // the consumers read the slot's kind after its full barrier completes,
+        // which happens only once it is issued (in order)
+        slot_kind[slot & 1] = kind;
+        slot_info[slot & 1] = info;
+        slot_round[slot & 1] = rnd;
+        progress();
       };
-      auto issue_c = [&]() {  // !RED: the next tile's C once the C buffer is free
-        while (c_next < claimed && rk[c_next & 3] != LA_TILE) ++c_next;
-        if (!RED && cs_free && c_next < claimed) {
-          const int pk = rt[c_next & 3];
-          mbar_arrive_expect_tx(&full_c, P3T_C_BYTES);
-          tma_load_2d(Cs, &mapC, &full_c, (pk & 0xFFFF) * BNW * Op::EPW, (pk >> 16) * BM);
-          ++n_c;
-          cs_free = false;
-          ++c_next;
-        }
-      };
-      q0 = atomicAdd(la.cnt + 0, 2);
+      q0 = (long long)atomicAdd(P.items, 2ull);
       q1 = q0 + 1;
       claim();
       if (!stop && hold < 0) claim();
-      if (!RED) issue_c();
-      for (int i = 0;; ++i) {
+      for (int i = 0; ok; ++i) {
         const int kind = rk[i & 3], s = i & 1;
-        if (kind == LA_END) break;
-        if (!mbar_wait_bounded(&empty_ab[s], (uint32_t)(i >> 1) & 1u, P3T_WAIT_LIMIT)) {
+        if (kind == LA_END) {
+          // the end slot (and anything before it) must reach the consumers
+          uint32_t it = 0;
+          while (issued < claimed && ++it < P3T_WAIT_LIMIT) progress();
+          ok = issued == claimed;
+          break;
+        }
+        if (!wait_bar(&empty_ab[s], (uint32_t)(i >> 1) & 1u)) {
           ok = false;
           break;
         }
-        if (!stop && hold < 0 && claimed < i + 3) {
-          claim();
-          if (!RED) issue_c();
-        }
-        if (!mbar_wait_bounded(&cdone, (uint32_t)i & 1u, P3T_WAIT_LIMIT)) {
+        if (!stop && hold < 0 && claimed < i + 3) claim();
+        if (!wait_bar(&cdone, (uint32_t)i & 1u)) {
           ok = false;
           break;
         }
         if (kind == LA_TILE) {
-          const int pk = rt[i & 3];
+          const int pk = rt[i & 3], k = rr[i & 3];
           const int ty_ = pk >> 16, tx_ = pk & 0xFFFF;
           const int r0 = ty_ * BM, c0 = tx_ * BNW * Op::EPW;
-          const bool prio = is_prio(ty_, tx_);
           if (RED) {
             if (c0 < red_cols(n)) {  // mapC ends at red_cols(n) in this mode
               tma_reduce_min_2d(&mapC, Cs, c0, r0);
               bulk_commit();
-              if (prio) {
-                bulk_wait_all();
-                fence_proxy_async_global();
-              } else {
-                bulk_wait_read_all();
-              }
+              bulk_wait_all();
+              fence_proxy_async_global();
             }
             mbar_arrive(&cfree);
           } else {
-            if (interior_of(r0, c0)) {
+            if (interior_of(k, r0, c0)) {
               tma_store_2d(&mapC, Cs, c0, r0);
               bulk_commit();
-              if (prio) {
-                bulk_wait_all();
-                fence_proxy_async_global();
-              } else {
-                bulk_wait_read_all();
-              }
+              bulk_wait_all();
+              fence_proxy_async_global();
             }
             cs_free = true;
-            issue_c();
           }
-          if (prio) {
-            __threadfence();
-            atomicAdd(la.cnt + 1, 1);
+          // the tile of round k is written: publish it
+          __threadfence();
+          if (!RED) atomicExch(P.tile_round + ty_ * P.tiles_x + tx_, k + 1);
+          atomicAdd(cnt(k, 4), 1);
+          if (k + 1 < P.q) {
+            const SolveRound r = round_info(k + 1);
+            if ((ty_ == r.R && tx_ >= r.row_x0) || (tx_ == r.C && ty_ < r.col_y1)) atomicAdd(cnt(k + 1, 0), 1);
           }
+          progress();
         } else if (!TASK_IN_C) {
-          // a next-round task finished: both stage buffers are free again
+          // a task finished: both stage buffers are free again
           hold = -1;
           while (!stop && hold < 0 && claimed < i + 3) claim();
-          if (!RED) issue_c();
         }
       }
       bulk_wait_all();
@@ -971,19 +1111,16 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
   } else {
     // ------------------------------------------------------------ consumers
     const int tx = tid % Map::TX, ty = tid / Map::TX;
-    const int n_p2 = la.n_p2row + la.n_p2col;
     uint32_t acc[8][TN];
     int ct = 0;  // tiles done by this CTA
     for (int i = 0;; ++i) {
       const int s = i & 1;
-      // warps go on independently; a warp that gives up leaves, and the
-      // next-round tasks synchronize only through bounded waits (GroupBar)
       const bool bad = !mbar_wait_bounded(&full_ab[s], (uint32_t)(i >> 1) & 1u, P3T_WAIT_LIMIT);
       if (__any_sync(0xffffffffu, bad)) {
         if (lane == 0) abort_flag = 1;
         break;
       }
-      const int kind = slot_kind[s], info = slot_info[s];
+      const int kind = slot_kind[s], info = slot_info[s], rnd = slot_round[s];
       if (kind == LA_END) break;
       if (kind == LA_TILE) {
         const int cty = info >> 16, ctx = info & 0xFFFF;
@@ -1013,7 +1150,9 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
         } else {
           ebad = !mbar_wait_bounded(&full_c, (uint32_t)ct & 1u, P3T_WAIT_LIMIT);
           if (!__any_sync(0xffffffffu, ebad)) {
-            const bool interior = interior_of(r0, c0);
+            int64_t p0, p1;
+            span(rnd, p0, p1);
+            const bool interior = interior_of(rnd, r0, c0);
 #pragma unroll
             for (int r = 0; r < 8; ++r)
 #pragma unroll
@@ -1037,10 +1176,8 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
           break;
         }
       } else {
-        // a next-round task
+        // a task of round rnd
         if (TASK_IN_C) {
-          // the stage is not used: hand it back at once; the task needs the
-          // C buffer, free once the previous tile's reduction has read it
           __syncwarp();
           if (lane == 0) mbar_arrive(&empty_ab[s]);
           const bool cb = ct > 0 && !mbar_wait_bounded(&cfree, (uint32_t)(ct - 1) & 1u, P3T_WAIT_LIMIT);
@@ -1049,30 +1186,18 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
             break;
           }
         }
-        int *dep = nullptr;
-        int target = 0;
-        if (kind == LA_P1) {
-          dep = la.cnt + 1;
-          target = la.n_prio;
-        } else if (kind == LA_P2) {
-          dep = la.cnt + 2;
-          target = 1;
-        } else {
-          dep = la.cnt + 3;
-          target = n_p2;
-        }
-        // each warp waits (bounded) for the task's inputs
+        const SolveRound r = round_info(rnd);
+        const int n_p2 = r.n_p2row + r.n_p2col;
         bool dbad = false;
         if (lane == 0) {
-          uint32_t spins = 0;
-          while (*reinterpret_cast<volatile int *>(dep) < target) {
-            if (++spins > P3T_WAIT_LIMIT / 4) {
-              dbad = true;
-              break;
-            }
-            __nanosleep(64);
+          if (kind == LA_P1) {
+            if (rnd >= 1) dbad = !wait_count(cnt(rnd, 0), r.n_prio);
+            if (!dbad && rnd >= 2) dbad = !wait_count(cnt(rnd - 2, 4), P.tiles_total);
+          } else if (kind == LA_P2) {
+            dbad = !wait_count(cnt(rnd, 1), 1);
+          } else {
+            dbad = !wait_count(cnt(rnd, 2), n_p2);
           }
-          __threadfence();
         }
         if (__any_sync(0xffffffffu, dbad)) {
           la_grp_abort = 1;
@@ -1085,15 +1210,17 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
           break;
         }
         uint32_t *tsm = TASK_IN_C ? Cs : reinterpret_cast<uint32_t *>(base);
+        uint32_t *colT = P.colT[rnd & 1];
+        typename Op::elem *rowP = P.rowP[rnd & 1];
         if (kind == LA_P1) {
-          la_task_p1<Op, BK>(D, ld, n, la.p0n, la.colTn, ldT, la.rowPn, tsm, tid);
+          la_task_p1<Op, BK>(D, ld, n, r.p0, colT, P.ldT, rowP, tsm, tid);
         } else if (kind == LA_P2) {
-          la_task_p2<Op, BK>(D, ld, n, la.p0n, la.p1n, la.colTn, ldT, info, la.n_p2row, la.p2_row_first,
-                             la.vec != 0, SymPanel<Op>{la.rowPn, la.band_end_n}, sym != 0, tsm, tid);
+          la_task_p2<Op, BK>(D, ld, n, r.p0, r.p1, colT, P.ldT, info, r.n_p2row, r.p2_row_first, P.vec != 0,
+                             SymPanel<Op>{rowP, r.band_end}, P.sym != 0, tsm, tid);
         } else {
-          const int rows = la.rowPn ? LA_FIN_ROWS : BK;
-          la_task_fin<Op>(D, ld, n, la.p0n, la.colTn, ldT, la.rowPn, la.band_start_n, info * rows,
-                          min((int)(la.p1n - la.p0n), (info + 1) * rows), tid);
+          const int rows = rowP ? LA_FIN_ROWS : BK;
+          la_task_fin<Op>(D, ld, n, r.p0, colT, P.ldT, rowP, r.band_start, info * rows,
+                          min((int)(r.p1 - r.p0), (info + 1) * rows), tid);
         }
         fence_proxy_async_smem();  // the task's shared memory is refilled by TMA next
         GroupBar::sync();          // every consumer's writes of the task are done
@@ -1101,9 +1228,11 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
           if (lane == 0) abort_flag = 1;
           break;
         }
-        if (tid == 0 && kind != LA_FIN) {
+        if (tid == 0) {
           __threadfence();
-          atomicAdd(la.cnt + (kind == LA_P1 ? 2 : 3), 1);
+          if (kind == LA_P1) atomicAdd(cnt(rnd, 1), 1);
+          else if (kind == LA_P2) atomicAdd(cnt(rnd, 2), 1);
+          atomicAdd(cnt(rnd, 3), 1);
         }
         if (!TASK_IN_C) {
           __syncwarp();
@@ -1539,7 +1668,6 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
   uint32_t *colTb[2], *colT = static_cast<uint32_t *>(colTv);
   colTb[0] = colT;
   colTb[1] = la_on ? colT + (int64_t)kMaxRoundWidth * ldT : colT;
-  int *cnt = la_on ? reinterpret_cast<int *>(colT + 2 * (int64_t)kMaxRoundWidth * ldT) : nullptr;
   // symmetric mode: the element panel (B operand of Phase 3) is colT itself
   // for 32-bit elements, a separate BK x ldT buffer for packed 16-bit
   Elem *rowP = sym ? (Op::EPW == 2 ? static_cast<Elem *>(rowPv) : nullptr) : nullptr;
@@ -1586,10 +1714,6 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(fw_phase3_ws<Op, BK, Op::DTYPE == 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  P3T<BK>::SMEM);
-      if constexpr (kLookaheadWidth<BK>)
-        if (e == cudaSuccess && la_on)
-          e = cudaFuncSetAttribute(fw_round_la<Op, BK, Op::DTYPE == 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   P3T<BK>::SMEM);
       if (e != cudaSuccess) return e;
     }
   }
@@ -1680,63 +1804,50 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
       if (tm) tm->after(2, s, p3_work(k));
     }
   } else if constexpr (kLookaheadWidth<BK>) {
-    using F = LaP2<Op, BK>;
-    e = cudaMemsetAsync(cnt, 0, sizeof(int) * 4 * (size_t)q, s);
-    if (e != cudaSuccess) return e;
-    panels(0, colTb[0], rowPb[0]);
-    const int nrow_la = (int)((n + F::ROW_BNW * Op::EPW - 1) / (F::ROW_BNW * Op::EPW));
-    const int ncol_la = (int)((n + F::COL_BM - 1) / F::COL_BM);
-    for (int64_t k = 0; k < q; ++k) {
-      const int b = (int)(k & 1);
-      int64_t p0, p1;
-      span(k, p0, p1);
-      if (tm) tm->before(2, s);
-      double work = p3_work(k);
-      if (k + 1 == q) {
-        fw_phase3_ws<Op, BK, Op::DTYPE == 0><<<grid_tma, P3W_THREADS, P3T<BK>::SMEM, s>>>(
-            mA[b], mB[b], mC, D, ld, n, p0, p1, tiles_x, tiles_total, err, sym ? 1 : 0, tiles_y);
-      } else {
-        RoundLA<Op> la{};
-        span(k + 1, la.p0n, la.p1n);
-        la.colTn = colTb[b ^ 1];
-        la.rowPn = rowPb[b ^ 1];
-        la.cnt = cnt + 4 * k;
-        la.prio_ty = (int)(la.p0n / 128);
-        la.prio_tx = (int)(la.p0n / (128 * Op::EPW));
-        la.row_x0 = sym ? la.prio_tx : 0;
-        la.col_y1 = sym ? std::min(tiles_y, la.prio_tx * Op::EPW + Op::EPW) : tiles_y;
-        la.n_prio = (tiles_x - la.row_x0) + (la.col_y1 - (la.prio_ty < la.col_y1 ? 1 : 0));
-        if (sym) {
-          la.p2_row_first = (int)(la.p1n / (F::ROW_BNW * Op::EPW));
-          la.n_p2row = std::max(0, nrow_la - la.p2_row_first);
-          la.n_p2col = (int)((la.p0n + F::COL_BM - 1) / F::COL_BM);
-        } else {
-          la.p2_row_first = 0;
-          la.n_p2row = nrow_la;
-          la.n_p2col = ncol_la;
-        }
-        la.band_start_n = (la.p0n / (128 * Op::EPW)) * (128 * Op::EPW);
-        la.band_end_n = la.band_start_n + 128 * Op::EPW;
-        const int wn = (int)(la.p1n - la.p0n);
-        la.n_fin = 0;
-        if (sym && la.p0n > 0)
-          la.n_fin = la.rowPn ? (wn + LA_FIN_ROWS - 1) / LA_FIN_ROWS : (la.p0n > la.band_start_n ? 1 : 0);
-        const int len_t = la.n_prio + tiles_total;
-        // items are taken about grid_tma per tile time: P1 two tile times after
-        // the priority tiles (which are written by then), the Phase-2 chunks four
-        // more (P1 done), the publication three more (the chunks done)
-        la.b1 = std::min(len_t, la.n_prio + 2 * grid_tma);
-        la.b2 = std::min(len_t, la.b1 + 4 * grid_tma);
-        la.b3 = std::min(len_t, la.b2 + 3 * grid_tma);
-        la.vec = vec ? 1 : 0;
-        fw_round_la<Op, BK, Op::DTYPE == 0><<<grid_tma, P3W_THREADS, P3T<BK>::SMEM, s>>>(
-            mA[b], mB[b], mC, D, ld, n, p0, p1, tiles_x, tiles_y, tiles_total, err, sym ? 1 : 0, ldT, la);
-        const double w1 = (double)wn, rest1 = (double)(n - wn);
-        work += w1 * w1 * w1 + (sym ? rest1 * w1 * w1 : 2.0 * rest1 * w1 * w1);
-      }
-      if (launches) *launches += 1;
-      if (tm) tm->after(2, s, work);
+    // every round in one persistent launch (fw_solve_ws)
+    constexpr bool RED = Op::DTYPE == 0;
+    SolvePlan<Op> P{};
+    P.n = n;
+    P.ld = ld;
+    P.ldT = ldT;
+    P.q = (int)q;
+    P.tiles_x = tiles_x;
+    P.tiles_y = tiles_y;
+    P.tiles_total = tiles_total;
+    P.grid = grid_tma;
+    P.sym = sym ? 1 : 0;
+    P.vec = vec ? 1 : 0;
+    P.colT[0] = colTb[0];
+    P.colT[1] = colTb[1];
+    P.rowP[0] = rowPb[0];
+    P.rowP[1] = rowPb[1];
+    char *cbase = reinterpret_cast<char *>(colT) + lookahead_counter_offset(ldT);
+    P.items = reinterpret_cast<unsigned long long *>(cbase);
+    P.cnt = reinterpret_cast<int *>(cbase + 16);
+    P.tile_round = P.cnt + 6 * q;
+    const bool has_rowP = rowPb[0] != nullptr;
+    P.base1 = solve_round<Op, BK>(n, P.q, tiles_x, tiles_y, tiles_total, grid_tma, P.sym, has_rowP, 0).total;
+    P.block = 0;
+    double work = 0.0;
+    for (int j = 1; j <= P.q; ++j) {
+      const SolveRound r = solve_round<Op, BK>(n, P.q, tiles_x, tiles_y, tiles_total, grid_tma, P.sym, has_rowP, j);
+      P.block = std::max(P.block, r.total);
+      work += p3_work(j - 1);
     }
+    for (int j = 0; j < P.q; ++j) {  // Phase 1 and Phase 2 of every round run inside the launch too
+      int64_t p0, p1;
+      span(j, p0, p1);
+      const double w1 = (double)(p1 - p0), rest1 = (double)(n - (p1 - p0));
+      work += w1 * w1 * w1 + (sym ? rest1 * w1 * w1 : 2.0 * rest1 * w1 * w1);
+    }
+    e = cudaMemsetAsync(cbase, 0, 16 + sizeof(int) * (6 * (size_t)q + (RED ? 0 : (size_t)tiles_x * tiles_y)), s);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fw_solve_ws<Op, BK, RED>, cudaFuncAttributeMaxDynamicSharedMemorySize, P3T<BK>::SMEM);
+    if (e != cudaSuccess) return e;
+    if (tm) tm->before(2, s);
+    fw_solve_ws<Op, BK, RED><<<grid_tma, P3W_THREADS, P3T<BK>::SMEM, s>>>(mA[0], mA[1], mB[0], mB[1], mC, D, err, P);
+    if (launches) *launches += 1;
+    if (tm) tm->after(2, s, work);
   }
   if (sym && q > 1) {  // the lower triangle from the upper
     const dim3 gm((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));

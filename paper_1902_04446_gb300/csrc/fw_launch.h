@@ -42,12 +42,15 @@ constexpr int64_t kMaxRoundWidth = 64;  // panel buffers are sized for this
 
 // Bytes of the colT panel buffer launch_rounds needs for n (ldT = its row
 // pitch in words): one kMaxRoundWidth x ldT panel of 32-bit words, or with
-// lookahead two of them and 4 counters per round (round width >= 32).
+// lookahead two of them, a 64-bit item counter, 6 counters per round (round
+// width >= 32) and one per Phase-3 tile.
+inline size_t lookahead_counter_offset(int64_t ldT) { return 2 * (size_t)kMaxRoundWidth * (size_t)ldT * 4; }
 inline size_t panel_buffer_bytes(int64_t n, int64_t ldT, bool lookahead) {
   const size_t one = (size_t)kMaxRoundWidth * (size_t)ldT * 4;
   if (!lookahead) return one;
   const size_t rounds = (size_t)((n + 31) / 32) + 1;
-  return 2 * one + 4 * sizeof(int) * rounds;
+  const size_t tiles = (size_t)((n + 127) / 128) * (size_t)((n + 127) / 128);
+  return 2 * one + 16 + sizeof(int) * (6 * rounds + tiles);
 }
 // Bytes of the element panel (symmetric mode, packed 16-bit).
 inline size_t row_panel_bytes(int64_t ldT, bool lookahead) {

@@ -84,6 +84,35 @@ def test_serving_mixed_equals_alone_and_oracle(H):
         np.testing.assert_array_equal(o.numpy().astype(np.int64), oracle.fw(W.astype(np.int64)))
 
 
+def test_serving_large_requests_on_round_kernels(H):
+    """Requests with n >= 1536 take their own group on the per-round (lookahead) kernels, an undirected one in
+    symmetric mode and a directed one on the general path; mixed with small batched requests, each result equals
+    the same matrix solved alone and the oracle's (Dijkstra from every source)."""
+    rng = np.random.default_rng(1536)
+    cases = []
+    for n, directed in ((1600, False), (1700, True), (300, False), (2100, False), (500, True)):
+        m = int(4 * n)
+        s = rng.integers(0, n, m); d = rng.integers(0, n, m); keep = s != d
+        s, d = s[keep], d[keep]
+        w = rng.integers(1, 500, s.shape[0])
+        W = gen.dense_matrix(n, s, d, w, dtype=np.int32, directed=directed)
+        cases.append((W, s, d, w, directed))
+    tickets = [H.submit(dev(W)) for W, *_ in cases]
+    for t, (W, s, d, w, directed) in zip(tickets, cases):
+        n = W.shape[0]
+        assert H.wait(t, 120000) == 0
+        st, ptr, rc = H.poll(t)
+        assert st == 3 and rc == 0 and ptr
+        out = torch.empty((n, n), dtype=torch.int32, device="cuda")
+        H.fetch(t, out)
+        torch.cuda.synchronize()
+        assert H.release(t) == 0
+        alone = H.solve_t("int32", dev(W))
+        assert torch.equal(out, alone)
+        exp = oracle.dijkstra(n, s, d, w, np.arange(n), directed=directed)
+        np.testing.assert_array_equal(out.cpu().numpy().astype(np.int64), exp)
+
+
 def test_serving_budget_admission_busy_cancel(lib):
     big = er_dense(1000, 5)
     small = [er_dense(n, n) for n in (300, 320, 340)]  # each larger than the big one's panel buffer
