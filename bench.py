@@ -401,14 +401,15 @@ def run_gpu(args):
     peak = ADDMIN_LANES_PER_CLK_PER_SM * sms * sm_max_mhz * 1e6 / 1e9
     phase_ms = {f"phase{p}": round(prof[p][1] / args.steps, 3) for p in (1, 2, 3)}
     roofline = {"bound": "alu",
-                "kernel": "fw_round_la<int32> (Phase 3 of round k with round k+1's Phase 1 and Phase 2 as tasks)",
+                "kernel": "fw_solve_ws<int32> (every round in one launch: Phase-3 tiles with each round's "
+                          "Phase 1 and Phase 2 as tasks)",
                 "achieved": achieved, "peak": peak, "unit": UNIT,
-                "work": "relaxations performed in the launches: Phase 3 (in symmetric mode only the tiles touching "
-                        "the upper triangle) plus the next round's Phase 1 and Phase 2",
+                "work": "relaxations performed in the launch: Phase 3 (in symmetric mode only the tiles touching "
+                        "the upper triangle) plus every round's Phase 1 and Phase 2",
                 "frac": (achieved / peak) if achieved else None,
                 "peak_basis": f"{ADDMIN_LANES_PER_CLK_PER_SM} add-min lanes/clk/SM (measured) x {sms} SMs x "
                               f"{sm_max_mhz:.0f} MHz (max SM clock)",
-                "traffic": ncu_traffic(f"fw_round_la_int32_{args.workload}"),
+                "traffic": ncu_traffic(f"fw_solve_ws_int32_{args.workload}"),
                 "phase_ms_per_step": phase_ms,
                 "phase3_share_of_step": prof[3][1] / ms if ms else None}
     if clocks and achieved:
@@ -586,10 +587,10 @@ def run_round_shapes(args):
     Wd = dense_on_device(torch, g, torch.int32, 1073741823, 0)
     Dd = torch.empty_like(Wd)
     names = {1: "one CTA per tile", 2: "TMA, 256 threads", 3: "TMA, 512 threads",
-             4: "warp-specialized (lookahead rounds at width 64)"}
+             4: "warp-specialized, one launch per round", 5: "warp-specialized, every round in one launch"}
     peak = ADDMIN_LANES_PER_CLK_PER_SM * torch.cuda.get_device_properties(0).multi_processor_count * 2070.0 / 1e3
     for bk in (32, 64):
-        for v in (1, 2, 3, 4):
+        for v in (1, 2, 3, 4, 5):
             with apsp.Handle(device=0, block_k=bk, phase3_variant=v) as h:
                 ms, launches, prof = timed_solves(torch, h, "int32", Wd, Dd, args.steps, args.warmup, None,
                                                   profile=True)

@@ -80,10 +80,12 @@ typedef struct {
   int queue_depth;       /* serving: pending requests before APSP_E_BUSY (default 4096) */
   int64_t memory_budget; /* serving: bytes of device memory for admitted requests (0 = free HBM - reserve) */
   int64_t spin_limit;    /* bounded device waits: iterations before APSP_E_TIMEOUT (0 = default) */
-  int phase3_variant;    /* Phase-3 kernel: 0 = tuned or default, 1 = one CTA per tile, 2 = persistent
-                            TMA kernel with 256 threads, 3 = persistent TMA kernel with 512 threads,
-                            4 = warp-specialized persistent kernel (TMA producer warp; int32 results
-                            leave by a TMA min-reduction) -- the default */
+  int phase3_variant;    /* Phase-3 kernel: 0 = tuned, else by n (5 from n = 3072, 4 below), 1 = one
+                            CTA per tile, 2 = persistent TMA kernel with 256 threads, 3 = persistent TMA
+                            kernel with 512 threads, 4 = warp-specialized persistent kernel (TMA producer
+                            warp; int32 results leave by a TMA min-reduction), one launch per round,
+                            5 = the same kernel running every round in one launch with each round's
+                            Phase 1 and Phase 2 as tasks inside it (round width 64) */
   int symmetric;         /* symmetric mode for undirected graphs (Sec. 3: A_ij = A_ji; the paper keeps
                             only the upper triangle): Phase 3 updates only the tiles touching the upper
                             triangle and the lower triangle is mirrored at the end -- same result, about
@@ -239,8 +241,8 @@ apsp_status apsp_cancel(apsp_handle *h, uint64_t ticket);
 /* The paper picks its block size b per problem size (Sec. 3 "user-provided
  * (or auto-tuned)", Sec. 5.2-5.4, Table 3).  For `dtype` and every n bucket
  * (powers of two from 128 up to n_max) this times the candidate round shapes
- * -- round width Bk in {32, 64} x Phase-3 variant (the persistent TMA kernels
- * or one CTA per tile) -- on a synthetic matrix generated on the device (the
+ * -- round width Bk in {32, 64} x Phase-3 variant (the persistent TMA kernels,
+ * per round or all rounds in one launch, or one CTA per tile) -- on a synthetic matrix generated on the device (the
  * kernels do the same work for any graph of a given n), and keeps the
  * fastest for later solves on this handle.  cache_path (nullable): a JSON
  * file keyed by GPU name; entries for this GPU are loaded instead of timing
@@ -249,7 +251,8 @@ apsp_status apsp_autotune(apsp_handle *h, int dtype, int64_t n_max, const char *
 
 /* The round shape the handle uses for (dtype, n): *block_k and *tma, the
  * Phase-3 kernel numbered as apsp_config.phase3_variant minus one (0 = one
- * CTA per tile, 1-3 = the persistent TMA kernels). */
+ * CTA per tile, 1-3 = the persistent TMA kernels launched per round, 4 = every
+ * round in one launch). */
 apsp_status apsp_tuned_config(apsp_handle *h, int dtype, int64_t n, int *block_k, int *tma);
 
 /* ---- solve without allocation -------------------------------------------- */

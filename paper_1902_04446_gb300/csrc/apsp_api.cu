@@ -214,6 +214,7 @@ int64_t bucket_of(int64_t n) {
 // largest tuned bucket for larger n), else Bk = 64 with the TMA Phase 3.
 apsp::RoundConfig config_for(apsp_handle *h, int dtype, int64_t n) {
   apsp::RoundConfig c;
+  c.p3 = apsp::default_phase3(n);
   const int64_t b = bucket_of(n);
   auto it = h->tuned.find({dtype, b});
   if (it != h->tuned.end()) {
@@ -226,7 +227,7 @@ apsp::RoundConfig config_for(apsp_handle *h, int dtype, int64_t n) {
       }
   }
   if (h->cfg.block_k == 32 || h->cfg.block_k == 64) c.bk = h->cfg.block_k;
-  if (h->cfg.phase3_variant >= 1 && h->cfg.phase3_variant <= 4) c.p3 = h->cfg.phase3_variant - 1;
+  if (h->cfg.phase3_variant >= 1 && h->cfg.phase3_variant <= 5) c.p3 = h->cfg.phase3_variant - 1;
   return c;
 }
 
@@ -236,8 +237,7 @@ apsp_status run_rounds_locked(apsp_handle *h, int dtype, void *D, int64_t n, int
                               bool known_sym = false) {
   const int64_t ldT = panel_ld(n);
   apsp::RoundConfig rc = config_for(h, dtype, n);
-  rc.lookahead = rc.p3 == 3;
-  cudaError_t e = ensure(&h->colT, &h->colT_bytes, apsp::panel_buffer_bytes(n, ldT, rc.lookahead));
+  cudaError_t e = ensure(&h->colT, &h->colT_bytes, apsp::panel_buffer_bytes(n, ldT, rc.p3 == 4));
   if (e != cudaSuccess) {
     h->last_error = std::string("panel workspace: ") + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? APSP_E_NOMEM : APSP_E_CUDA;
@@ -259,7 +259,7 @@ apsp_status run_rounds_locked(apsp_handle *h, int dtype, void *D, int64_t n, int
     rc.sym = h->h_status[1] == 0;
   }
   if (rc.sym && dtype == APSP_U16) {
-    e = ensure(&h->rowP, &h->rowP_bytes, apsp::row_panel_bytes(ldT, rc.lookahead));
+    e = ensure(&h->rowP, &h->rowP_bytes, apsp::row_panel_bytes(ldT, rc.p3 == 4));
     if (e != cudaSuccess) {
       h->last_error = std::string("panel workspace: ") + cudaGetErrorString(e);
       return e == cudaErrorMemoryAllocation ? APSP_E_NOMEM : APSP_E_CUDA;
@@ -371,7 +371,7 @@ apsp_status apsp_create(apsp_handle **out, const apsp_config *cfg) {
   if (cfg) c = *cfg;
   if (c.dtype != APSP_AUTO && !valid_dtype(c.dtype)) return APSP_E_INVALID;
   if (c.block_k != 0 && c.block_k != 32 && c.block_k != 64) return APSP_E_INVALID;
-  if (c.phase3_variant < 0 || c.phase3_variant > 4) return APSP_E_INVALID;
+  if (c.phase3_variant < 0 || c.phase3_variant > 5) return APSP_E_INVALID;
   if (c.symmetric < 0 || c.symmetric > 2) return APSP_E_INVALID;
   if (c.max_batch <= 0) c.max_batch = 64;
   if (c.queue_depth <= 0) c.queue_depth = 4096;
@@ -872,11 +872,10 @@ apsp_status apsp_autotune(apsp_handle *h, int dtype, int64_t n_max, const char *
     double best = 1e30;
     apsp::RoundConfig best_c;
     for (int bk : {32, 64})
-      for (int var : {3, 2, 1, 0}) {
+      for (int var : {4, 3, 2, 1, 0}) {
         apsp::RoundConfig c;
         c.bk = bk;
         c.p3 = var;
-        c.lookahead = var == 3;
         double t_min = 1e30;
         for (int rep = 0; rep < 4; ++rep) {
           apsp::launch_synth(dtype, M, b, b, nullptr);
@@ -1083,8 +1082,10 @@ apsp_status admit_group(apsp_handle *h, const std::vector<Request *> &rs) {
     const int64_t rn = rs[0]->req.n;
     const int64_t ldT = panel_ld(rn);
     apsp::RoundConfig rc = config_for(h, APSP_I32, rn);
-    rc.lookahead = rc.p3 == 3;
-    if (cudaMallocAsync(&g->ws, apsp::panel_buffer_bytes(rn, ldT, rc.lookahead), s) != cudaSuccess)
+    // one launch per round here, so that the batched groups on other streams
+    // keep running between this request's rounds
+    if (rc.p3 == 4) rc.p3 = 3;
+    if (cudaMallocAsync(&g->ws, apsp::panel_buffer_bytes(rn, ldT, false), s) != cudaSuccess)
       return APSP_E_CUDA;
     if (h->cfg.symmetric != 2) {
       int flag = 0;
@@ -1143,7 +1144,7 @@ void worker_loop(apsp_handle *h) {
         Request *r = h->reqs[h->queue.front()].get();
         const bool large = r->req.n >= kLargeN;
         if (large && !rs.empty()) break;  // a large request starts its own group
-        const int64_t b = r->bytes + panel_bytes(r->req.n) + (large ? (int64_t)apsp::panel_buffer_bytes(r->req.n, panel_ld(r->req.n), true) : 0);
+        const int64_t b = r->bytes + panel_bytes(r->req.n) + (large ? (int64_t)apsp::panel_buffer_bytes(r->req.n, panel_ld(r->req.n), false) : 0);
         if (h->used + add + b > h->budget) break;  // wait for memory to free up
         h->queue.pop_front();
         r->transient = b - r->bytes;

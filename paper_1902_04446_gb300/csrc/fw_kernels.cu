@@ -1655,7 +1655,7 @@ static inline unsigned grid_cols(int64_t n, int threads) {
 template <class Op, int BK>
 static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int64_t ldT, bool vec, int variant,
                                cudaStream_t s, int64_t *launches, PhaseTimer *tm, int *wait_err, bool sym,
-                               void *rowPv, bool lookahead) {
+                               void *rowPv) {
   const bool use_tma = variant != 0;
   using Elem = typename Op::elem;
   using E = Elem;
@@ -1664,7 +1664,9 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
   // lookahead rounds (the warp-specialized Phase 3 with the TMA path and more
   // than one round): two panel buffers used by round parity, then 4 counters
   // per round
-  bool la_on = kLookaheadWidth<BK> && lookahead && use_tma && vec && variant == 3 && q > 1;
+  // kernel 4 (every round in one launch) when its conditions hold, else 3
+  bool la_on = kLookaheadWidth<BK> && use_tma && vec && variant == 4 && q > 1;
+  if (variant == 4) variant = 3;
   uint32_t *colTb[2], *colT = static_cast<uint32_t *>(colTv);
   colTb[0] = colT;
   colTb[1] = la_on ? colT + (int64_t)kMaxRoundWidth * ldT : colT;
@@ -1866,11 +1868,9 @@ static cudaError_t rounds_bk(const RoundConfig &cfg, void *D, int64_t ld, int64_
                              cudaStream_t s, int64_t *launches, PhaseTimer *tm, int *wait_err) {
   const bool vec = aligned16(D, ld, sizeof(typename Op::elem));
   if (cfg.bk == 32)
-    return rounds_impl<Op, 32>(D, ld, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err, cfg.sym, cfg.rowP,
-                               cfg.lookahead);
+    return rounds_impl<Op, 32>(D, ld, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err, cfg.sym, cfg.rowP);
   if (cfg.bk == 64)
-    return rounds_impl<Op, 64>(D, ld, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err, cfg.sym, cfg.rowP,
-                               cfg.lookahead);
+    return rounds_impl<Op, 64>(D, ld, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err, cfg.sym, cfg.rowP);
   return cudaErrorInvalidValue;
 }
 

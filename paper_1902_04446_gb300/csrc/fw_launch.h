@@ -14,51 +14,56 @@ struct PhaseTimer {
   virtual ~PhaseTimer() {}
 };
 
-// Tunable shape of the per-round kernels: round width Bk (32 or 64) and the
-// Phase-3 variant: 0 = one CTA per tile, 1 = persistent TMA kernel with 256
-// threads (8 x 8 words each), 2 = persistent TMA kernel with 512 threads
-// (8 x 4 words each), 3 = warp-specialized persistent kernel (8 consumer
-// warps with 8 x 8 words each and a TMA producer warp; int32 results leave by
-// a TMA min-reduction).  The TMA variants need a 16-byte addressable matrix
-// and fall back to variant 0 otherwise.
+// Tunable shape of the rounds: round width Bk (32 or 64) and the Phase-3
+// kernel: 0 = one CTA per tile, 1 = persistent TMA kernel with 256 threads
+// (8 x 8 words each), 2 = persistent TMA kernel with 512 threads (8 x 4 words
+// each), 3 = warp-specialized persistent kernel (8 consumer warps with 8 x 8
+// words each and a TMA producer warp; int32 results leave by a TMA
+// min-reduction), one launch per round, 4 = the same kernel running every
+// round in one launch, each round's Phase 1 and Phase 2 as tasks inside it
+// (fw_solve_ws; round width 64, needs the double panel buffer of
+// panel_buffer_bytes(n, ldT, true); otherwise it falls back to 3).  The TMA
+// kernels need a 16-byte addressable matrix and fall back to 0 otherwise.
 // sym: symmetric mode for undirected (symmetric) inputs -- Phase 3 updates
 // only the tiles that touch the upper triangle, both of its operands come from
 // one symmetric panel, and a final pass mirrors the upper triangle into the
-// lower; rowP is the BK x ldT element panel that packed 16-bit needs for it.
-// lookahead: with variant 3, round k's Phase-3 launch also runs round k+1's
-// Phase 1 and Phase 2 (one launch per round); needs the double panel buffers
-// of panel_buffer_bytes / row_panel_bytes(..., true).
+// lower; rowP is the BK x ldT element panel that packed 16-bit needs for it
+// (row_panel_bytes(ldT, p3 == 4)).
 struct RoundConfig {
   int bk = 64;
-  int p3 = 3;  // fastest on GB300 at n = 16384 (profiles/phase3_variants_gmm16k.md)
+  int p3 = 3;
   bool sym = false;
   void *rowP = nullptr;
-  bool lookahead = false;
 };
+// The default Phase-3 kernel for n when nothing was tuned: every round in one
+// launch from n = 3072 (profiles/phase3_variants_gmm16k.md; below it the
+// per-round launches are faster).
+inline int default_phase3(int64_t n) { return n >= 3072 ? 4 : 3; }
 
 // flag |= 1 when D (n x n, leading dimension ld) is not symmetric.
 cudaError_t launch_symmetry_check(int dtype, const void *D, int64_t n, int64_t ld, int *flag, cudaStream_t s);
 constexpr int64_t kMaxRoundWidth = 64;  // panel buffers are sized for this
 
 // Bytes of the colT panel buffer launch_rounds needs for n (ldT = its row
-// pitch in words): one kMaxRoundWidth x ldT panel of 32-bit words, or with
-// lookahead two of them, a 64-bit item counter, 6 counters per round (round
-// width >= 32) and one per Phase-3 tile.
+// pitch in words): one kMaxRoundWidth x ldT panel of 32-bit words, or for
+// Phase-3 kernel 4 (every round in one launch, `all_rounds`) two of them, a
+// 64-bit item counter, 6 counters per round (round width >= 32) and one per
+// Phase-3 tile.
 inline size_t lookahead_counter_offset(int64_t ldT) { return 2 * (size_t)kMaxRoundWidth * (size_t)ldT * 4; }
-inline size_t panel_buffer_bytes(int64_t n, int64_t ldT, bool lookahead) {
+inline size_t panel_buffer_bytes(int64_t n, int64_t ldT, bool all_rounds) {
   const size_t one = (size_t)kMaxRoundWidth * (size_t)ldT * 4;
-  if (!lookahead) return one;
+  if (!all_rounds) return one;
   const size_t rounds = (size_t)((n + 31) / 32) + 1;
   const size_t tiles = (size_t)((n + 127) / 128) * (size_t)((n + 127) / 128);
   return 2 * one + 16 + sizeof(int) * (6 * rounds + tiles);
 }
 // Bytes of the element panel (symmetric mode, packed 16-bit).
-inline size_t row_panel_bytes(int64_t ldT, bool lookahead) {
-  return (lookahead ? 2 : 1) * (size_t)kMaxRoundWidth * (size_t)ldT * 2;
+inline size_t row_panel_bytes(int64_t ldT, bool all_rounds) {
+  return (all_rounds ? 2 : 1) * (size_t)kMaxRoundWidth * (size_t)ldT * 2;
 }
 
 // q rounds of Phase 1 -> Phase 2 -> Phase 3 on D (n x n, leading dimension ld).
-// colT is the panel buffer (panel_buffer_bytes(n, ldT, cfg.lookahead) bytes),
+// colT is the panel buffer (panel_buffer_bytes(n, ldT, cfg.p3 == 4) bytes),
 // ldT a multiple of 256 and >= n; cfg.rowP the element panel when needed.
 // wait_err: device word that the persistent Phase-3 kernel ORs 4 into when a
 // bounded wait gives up; nullptr = a per-device word the library allocates on

@@ -73,41 +73,59 @@ __device__ __forceinline__ void phase1_body(typename Op::elem *__restrict__ D, i
   for (int r = 0; r < PT; ++r)
 #pragma unroll
     for (int c = 0; c < PT; ++c) v[r][c] = s[by * PT + r][bx * PT + c];
-  // Step t relaxes every entry through vertex p0 + t; entries live in
-  // registers.  Step t + 1 reads only row t + 1 and column t + 1, so only
-  // those entries go back to shared memory after step t.  Row t and column t
-  // do not change in step t (D_tt = 0, and INF + x >= x on padded vertices),
-  // so a write-back that lands while another thread still reads step t's row
-  // or column stores the value already there; one barrier per step orders the
-  // steps.  The step loop is unrolled by PT so that every register index is a
-  // compile-time constant.
-  for (int t0 = 0; t0 < BK; t0 += PT) {
+  // The pivots are taken PT at a time, t0 = p*PT .. t0+PT-1 (the rows and
+  // columns of thread block p): the net effect of those PT Floyd-Warshall steps
+  // on entry (i, j) is min(D_ij, min_{s,s'} D_i,t0+s + K*_ss' + D_t0+s',j), K*
+  // the closure of the PT x PT corner at (t0, t0).  Every thread closes K itself
+  // (PT^3 add-mins), forms a' = a (x) K* for its rows (a = its pivot-column
+  // values, kept with a' >= a, so every sum has two terms and cannot overflow)
+  // and applies a' (x) b (b = the pivot-row values of its columns).  Then the
+  // owners of the next pivot block's rows and columns write their blocks back,
+  // and one barrier per pivot block (not per pivot) orders the steps.  A
+  // write-back that lands while another thread still reads this block's
+  // pivot column only replaces a value by its own update a', which gives the
+  // same a' again (K* is closed).
+#pragma unroll 1
+  for (int p = 0; p < G; ++p) {
+    const int t0 = p * PT;
+    S K[PT][PT], a[PT][PT], b[PT][PT];
 #pragma unroll
-    for (int tt = 0; tt < PT; ++tt) {
-      const int t = t0 + tt;
-      S a[PT], b[PT];
+    for (int i = 0; i < PT; ++i)
 #pragma unroll
-      for (int r = 0; r < PT; ++r) a[r] = s[by * PT + r][t];
+      for (int j = 0; j < PT; ++j) {
+        K[i][j] = s[t0 + i][t0 + j];
+        a[i][j] = s[by * PT + i][t0 + j];
+        b[i][j] = s[t0 + i][bx * PT + j];
+      }
 #pragma unroll
-      for (int c = 0; c < PT; ++c) b[c] = s[t][bx * PT + c];
+    for (int m = 0; m < PT; ++m)
+#pragma unroll
+      for (int i = 0; i < PT; ++i)
+#pragma unroll
+        for (int j = 0; j < PT; ++j) K[i][j] = Op::s_addmin(K[i][m], K[m][j], K[i][j]);
+    S a2[PT][PT];
+#pragma unroll
+    for (int r = 0; r < PT; ++r)
+#pragma unroll
+      for (int j = 0; j < PT; ++j) {
+        S x = a[r][j];
+#pragma unroll
+        for (int i = 0; i < PT; ++i) x = Op::s_addmin(a[r][i], K[i][j], x);
+        a2[r][j] = x;
+      }
+#pragma unroll
+    for (int r = 0; r < PT; ++r)
+#pragma unroll
+      for (int c = 0; c < PT; ++c)
+#pragma unroll
+        for (int j = 0; j < PT; ++j) v[r][c] = Op::s_addmin(a2[r][j], b[j][c], v[r][c]);
+    if (p + 1 < G && (by == p + 1 || bx == p + 1)) {
 #pragma unroll
       for (int r = 0; r < PT; ++r)
 #pragma unroll
-        for (int c = 0; c < PT; ++c) v[r][c] = Op::s_addmin(a[r], b[c], v[r][c]);
-      const int q = (tt + 1) % PT;                 // local index of row / column t + 1 (constant once unrolled)
-      const int owner = t0 / PT + (tt + 1) / PT;   // block index of row / column t + 1
-      if (t + 1 < BK) {
-        if (by == owner) {
-#pragma unroll
-          for (int c = 0; c < PT; ++c) s[t + 1][bx * PT + c] = v[q][c];
-        }
-        if (bx == owner) {
-#pragma unroll
-          for (int r = 0; r < PT; ++r) s[by * PT + r][t + 1] = v[r][q];
-        }
-      }
-      Bar::sync();
+        for (int c = 0; c < PT; ++c) s[by * PT + r][bx * PT + c] = v[r][c];
     }
+    Bar::sync();
   }
 #pragma unroll
   for (int r = 0; r < PT; ++r)

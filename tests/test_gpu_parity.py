@@ -390,7 +390,7 @@ def test_gmm16k_auto_equals_int32(H):
 
 # ------------------------------------------------------------------ every round shape
 @pytest.mark.parametrize("block_k", [32, 64])
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("dt", ["int32", "u16", "fp32"])
 def test_every_round_shape_matches_oracle(lib, block_k, variant, dt):
     n = 777
@@ -409,7 +409,7 @@ def test_every_round_shape_matches_oracle(lib, block_k, variant, dt):
 
 
 @pytest.mark.parametrize("block_k", [32, 64])
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("dt", ["int32", "u16", "fp32"])
 def test_directed_every_phase3_kernel(lib, block_k, variant, dt):
     """Directed input (general mode) through every Phase-3 kernel.  The int32
@@ -462,7 +462,7 @@ def test_lookahead_midstream_u16_sampled_rows(lib):
 
 # ------------------------------------------------------------------ symmetric mode
 @pytest.mark.parametrize("symmetric", [0, 1, 2])
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("dt", ["int32", "u16", "fp32"])
 @pytest.mark.parametrize("n", [65, 300, 1000])
 def test_symmetric_mode_matches_oracle(lib, symmetric, variant, dt, n):
