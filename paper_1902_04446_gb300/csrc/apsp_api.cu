@@ -69,10 +69,12 @@ struct Profiler : apsp::PhaseTimer {
   struct Pair {
     cudaEvent_t a, b;
     int phase;
-    double relax;
+    double relax, relax_alt;
+    int *flag;  // pinned copy of a device mode flag (0: relax, else relax_alt), or nullptr
   };
   std::vector<Pair> pairs;       // recorded, not yet read
   std::vector<cudaEvent_t> pool; // free events
+  std::vector<int *> flags;      // free pinned flag slots
   cudaEvent_t get() {
     if (!pool.empty()) {
       cudaEvent_t e = pool.back();
@@ -91,7 +93,25 @@ struct Profiler : apsp::PhaseTimer {
   void after(int phase, cudaStream_t s, double relax) override {
     cudaEvent_t b = get();
     cudaEventRecord(b, s);
-    pairs.push_back({pending, b, phase, relax});
+    pairs.push_back({pending, b, phase, relax, relax, nullptr});
+    pending = nullptr;
+  }
+  void after_choice(int phase, cudaStream_t s, double relax_sym, double relax_gen, const int *dflag) override {
+    int *f = nullptr;
+    if (!flags.empty()) {
+      f = flags.back();
+      flags.pop_back();
+    } else if (cudaHostAlloc(&f, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+      f = nullptr;
+      cudaGetLastError();
+    }
+    if (f && cudaMemcpyAsync(f, dflag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+      flags.push_back(f);
+      f = nullptr;
+    }
+    cudaEvent_t b = get();  // after the flag copy: the pair's end event covers it
+    cudaEventRecord(b, s);
+    pairs.push_back({pending, b, phase, relax_sym, relax_gen, f});
     pending = nullptr;
   }
   void read(int64_t *launches, double *ms, double *relax) {
@@ -106,7 +126,8 @@ struct Profiler : apsp::PhaseTimer {
       cudaEventElapsedTime(&t, q.a, q.b);
       if (launches) launches[q.phase] += 1;
       if (ms) ms[q.phase] += t;
-      if (relax) relax[q.phase] += q.relax;
+      if (relax) relax[q.phase] += (q.flag && *q.flag != 0) ? q.relax_alt : q.relax;
+      if (q.flag) flags.push_back(q.flag);
       pool.push_back(q.a);
       pool.push_back(q.b);
     }
@@ -116,8 +137,10 @@ struct Profiler : apsp::PhaseTimer {
     for (Pair &q : pairs) {
       cudaEventDestroy(q.a);
       cudaEventDestroy(q.b);
+      if (q.flag) cudaFreeHost(q.flag);
     }
     for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    for (int *f : flags) cudaFreeHost(f);
   }
 };
 
@@ -244,6 +267,18 @@ apsp_status run_rounds_locked(apsp_handle *h, int dtype, void *D, int64_t n, int
   }
   if (h->cfg.symmetric == 1 || (h->cfg.symmetric == 0 && known_sym)) {
     rc.sym = true;
+  } else if (h->cfg.symmetric == 0 && n > 1 && apsp::single_launch(dtype, D, ld, n, rc)) {
+    // device check of W == W^T whose answer the single launch reads itself:
+    // no host round trip before the rounds are enqueued
+    int *flag = h->d_status + 1;
+    e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = apsp::launch_symmetry_check(dtype, D, n, ld, flag, s);
+    if (e != cudaSuccess) {
+      h->last_error = std::string("symmetry check: ") + cudaGetErrorString(e);
+      return APSP_E_CUDA;
+    }
+    h->launches += 1;
+    rc.sym_flag = flag;
   } else if (h->cfg.symmetric == 0 && n > 1) {
     // device check of W == W^T; the answer is read back before the rounds are enqueued
     int *flag = h->d_status + 1;
@@ -258,7 +293,7 @@ apsp_status run_rounds_locked(apsp_handle *h, int dtype, void *D, int64_t n, int
     h->launches += 1;
     rc.sym = h->h_status[1] == 0;
   }
-  if (rc.sym && dtype == APSP_U16) {
+  if ((rc.sym || rc.sym_flag) && dtype == APSP_U16) {
     e = ensure(&h->rowP, &h->rowP_bytes, apsp::row_panel_bytes(ldT, rc.p3 == 4));
     if (e != cudaSuccess) {
       h->last_error = std::string("panel workspace: ") + cudaGetErrorString(e);

@@ -126,8 +126,9 @@ __global__ void __launch_bounds__(P1_THREADS) fw_phase1_sym(typename Op::elem *_
 // D[r][c] = D[c][r] for every r > c (the lower triangle from the upper), by
 // 32 x 32 blocks through shared memory; block (R, C) with R >= C.
 template <class Op>
-__global__ void mirror_kernel(typename Op::elem *__restrict__ D, int64_t n, int64_t ld) {
+__global__ void mirror_kernel(typename Op::elem *__restrict__ D, int64_t n, int64_t ld, const int *sym_flag) {
   __shared__ typename Op::elem tile[32][33];
+  if (sym_flag && *sym_flag != 0) return;  // the device found D not symmetric: the general path ran
   const int64_t R = blockIdx.y, Cb = blockIdx.x;
   if (R < Cb) return;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
@@ -750,6 +751,14 @@ struct SolvePlan {
   int *tile_round;   // packed 16-bit / fp32: rounds written per tile
 };
 
+// The plan of each mode ([0] general, [1] symmetric) and, when the host left
+// the choice to the device, the symmetry flag (0 = symmetric) to pick it by.
+template <class Op>
+struct SolvePlans {
+  SolvePlan<Op> p[2];
+  const int *sym_flag;
+};
+
 // Round j's tasks and the priority tiles (of round j-1) they depend on.
 struct SolveRound {
   int64_t p0, p1, band_start, band_end;
@@ -812,8 +821,10 @@ template <class Op, int BK, bool RED>
 __global__ void __launch_bounds__(P3W_THREADS, 1)
     fw_solve_ws(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
                 const __grid_constant__ CUtensorMap mapB0, const __grid_constant__ CUtensorMap mapB1,
-                const __grid_constant__ CUtensorMap mapC, typename Op::elem *__restrict__ D, int *err,
-                const SolvePlan<Op> P) {
+                const __grid_constant__ CUtensorMap mapBg, const __grid_constant__ CUtensorMap mapC,
+                typename Op::elem *__restrict__ D, int *err, const SolvePlans<Op> PP) {
+  // mapB0/mapB1: B of symmetric mode (the element panel of each parity); mapBg: B of the general mode (D)
+  const SolvePlan<Op> P = PP.p[PP.sym_flag ? (__ldcg(PP.sym_flag) == 0 ? 1 : 0) : 0];
   constexpr int BM = 128, BNW = 128, TN = 8;
   using Map = TileMap<BM, BNW, TN>;
   constexpr int NCW = Map::THREADS / 32;
@@ -853,6 +864,7 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
     prefetch_tensormap(&mapA1);
     prefetch_tensormap(&mapB0);
     prefetch_tensormap(&mapB1);
+    prefetch_tensormap(&mapBg);
     prefetch_tensormap(&mapC);
     abort_flag = 0;
   }
@@ -985,7 +997,7 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
             int64_t p0, p1;
             span(rnd, p0, p1);
             const CUtensorMap *mA = (rnd & 1) ? &mapA1 : &mapA0;
-            const CUtensorMap *mB = (rnd & 1) ? &mapB1 : &mapB0;
+            const CUtensorMap *mB = P.sym ? ((rnd & 1) ? &mapB1 : &mapB0) : &mapBg;
             mbar_arrive_expect_tx(&full_ab[s], STAGE);
             tma_load_2d(stA(s), mA, &full_ab[s], (info >> 16) * BM, 0);
             tma_load_2d(stB(s), mB, &full_ab[s], (info & 0xFFFF) * BNW * Op::EPW, P.sym ? 0 : (int)p0);
@@ -1655,7 +1667,7 @@ static inline unsigned grid_cols(int64_t n, int threads) {
 template <class Op, int BK>
 static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int64_t ldT, bool vec, int variant,
                                cudaStream_t s, int64_t *launches, PhaseTimer *tm, int *wait_err, bool sym,
-                               void *rowPv) {
+                               void *rowPv, const int *sym_flag) {
   const bool use_tma = variant != 0;
   using Elem = typename Op::elem;
   using E = Elem;
@@ -1667,16 +1679,23 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
   // kernel 4 (every round in one launch) when its conditions hold, else 3
   bool la_on = kLookaheadWidth<BK> && use_tma && vec && variant == 4 && q > 1;
   if (variant == 4) variant = 3;
+  // the device picks the symmetric mode (single launch only; otherwise the
+  // general path, which is exact for any input)
+  const bool dev_sym = la_on && !sym && sym_flag != nullptr;
+  const bool any_sym = sym || dev_sym;
   uint32_t *colTb[2], *colT = static_cast<uint32_t *>(colTv);
   colTb[0] = colT;
   colTb[1] = la_on ? colT + (int64_t)kMaxRoundWidth * ldT : colT;
   // symmetric mode: the element panel (B operand of Phase 3) is colT itself
   // for 32-bit elements, a separate BK x ldT buffer for packed 16-bit
-  Elem *rowP = sym ? (Op::EPW == 2 ? static_cast<Elem *>(rowPv) : nullptr) : nullptr;
-  if (sym && Op::EPW == 2 && !rowP) return cudaErrorInvalidValue;
+  Elem *rowP = any_sym ? (Op::EPW == 2 ? static_cast<Elem *>(rowPv) : nullptr) : nullptr;
+  if (any_sym && Op::EPW == 2 && !rowP) return cudaErrorInvalidValue;
   Elem *rowPb[2] = {rowP, (la_on && rowP) ? rowP + (int64_t)kMaxRoundWidth * ldT : rowP};
   auto symB_of = [&](int b) -> const Elem * {
     return sym ? (Op::EPW == 2 ? rowPb[b] : reinterpret_cast<const Elem *>(colTb[b])) : nullptr;
+  };
+  auto symB_any = [&](int b) -> const Elem * {  // the symmetric-mode B when the device may pick it
+    return Op::EPW == 2 ? rowPb[b] : reinterpret_cast<const Elem *>(colTb[b]);
   };
   using C2 = P2Cfg<Op, BK>;
   using C3 = P3Cfg<Op>;
@@ -1689,7 +1708,7 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
   // persistent TMA Phase 3 when D is 16-byte addressable (otherwise the
   // per-tile kernel with scalar edge handling); A (and B in symmetric mode)
   // maps for each panel buffer
-  CUtensorMap mA[2], mB[2], mC;
+  CUtensorMap mA[2], mB[2], mC, mBs[2];  // mBs: B of the symmetric mode when the device picks the mode
   bool tma = vec && use_tma;
   int *err = nullptr;
   if (tma) {
@@ -1702,6 +1721,9 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
             (sym ? make_map(&mB[b], dt, symB_of(b), (uint64_t)ldT, (uint64_t)BK, (uint64_t)ldT * sizeof(E),
                             128 * Op::EPW, BK)
                  : make_map(&mB[b], dt, D, (uint64_t)n, (uint64_t)n, (uint64_t)ld * sizeof(E), 128 * Op::EPW, BK));
+    for (int b = 0; b < 2 && dev_sym && tma; ++b)
+      tma = make_map(&mBs[b], dt, symB_any(b), (uint64_t)ldT, (uint64_t)BK, (uint64_t)ldT * sizeof(E), 128 * Op::EPW,
+                     BK);
     // int32 (TMA min-reduction epilogue of variant 3): x extent red_cols(n)
     const uint64_t cx = (Op::DTYPE == 0 && variant == 3) ? (uint64_t)(n & ~(int64_t)3) : (uint64_t)n;
     tma = tma && cx > 0 &&
@@ -1808,52 +1830,68 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
   } else if constexpr (kLookaheadWidth<BK>) {
     // every round in one persistent launch (fw_solve_ws)
     constexpr bool RED = Op::DTYPE == 0;
-    SolvePlan<Op> P{};
-    P.n = n;
-    P.ld = ld;
-    P.ldT = ldT;
-    P.q = (int)q;
-    P.tiles_x = tiles_x;
-    P.tiles_y = tiles_y;
-    P.tiles_total = tiles_total;
-    P.grid = grid_tma;
-    P.sym = sym ? 1 : 0;
-    P.vec = vec ? 1 : 0;
-    P.colT[0] = colTb[0];
-    P.colT[1] = colTb[1];
-    P.rowP[0] = rowPb[0];
-    P.rowP[1] = rowPb[1];
+    int tiles_sym = 0;  // tiles with tx >= ty / EPW
+    for (int y = 0; y < tiles_y; ++y) tiles_sym += tiles_x - std::min(tiles_x, y / Op::EPW);
+    const int grid = std::min(sm_count(), tiles_sym);  // one launch grid for either mode
     char *cbase = reinterpret_cast<char *>(colT) + lookahead_counter_offset(ldT);
-    P.items = reinterpret_cast<unsigned long long *>(cbase);
-    P.cnt = reinterpret_cast<int *>(cbase + 16);
-    P.tile_round = P.cnt + 6 * q;
-    const bool has_rowP = rowPb[0] != nullptr;
-    P.base1 = solve_round<Op, BK>(n, P.q, tiles_x, tiles_y, tiles_total, grid_tma, P.sym, has_rowP, 0).total;
-    P.block = 0;
-    double work = 0.0;
-    for (int j = 1; j <= P.q; ++j) {
-      const SolveRound r = solve_round<Op, BK>(n, P.q, tiles_x, tiles_y, tiles_total, grid_tma, P.sym, has_rowP, j);
-      P.block = std::max(P.block, r.total);
-      work += p3_work(j - 1);
-    }
-    for (int j = 0; j < P.q; ++j) {  // Phase 1 and Phase 2 of every round run inside the launch too
-      int64_t p0, p1;
-      span(j, p0, p1);
-      const double w1 = (double)(p1 - p0), rest1 = (double)(n - (p1 - p0));
-      work += w1 * w1 * w1 + (sym ? rest1 * w1 * w1 : 2.0 * rest1 * w1 * w1);
-    }
+    double work[2] = {0.0, 0.0};
+    auto plan = [&](bool msym) {
+      SolvePlan<Op> P{};
+      P.n = n;
+      P.ld = ld;
+      P.ldT = ldT;
+      P.q = (int)q;
+      P.tiles_x = tiles_x;
+      P.tiles_y = tiles_y;
+      P.tiles_total = msym ? tiles_sym : tiles_x * tiles_y;
+      P.grid = grid;
+      P.sym = msym ? 1 : 0;
+      P.vec = vec ? 1 : 0;
+      P.colT[0] = colTb[0];
+      P.colT[1] = colTb[1];
+      P.rowP[0] = msym ? rowPb[0] : nullptr;
+      P.rowP[1] = msym ? rowPb[1] : nullptr;
+      P.items = reinterpret_cast<unsigned long long *>(cbase);
+      P.cnt = reinterpret_cast<int *>(cbase + 16);
+      P.tile_round = P.cnt + 6 * q;
+      const bool has_rowP = P.rowP[0] != nullptr;
+      P.base1 = solve_round<Op, BK>(n, P.q, tiles_x, tiles_y, P.tiles_total, grid, P.sym, has_rowP, 0).total;
+      P.block = 0;
+      double &wk = work[msym ? 1 : 0];
+      const double frac = (double)P.tiles_total / ((double)tiles_x * tiles_y);
+      for (int j = 1; j <= P.q; ++j) {
+        P.block = std::max(P.block,
+                           solve_round<Op, BK>(n, P.q, tiles_x, tiles_y, P.tiles_total, grid, P.sym, has_rowP, j).total);
+        int64_t p0, p1;
+        span(j - 1, p0, p1);
+        const double w = (double)(p1 - p0), rest = (double)(n - (p1 - p0));
+        wk += rest * rest * w * frac;  // the processed tiles' share of (n - w)^2 w
+        wk += w * w * w + (msym ? rest * w * w : 2.0 * rest * w * w);  // the round's Phase 1 and Phase 2
+      }
+      return P;
+    };
+    SolvePlans<Op> PP{};
+    PP.p[0] = plan(sym);
+    PP.p[1] = dev_sym ? plan(true) : PP.p[0];
+    PP.sym_flag = dev_sym ? sym_flag : nullptr;
+    // B maps: symmetric mode's element panels (by parity) and the general mode's D rows
+    const CUtensorMap &b0 = dev_sym ? mBs[0] : mB[0], &b1 = dev_sym ? mBs[1] : mB[1];
+    const CUtensorMap &bg = mB[0];  // D rows unless the host fixed the symmetric mode (then unused)
     e = cudaMemsetAsync(cbase, 0, 16 + sizeof(int) * (6 * (size_t)q + (RED ? 0 : (size_t)tiles_x * tiles_y)), s);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(fw_solve_ws<Op, BK, RED>, cudaFuncAttributeMaxDynamicSharedMemorySize, P3T<BK>::SMEM);
     if (e != cudaSuccess) return e;
     if (tm) tm->before(2, s);
-    fw_solve_ws<Op, BK, RED><<<grid_tma, P3W_THREADS, P3T<BK>::SMEM, s>>>(mA[0], mA[1], mB[0], mB[1], mC, D, err, P);
+    fw_solve_ws<Op, BK, RED><<<grid, P3W_THREADS, P3T<BK>::SMEM, s>>>(mA[0], mA[1], b0, b1, bg, mC, D, err, PP);
     if (launches) *launches += 1;
-    if (tm) tm->after(2, s, work);
+    if (tm) {
+      if (dev_sym) tm->after_choice(2, s, work[1], work[0], sym_flag);
+      else tm->after(2, s, work[sym ? 1 : 0]);
+    }
   }
-  if (sym && q > 1) {  // the lower triangle from the upper
+  if ((sym || dev_sym) && q > 1) {  // the lower triangle from the upper
     const dim3 gm((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
-    mirror_kernel<Op><<<gm, dim3(32, 8), 0, s>>>(D, n, ld);
+    mirror_kernel<Op><<<gm, dim3(32, 8), 0, s>>>(D, n, ld, dev_sym ? sym_flag : nullptr);
     if (launches) *launches += 1;
   }
   return cudaGetLastError();
@@ -1868,10 +1906,17 @@ static cudaError_t rounds_bk(const RoundConfig &cfg, void *D, int64_t ld, int64_
                              cudaStream_t s, int64_t *launches, PhaseTimer *tm, int *wait_err) {
   const bool vec = aligned16(D, ld, sizeof(typename Op::elem));
   if (cfg.bk == 32)
-    return rounds_impl<Op, 32>(D, ld, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err, cfg.sym, cfg.rowP);
+    return rounds_impl<Op, 32>(D, ld, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err, cfg.sym, cfg.rowP,
+                               cfg.sym_flag);
   if (cfg.bk == 64)
-    return rounds_impl<Op, 64>(D, ld, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err, cfg.sym, cfg.rowP);
+    return rounds_impl<Op, 64>(D, ld, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err, cfg.sym, cfg.rowP,
+                               cfg.sym_flag);
   return cudaErrorInvalidValue;
+}
+
+bool single_launch(int dtype, const void *D, int64_t ld, int64_t n, const RoundConfig &cfg) {
+  const size_t es = dtype == 1 ? 2 : 4;
+  return cfg.p3 == 4 && cfg.bk == 64 && n > 64 && aligned16(D, ld, es);
 }
 
 cudaError_t launch_symmetry_check(int dtype, const void *D, int64_t n, int64_t ld, int *flag, cudaStream_t s) {

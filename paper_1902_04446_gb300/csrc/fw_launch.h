@@ -11,6 +11,12 @@ namespace apsp {
 struct PhaseTimer {
   virtual void before(int phase, cudaStream_t s) = 0;
   virtual void after(int phase, cudaStream_t s, double relaxations) = 0;
+  // the count depends on a mode decided on the device: relax_sym when the int
+  // at dflag is 0 (symmetric), relax_gen otherwise
+  virtual void after_choice(int phase, cudaStream_t s, double relax_sym, double relax_gen, const int *dflag) {
+    (void)dflag;
+    after(phase, s, relax_gen);
+  }
   virtual ~PhaseTimer() {}
 };
 
@@ -29,12 +35,19 @@ struct PhaseTimer {
 // one symmetric panel, and a final pass mirrors the upper triangle into the
 // lower; rowP is the BK x ldT element panel that packed 16-bit needs for it
 // (row_panel_bytes(ldT, p3 == 4)).
+// sym_flag (device int, kernel 4 only): the symmetric mode is decided on the
+// device -- symmetric when the int is 0 (as left by launch_symmetry_check) --
+// so the host need not wait for the check; rowP must then be allocated.
 struct RoundConfig {
   int bk = 64;
   int p3 = 3;
   bool sym = false;
   void *rowP = nullptr;
+  const int *sym_flag = nullptr;
 };
+// Whether launch_rounds would run every round in one launch for this call
+// (kernel 4 with round width 64, a 16-byte addressable D and more than one round).
+bool single_launch(int dtype, const void *D, int64_t ld, int64_t n, const RoundConfig &cfg);
 // The default Phase-3 kernel for n when nothing was tuned: every round in one
 // launch from n = 3072 (profiles/phase3_variants_gmm16k.md; below it the
 // per-round launches are faster).

@@ -447,6 +447,25 @@ def test_lookahead_midstream_int32_full_matrix(lib, symmetric, directed):
     np.testing.assert_array_equal(D, E)
 
 
+@pytest.mark.parametrize("dt", ["u16", "fp32"])
+def test_single_launch_general_mode_16bit_fp32_full_matrix(lib, dt):
+    """Directed input (general mode) at a size where every round runs in one launch with its tasks between the
+    tiles: the 16-bit and fp32 tiles merge a loaded C and store it back, so each waits for its own previous
+    round; the whole matrix must equal the oracle's (Dijkstra from every source)."""
+    n = 4100
+    s, d, w = er_edges(n, seed=4100 + len(dt), deg=4.0, wmax=60, directed=True)
+    E = oracle.dijkstra(n, s, d, w, np.arange(n), directed=True)
+    with lib.Handle(device=0) as h:
+        if dt == "u16":
+            D16 = h.solve_t(dt, dev(dense_directed(n, s, d, w, dtype=np.int16, inf=0x7FFF))).cpu().numpy()
+            D = oracle.unpack_u16(D16.view(np.uint16)).astype(np.int64)
+        else:
+            Df = h.solve_t(dt, dev(dense_directed(n, s, d, w, dtype=np.float32, inf=np.inf))).cpu().numpy()
+            D = np.where(np.isinf(Df), INF, Df.astype(np.float64)).astype(np.int64)  # small integers: exact
+        assert h.last_status() == 0
+    np.testing.assert_array_equal(D, E)
+
+
 def test_lookahead_midstream_u16_sampled_rows(lib):
     n = 8200
     s, d, w = er_edges(n, seed=82, deg=4.0, wmax=60)
