@@ -159,12 +159,14 @@ apsp_status apsp_int16_bound(apsp_handle *h, const int32_t *W, int64_t n, int64_
 apsp_status apsp_solve_batch(apsp_handle *h, int64_t count, const int32_t *const *W, const int64_t *n,
                              const int64_t *ld, int32_t *const *D, void *stream);
 
-/* Diagnostic of the bounded device waits (no paper counterpart): runs one
- * batched launch over a small built-in graph whose first task waits on a
- * device flag that nothing sets, with the given spin limit (> 0).  Returns
- * APSP_E_TIMEOUT when the kernel gave up and reported it (the expected
- * outcome), APSP_OK if it did not wait, or another error.  Synchronizes the
- * device; the context stays usable. */
+/* Diagnostic of the bounded device waits (no paper counterpart): runs two
+ * launches over small built-in graphs (paths) whose first task waits on a
+ * device flag that nothing sets, with the given spin limit (> 0) on each wait
+ * for another work item: the batched kernel (96 nodes), then every round of a
+ * 320-node solve in one persistent launch (phase3_variant 5).  Returns
+ * APSP_E_TIMEOUT when both kernels gave up and reported it (the expected
+ * outcome), APSP_OK if one of them did not wait, or another error.
+ * Synchronizes the device; the context stays usable. */
 apsp_status apsp_check_bounded_wait(apsp_handle *h, int64_t spin_limit);
 
 /* ---- building blocks (Table 1) ------------------------------------------ */

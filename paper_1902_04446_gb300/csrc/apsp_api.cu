@@ -750,41 +750,65 @@ apsp_status apsp_check_bounded_wait(apsp_handle *h, int64_t spin_limit) {
   cudaError_t e = cudaSetDevice(h->cfg.device);
   if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
   std::lock_guard<std::mutex> g(h->mu);
-  const int64_t n = 96;  // two rounds
+  // two checks: the batched kernel on a 96-node path (two rounds), and every
+  // round of a 320-node path in one persistent launch (five rounds)
+  const int64_t n = 96, n1 = 320, ldT = 512;
+  const size_t oD1 = (size_t)n * n * 4, oT = oD1 + (size_t)n1 * n1 * 4;
+  const size_t oG = oT + ((apsp::panel_buffer_bytes(n1, ldT, true) + 255) & ~size_t(255));
   void *buf = nullptr;
-  e = cudaMalloc(&buf, (size_t)n * n * 4 + 256);
+  e = cudaMalloc(&buf, oG + 256);
   if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
-  int32_t *D = static_cast<int32_t *>(buf);
-  int *gate = reinterpret_cast<int *>(static_cast<char *>(buf) + (size_t)n * n * 4);
+  char *b = static_cast<char *>(buf);
+  int32_t *D = reinterpret_cast<int32_t *>(b), *D1 = reinterpret_cast<int32_t *>(b + oD1);
+  int *gate = reinterpret_cast<int *>(b + oG), *err1 = gate + 1;
   cudaStream_t s = nullptr;
   apsp_status st = APSP_OK;
   if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) st = APSP_E_CUDA;
-  if (st == APSP_OK) {
-    // a valid graph (a path), and a gate flag that nothing ever sets
-    std::vector<int32_t> hW((size_t)n * n, APSP_INF_I32);
-    for (int64_t i = 0; i < n; ++i) {
-      hW[(size_t)i * n + i] = 0;
-      if (i + 1 < n) hW[(size_t)i * n + i + 1] = hW[(size_t)(i + 1) * n + i] = 1;
+  // valid graphs (paths), and a gate flag that nothing ever sets
+  auto path = [](int64_t m) {
+    std::vector<int32_t> w((size_t)m * m, APSP_INF_I32);
+    for (int64_t i = 0; i < m; ++i) {
+      w[(size_t)i * m + i] = 0;
+      if (i + 1 < m) w[(size_t)i * m + i + 1] = w[(size_t)(i + 1) * m + i] = 1;
     }
-    if (cudaMemcpy(D, hW.data(), hW.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(gate, 0, sizeof(int)) != cudaSuccess)
+    return w;
+  };
+  if (st == APSP_OK) {
+    const std::vector<int32_t> w = path(n), w1 = path(n1);
+    if (cudaMemcpy(D, w.data(), w.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(D1, w1.data(), w1.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(gate, 0, 2 * sizeof(int)) != cudaSuccess)
       st = APSP_E_CUDA;
   }
+  auto read_flag = [&](const int *flag) {  // the word a kernel ORs 4 into when a wait gave up
+    e = cudaMemcpyAsync(h->h_status, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "sync");
+    return (*h->h_status & 4) ? APSP_E_TIMEOUT : APSP_OK;
+  };
   if (st == APSP_OK) {
     std::vector<const int32_t *> Wv{D};
     std::vector<int64_t> nv{n}, ldv{n};
     std::vector<int32_t *> Dv{D};
     st = batch_locked(h, Wv, nv, ldv, Dv, s, spin_limit, gate);
+    if (st == APSP_OK) st = read_flag(h->d_status);
   }
-  if (st == APSP_OK) {
-    e = cudaMemcpyAsync(h->h_status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) st = cuda_fail(nullptr, e, "sync");
-    else if (*h->h_status & 4) st = APSP_E_TIMEOUT;
+  if (st == APSP_E_TIMEOUT) {
+    apsp::RoundConfig rc;
+    rc.bk = 64;
+    rc.p3 = 4;
+    rc.gate = gate;
+    rc.dep_spins = (uint32_t)std::min<int64_t>(spin_limit, 0xFFFFFFFFll);
+    if (!apsp::single_launch(APSP_I32, D1, n1, n1, rc)) st = APSP_E_UNSUPPORTED;
+    else {
+      int64_t l = 0;
+      e = apsp::launch_rounds(APSP_I32, D1, n1, n1, b + oT, ldT, s, &l, nullptr, rc, err1);
+      st = e != cudaSuccess ? cuda_fail(nullptr, e, "launch_rounds") : read_flag(err1);
+    }
   }
   if (s) cudaStreamDestroy(s);
   cudaFree(buf);
-  if (st == APSP_E_TIMEOUT) h->last_error = "bounded wait gave up as expected";
+  if (st == APSP_E_TIMEOUT) h->last_error = "bounded waits gave up as expected";
   return st;
 }
 

@@ -631,6 +631,20 @@ __shared__ __align__(8) uint64_t la_grp_bar;
 __shared__ uint32_t la_grp_par[8];  // phase parity of each consumer warp's next sync
 __shared__ int la_grp_abort;
 
+// A bounded mbarrier wait that also gives up once *a, or *b when given, is
+// nonzero (read after every 32 failed tries, so a launch that is being aborted
+// ends without waiting out the full limit).
+__device__ __forceinline__ bool mbar_wait_or(uint64_t *bar, uint32_t parity, uint32_t limit, const int *a,
+                                             const int *b) {
+  for (uint32_t i = 0; i < limit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 31) == 31 &&
+        (*reinterpret_cast<const volatile int *>(a) || (b && *reinterpret_cast<const volatile int *>(b))))
+      return false;
+  }
+  return false;
+}
+
 struct GroupBar {
   __device__ __forceinline__ static void sync() {
     __syncwarp();
@@ -639,7 +653,7 @@ struct GroupBar {
     const uint32_t par = la_grp_par[w];
     __syncwarp();
     if ((threadIdx.x & 31) == 0) mbar_arrive(&la_grp_bar);
-    const bool ok = mbar_wait_bounded(&la_grp_bar, par, P3T_WAIT_LIMIT);
+    const bool ok = mbar_wait_or(&la_grp_bar, par, P3T_WAIT_LIMIT, &la_grp_abort, nullptr);
     __syncwarp();
     if ((threadIdx.x & 31) == 0) la_grp_par[w] = par ^ 1u;
     if (!ok) la_grp_abort = 1;
@@ -753,10 +767,17 @@ struct SolvePlan {
 
 // The plan of each mode ([0] general, [1] symmetric) and, when the host left
 // the choice to the device, the symmetry flag (0 = symmetric) to pick it by.
+// abort: a zeroed device word that a CTA sets when it gives up, so that the
+// others stop at their next wait instead of timing out one by one.  gate
+// (nullable): round 0's Phase 1 also waits for *gate >= 1 (a diagnostic of
+// the bounded waits).  dep_spins: the limit of each wait on another item.
 template <class Op>
 struct SolvePlans {
   SolvePlan<Op> p[2];
   const int *sym_flag;
+  int *abort;
+  const int *gate;
+  uint32_t dep_spins;
 };
 
 // Round j's tasks and the priority tiles (of round j-1) they depend on.
@@ -879,15 +900,21 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
     return r0 + BM <= n && c0 + BNW * Op::EPW <= n && (r0 + BM <= p0 || r0 >= p1) &&
            (c0 + BNW * Op::EPW <= p0 || c0 >= p1);
   };
-  // a bounded wait for a counter, by one thread; false: gave up
+  // a bounded wait for a counter, by one thread; false: gave up, or another CTA did
   auto wait_count = [&](const int *c, int target) {
     uint32_t spins = 0;
     while (vload(c) < target) {
-      if (++spins > P3T_WAIT_LIMIT / 4) return false;
+      if (++spins > PP.dep_spins || ((spins & 31) == 0 && vload(PP.abort))) return false;
       __nanosleep(64);
     }
     __threadfence();
     return true;
+  };
+  // this CTA gives up: its other warps stop at their next wait, the other CTAs at theirs
+  auto give_up = [&]() {
+    la_grp_abort = 1;
+    abort_flag = 1;
+    *reinterpret_cast<volatile int *>(PP.abort) = 1;
   };
 
   if (warp == NCW) {
@@ -1028,10 +1055,12 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
         issue_slots();
         issue_c();
       };
+      auto aborted = [&]() { return *reinterpret_cast<volatile int *>(&abort_flag) || vload(PP.abort); };
       auto wait_bar = [&](uint64_t *bar, uint32_t parity) {  // bounded, making progress meanwhile
         for (uint32_t it = 0; it < P3T_WAIT_LIMIT; ++it) {
           if (mbar_try_wait(bar, parity)) return true;
           progress();
+          if ((it & 31) == 31 && aborted()) return false;
         }
         return false;
       };
@@ -1063,7 +1092,7 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
         if (kind == LA_END) {
           // the end slot (and anything before it) must reach the consumers
           uint32_t it = 0;
-          while (issued < claimed && ++it < P3T_WAIT_LIMIT) progress();
+          while (issued < claimed && ++it < P3T_WAIT_LIMIT && ((it & 31) != 0 || !aborted())) progress();
           ok = issued == claimed;
           break;
         }
@@ -1114,7 +1143,8 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
       }
       bulk_wait_all();
       if (!ok) {
-        abort_flag = 1;
+        give_up();
+        // the copies in flight land before the CTA exits (these waits end: TMA completes)
         for (int st = 0; st < 2; ++st)
           if (n_ab[st] > 0) mbar_wait_bounded(&full_ab[st], (uint32_t)(n_ab[st] - 1) & 1u, P3T_WAIT_LIMIT);
         if (n_c > 0) mbar_wait_bounded(&full_c, (uint32_t)(n_c - 1) & 1u, P3T_WAIT_LIMIT);
@@ -1127,9 +1157,9 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
     int ct = 0;  // tiles done by this CTA
     for (int i = 0;; ++i) {
       const int s = i & 1;
-      const bool bad = !mbar_wait_bounded(&full_ab[s], (uint32_t)(i >> 1) & 1u, P3T_WAIT_LIMIT);
+      const bool bad = !mbar_wait_or(&full_ab[s], (uint32_t)(i >> 1) & 1u, P3T_WAIT_LIMIT, &abort_flag, PP.abort);
       if (__any_sync(0xffffffffu, bad)) {
-        if (lane == 0) abort_flag = 1;
+        give_up();
         break;
       }
       const int kind = slot_kind[s], info = slot_info[s], rnd = slot_round[s];
@@ -1146,7 +1176,7 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
         const int64_t r0 = (int64_t)cty * BM, c0 = (int64_t)ctx * BNW * Op::EPW;
         bool ebad;
         if (RED) {
-          ebad = ct > 0 && !mbar_wait_bounded(&cfree, (uint32_t)(ct - 1) & 1u, P3T_WAIT_LIMIT);
+          ebad = ct > 0 && !mbar_wait_or(&cfree, (uint32_t)(ct - 1) & 1u, P3T_WAIT_LIMIT, &abort_flag, PP.abort);
           if (!__any_sync(0xffffffffu, ebad)) {
 #pragma unroll
             for (int r = 0; r < 8; ++r)
@@ -1160,7 +1190,7 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
                 red_tail_store<BM, BNW, TN>(reinterpret_cast<int32_t *>(D), ld, n, n, r0, c0, acc, ty, tx);
           }
         } else {
-          ebad = !mbar_wait_bounded(&full_c, (uint32_t)ct & 1u, P3T_WAIT_LIMIT);
+          ebad = !mbar_wait_or(&full_c, (uint32_t)ct & 1u, P3T_WAIT_LIMIT, &abort_flag, PP.abort);
           if (!__any_sync(0xffffffffu, ebad)) {
             int64_t p0, p1;
             span(rnd, p0, p1);
@@ -1184,7 +1214,7 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
         }
         ++ct;
         if (__any_sync(0xffffffffu, ebad)) {
-          if (lane == 0) abort_flag = 1;
+          give_up();
           break;
         }
       } else {
@@ -1192,9 +1222,9 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
         if (TASK_IN_C) {
           __syncwarp();
           if (lane == 0) mbar_arrive(&empty_ab[s]);
-          const bool cb = ct > 0 && !mbar_wait_bounded(&cfree, (uint32_t)(ct - 1) & 1u, P3T_WAIT_LIMIT);
+          const bool cb = ct > 0 && !mbar_wait_or(&cfree, (uint32_t)(ct - 1) & 1u, P3T_WAIT_LIMIT, &abort_flag, PP.abort);
           if (__any_sync(0xffffffffu, cb)) {
-            if (lane == 0) abort_flag = 1;
+            give_up();
             break;
           }
         }
@@ -1203,6 +1233,7 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
         bool dbad = false;
         if (lane == 0) {
           if (kind == LA_P1) {
+            if (rnd == 0 && PP.gate) dbad = !wait_count(PP.gate, 1);
             if (rnd >= 1) dbad = !wait_count(cnt(rnd, 0), r.n_prio);
             if (!dbad && rnd >= 2) dbad = !wait_count(cnt(rnd - 2, 4), P.tiles_total);
           } else if (kind == LA_P2) {
@@ -1212,13 +1243,12 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
           }
         }
         if (__any_sync(0xffffffffu, dbad)) {
-          la_grp_abort = 1;
-          if (lane == 0) abort_flag = 1;
+          give_up();
           break;
         }
         GroupBar::sync();  // every consumer warp is here: the task's memory is no longer read
         if (*reinterpret_cast<volatile int *>(&la_grp_abort)) {
-          if (lane == 0) abort_flag = 1;
+          give_up();
           break;
         }
         uint32_t *tsm = TASK_IN_C ? Cs : reinterpret_cast<uint32_t *>(base);
@@ -1237,7 +1267,7 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
         fence_proxy_async_smem();  // the task's shared memory is refilled by TMA next
         GroupBar::sync();          // every consumer's writes of the task are done
         if (*reinterpret_cast<volatile int *>(&la_grp_abort)) {
-          if (lane == 0) abort_flag = 1;
+          give_up();
           break;
         }
         if (tid == 0) {
@@ -1667,7 +1697,7 @@ static inline unsigned grid_cols(int64_t n, int threads) {
 template <class Op, int BK>
 static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int64_t ldT, bool vec, int variant,
                                cudaStream_t s, int64_t *launches, PhaseTimer *tm, int *wait_err, bool sym,
-                               void *rowPv, const int *sym_flag) {
+                               void *rowPv, const int *sym_flag, const int *gate, uint32_t dep_spins) {
   const bool use_tma = variant != 0;
   using Elem = typename Op::elem;
   using E = Elem;
@@ -1874,6 +1904,9 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
     PP.p[0] = plan(sym);
     PP.p[1] = dev_sym ? plan(true) : PP.p[0];
     PP.sym_flag = dev_sym ? sym_flag : nullptr;
+    PP.abort = reinterpret_cast<int *>(cbase + 8);
+    PP.gate = gate;
+    PP.dep_spins = dep_spins ? dep_spins : P3T_WAIT_LIMIT / 4;
     // B maps: symmetric mode's element panels (by parity) and the general mode's D rows
     const CUtensorMap &b0 = dev_sym ? mBs[0] : mB[0], &b1 = dev_sym ? mBs[1] : mB[1];
     const CUtensorMap &bg = mB[0];  // D rows unless the host fixed the symmetric mode (then unused)
@@ -1907,10 +1940,10 @@ static cudaError_t rounds_bk(const RoundConfig &cfg, void *D, int64_t ld, int64_
   const bool vec = aligned16(D, ld, sizeof(typename Op::elem));
   if (cfg.bk == 32)
     return rounds_impl<Op, 32>(D, ld, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err, cfg.sym, cfg.rowP,
-                               cfg.sym_flag);
+                               cfg.sym_flag, cfg.gate, cfg.dep_spins);
   if (cfg.bk == 64)
     return rounds_impl<Op, 64>(D, ld, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err, cfg.sym, cfg.rowP,
-                               cfg.sym_flag);
+                               cfg.sym_flag, cfg.gate, cfg.dep_spins);
   return cudaErrorInvalidValue;
 }
 

@@ -44,6 +44,8 @@ struct RoundConfig {
   bool sym = false;
   void *rowP = nullptr;
   const int *sym_flag = nullptr;
+  const int *gate = nullptr;  // kernel 4 only: round 0's Phase 1 also waits for *gate >= 1
+  uint32_t dep_spins = 0;     // kernel 4 only: limit of each wait on another work item (0 = default)
 };
 // Whether launch_rounds would run every round in one launch for this call
 // (kernel 4 with round width 64, a 16-byte addressable D and more than one round).

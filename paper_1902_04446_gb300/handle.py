@@ -199,7 +199,8 @@ class Handle:
         return Ds
 
     def check_bounded_wait(self, spin_limit: int = 1 << 12) -> int:
-        """apsp_check_bounded_wait: status of a batched launch whose first wait can never be satisfied."""
+        """apsp_check_bounded_wait: status of a batched launch and of an all-rounds launch whose first wait can never
+        be satisfied (7, APSP_E_TIMEOUT, when both gave up as they should)."""
         return int(_L().apsp_check_bounded_wait(self._h, spin_limit))
 
     def autotune(self, dtype="int32", n_max: int = 4096, cache_path: str | None = None):

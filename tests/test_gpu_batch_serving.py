@@ -55,10 +55,20 @@ def test_solve_batch_equals_alone_and_handles_in_place_and_empty(H):
 
 
 def test_bounded_wait_reports_timeout_and_context_survives(H):
+    """The batched kernel and the all-rounds persistent launch each wait on a flag that nothing sets, give up
+    after the spin limit and report APSP_E_TIMEOUT; afterwards both kernels solve exactly on the same context."""
+    import time
+    t0 = time.perf_counter()
     assert H.check_bounded_wait(1 << 10) == 7  # APSP_E_TIMEOUT
+    assert time.perf_counter() - t0 < 30.0  # the CTAs stop together, not one full wait limit after another
     W = er_dense(200, 3)
     D = H.solve_t("int32", dev(W))
     np.testing.assert_array_equal(D.cpu().numpy().astype(np.int64), oracle.fw(W.astype(np.int64)))
+    n = 3100  # every round in one launch by default from n = 3072
+    s, d, w = gen.er_graph(n, 31, avg_degree=6.0)
+    D = H.solve_t("int32", dev(gen.dense_matrix(n, s, d, w, dtype=np.int32))).cpu().numpy()
+    rows = np.array([0, 1, 1550, 3099])
+    np.testing.assert_array_equal(D[rows].astype(np.int64), oracle.dijkstra(n, s, d, w, rows))
 
 
 def test_serving_mixed_equals_alone_and_oracle(H):
