@@ -400,16 +400,21 @@ def run_gpu(args):
     achieved = (r3 / n3) / (ms3 / n3 / 1e3) / 1e9 if n3 else None
     peak = ADDMIN_LANES_PER_CLK_PER_SM * sms * sm_max_mhz * 1e6 / 1e9
     phase_ms = {f"phase{p}": round(prof[p][1] / args.steps, 3) for p in (1, 2, 3)}
-    roofline = {"bound": "alu",
-                "kernel": "fw_solve_ws<int32> (every round in one launch: Phase-3 tiles with each round's "
-                          "Phase 1 and Phase 2 as tasks)",
-                "achieved": achieved, "peak": peak, "unit": UNIT,
-                "work": "relaxations performed in the launch: Phase 3 (in symmetric mode only the tiles touching "
-                        "the upper triangle) plus every round's Phase 1 and Phase 2",
+    if h.tuned_config("int32", n)[1] == 4:
+        kname, kkey = ("fw_solve_ws<int32> (every round in one launch: Phase-3 tiles with each round's Phase 1 and "
+                       "Phase 2 as tasks)"), "fw_solve_ws"
+        work = ("relaxations performed in the launch: Phase 3 (in symmetric mode only the tiles touching the upper "
+                "triangle) plus every round's Phase 1 and Phase 2")
+    else:
+        kname, kkey = "fw_phase3_ws<int32> (warp-specialized Phase 3, one launch per round)", "fw_phase3_ws"
+        work = ("relaxations performed by the Phase-3 launches (in symmetric mode only the tiles touching the upper "
+                "triangle)")
+    roofline = {"bound": "alu", "kernel": kname,
+                "achieved": achieved, "peak": peak, "unit": UNIT, "work": work,
                 "frac": (achieved / peak) if achieved else None,
                 "peak_basis": f"{ADDMIN_LANES_PER_CLK_PER_SM} add-min lanes/clk/SM (measured) x {sms} SMs x "
                               f"{sm_max_mhz:.0f} MHz (max SM clock)",
-                "traffic": ncu_traffic(f"fw_solve_ws_int32_{args.workload}"),
+                "traffic": ncu_traffic(f"{kkey}_int32_{args.workload}"),
                 "phase_ms_per_step": phase_ms,
                 "phase3_share_of_step": prof[3][1] / ms if ms else None}
     if clocks and achieved:

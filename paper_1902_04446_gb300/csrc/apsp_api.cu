@@ -237,7 +237,7 @@ int64_t bucket_of(int64_t n) {
 // largest tuned bucket for larger n), else Bk = 64 with the TMA Phase 3.
 apsp::RoundConfig config_for(apsp_handle *h, int dtype, int64_t n) {
   apsp::RoundConfig c;
-  c.p3 = apsp::default_phase3(n);
+  c.p3 = apsp::default_phase3(n, dtype);
   const int64_t b = bucket_of(n);
   auto it = h->tuned.find({dtype, b});
   if (it != h->tuned.end()) {

@@ -198,6 +198,7 @@ __global__ void __launch_bounds__(256, 2) fw_phase3(typename Op::elem *__restric
 // sum is INF and never wins.
 constexpr int P3T_C_BYTES = 128 * 128 * 4;
 constexpr uint32_t P3T_WAIT_LIMIT = 1u << 26;
+constexpr uint32_t P3T_SLEEP_NS = 256;  // longest sleep of one wait try in the persistent kernels' producers
 template <int BK>
 struct P3T {
   static constexpr int STAGE_BYTES = 2 * BK * 128 * 4;  // A + B tiles
@@ -491,7 +492,7 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
       if (!RED) issue_c(cty, ctx);
       for (int t = t_begin; t < t_end; ++t) {
         const int i = t - t_begin, s = i & 1;
-        if (!mbar_wait_bounded(&empty_ab[s], (uint32_t)(i >> 1) & 1u, P3T_WAIT_LIMIT)) {
+        if (!mbar_wait_sleep_bounded(&empty_ab[s], (uint32_t)(i >> 1) & 1u, P3T_WAIT_LIMIT, P3T_SLEEP_NS)) {
           ok = false;
           break;
         }
@@ -499,7 +500,7 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
           issue_ab(aty, atx, s);
           step(aty, atx);
         }
-        if (!mbar_wait_bounded(&cdone, (uint32_t)i & 1u, P3T_WAIT_LIMIT)) {
+        if (!mbar_wait_sleep_bounded(&cdone, (uint32_t)i & 1u, P3T_WAIT_LIMIT, P3T_SLEEP_NS)) {
           ok = false;
           break;
         }
@@ -920,6 +921,26 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
   if (warp == NCW) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
+      // The per-item bookkeeping stays cheap: this thread shares its SM
+      // sub-partition's integer pipe with two consumer warps.  One CTA's items
+      // only increase, so the round of the last block met, the block's first
+      // item and the last tile row of the stream met are kept and reused.
+      SolveRound cr{};
+      int cr_j = -1;
+      auto round_at = [&](int j) -> const SolveRound & {
+        if (j != cr_j) {
+          cr = round_info(j);
+          cr_j = j;
+        }
+        return cr;
+      };
+      long long blk_lo = 0;  // first item of block blk_j, relative to base1
+      int blk_j = 0;
+      int sy = -1;  // tile row sy holds the stream positions [spre, snext)
+      long long spre = 0, snext = 0;
+      auto row_prefix = [&](int y) -> long long {
+        return P.sym ? sym_prefix(y, P.tiles_x, Op::EPW) : (long long)y * P.tiles_x;
+      };
       // tile-stream position -> packed tile, or -1 for a priority tile met again
       auto stream_tile = [&](const SolveRound &r, int j) -> int {
         int y, x;
@@ -936,26 +957,36 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
           return (y << 16) | x;
         }
         const int idx = j - r.n_prio;
-        if (!P.sym) {
-          y = idx / P.tiles_x;
-          x = idx % P.tiles_x;
-        } else {
-          int lo = 0, hi = P.tiles_y - 1;
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (sym_prefix(mid, P.tiles_x, Op::EPW) <= idx) lo = mid;
-            else hi = mid - 1;
+        if (sy < 0 || idx < spre || idx >= snext) {
+          y = -1;
+          if (sy >= 0 && idx >= snext)  // a few rows on
+            for (int c = sy + 1; c < sy + 5 && c < P.tiles_y; ++c)
+              if (idx < row_prefix(c + 1)) {
+                y = c;
+                break;
+              }
+          if (y < 0) {  // the last row whose first position is <= idx
+            int lo = 0, hi = P.tiles_y - 1;
+            while (lo < hi) {
+              const int mid = (lo + hi + 1) >> 1;
+              if (row_prefix(mid) <= idx) lo = mid;
+              else hi = mid - 1;
+            }
+            y = lo;
           }
-          y = lo;
-          x = lo / Op::EPW + (int)(idx - sym_prefix(lo, P.tiles_x, Op::EPW));
+          sy = y;
+          spre = row_prefix(y);
+          snext = row_prefix(y + 1);
         }
+        y = sy;
+        x = (P.sym ? sy / Op::EPW : 0) + (int)(idx - spre);
         const bool prio = r.n_prio > 0 && ((y == r.R && x >= r.row_x0) || (x == r.C && y < r.col_y1));
         return prio ? -1 : ((y << 16) | x);
       };
       // item -> kind, round (tiles: their round; tasks: the round they build), info
       auto decode = [&](long long item, int &kind, int &rnd, int &info) {
         if (item < P.base1) {
-          const SolveRound r0 = round_info(0);
+          const SolveRound &r0 = round_at(0);
           rnd = 0;
           if (item == 0) { kind = LA_P1; info = 0; }
           else if (item < 1 + r0.n_p2row + r0.n_p2col) { kind = LA_P2; info = (int)item - 1; }
@@ -963,9 +994,16 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
           return;
         }
         const long long rel = item - P.base1;
-        const int j = 1 + (int)(rel / P.block), pos = (int)(rel % P.block);
+        if (blk_j > 0 && rel >= blk_lo + P.block && rel < blk_lo + 2 * (long long)P.block) {
+          ++blk_j;
+          blk_lo += P.block;
+        } else if (blk_j == 0 || rel < blk_lo || rel >= blk_lo + P.block) {
+          blk_j = 1 + (int)(rel / P.block);
+          blk_lo = (long long)(blk_j - 1) * P.block;
+        }
+        const int j = blk_j, pos = (int)(rel - blk_lo);
         if (j > P.q) { kind = LA_END; rnd = P.q; info = 0; return; }
-        const SolveRound r = round_info(j);
+        const SolveRound &r = round_at(j);
         if (pos >= r.total) { kind = LA_SKIP; rnd = j; info = 0; return; }
         const int n_p2 = r.n_p2row + r.n_p2col;
         if (j < P.q) {
@@ -1056,10 +1094,17 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
         issue_c();
       };
       auto aborted = [&]() { return *reinterpret_cast<volatile int *>(&abort_flag) || vload(PP.abort); };
-      auto wait_bar = [&](uint64_t *bar, uint32_t parity) {  // bounded, making progress meanwhile
+      // bounded, making progress meanwhile; with nothing to progress the thread
+      // sleeps in the wait instead of spinning (its instructions would take issue
+      // and integer-pipe cycles from the consumer warps of its sub-partition)
+      auto wait_bar = [&](uint64_t *bar, uint32_t parity) {
         for (uint32_t it = 0; it < P3T_WAIT_LIMIT; ++it) {
-          if (mbar_try_wait(bar, parity)) return true;
-          progress();
+          if (issued < claimed || (!RED && cs_free && c_next < claimed)) {
+            if (mbar_try_wait(bar, parity)) return true;
+            progress();
+          } else if (mbar_try_wait_sleep(bar, parity, P3T_SLEEP_NS)) {
+            return true;
+          }
           if ((it & 31) == 31 && aborted()) return false;
         }
         return false;
@@ -1109,29 +1154,32 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
           const int pk = rt[i & 3], k = rr[i & 3];
           const int ty_ = pk >> 16, tx_ = pk & 0xFFFF;
           const int r0 = ty_ * BM, c0 = tx_ * BNW * Op::EPW;
+          // Cs is free again once the copy out has read it; the next tile's C
+          // load (merge path) starts while this tile's copy completes
           if (RED) {
             if (c0 < red_cols(n)) {  // mapC ends at red_cols(n) in this mode
               tma_reduce_min_2d(&mapC, Cs, c0, r0);
               bulk_commit();
-              bulk_wait_all();
-              fence_proxy_async_global();
+              bulk_wait_read_all();
             }
             mbar_arrive(&cfree);
           } else {
             if (interior_of(k, r0, c0)) {
               tma_store_2d(&mapC, Cs, c0, r0);
               bulk_commit();
-              bulk_wait_all();
-              fence_proxy_async_global();
+              bulk_wait_read_all();
             }
             cs_free = true;
+            issue_c();
           }
-          // the tile of round k is written: publish it
+          // the tile of round k is written once its copy has completed: publish it
+          bulk_wait_all();
+          fence_proxy_async_global();
           __threadfence();
           if (!RED) atomicExch(P.tile_round + ty_ * P.tiles_x + tx_, k + 1);
           atomicAdd(cnt(k, 4), 1);
           if (k + 1 < P.q) {
-            const SolveRound r = round_info(k + 1);
+            const SolveRound &r = round_at(k + 1);
             if ((ty_ == r.R && tx_ >= r.row_x0) || (tx_ == r.C && ty_ < r.col_y1)) atomicAdd(cnt(k + 1, 0), 1);
           }
           progress();
@@ -1409,14 +1457,14 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
       if (!RED) issue_c(t_begin);
       for (long long j = 0; j < n_slots; ++j) {
         const int s = (int)(j & 1);
-        if (!mbar_wait_bounded(&empty_ab[s], (uint32_t)(j >> 1) & 1u, P3T_WAIT_LIMIT)) {
+        if (!mbar_wait_sleep_bounded(&empty_ab[s], (uint32_t)(j >> 1) & 1u, P3T_WAIT_LIMIT, P3T_SLEEP_NS)) {
           ok = false;
           break;
         }
         if (j + 2 < n_slots) issue_ab(j + 2);
         if (j % nk != nk - 1) continue;
         const int ti = (int)(j / nk), t = t_begin + ti;  // the tile's last chunk: write it back
-        if (!mbar_wait_bounded(&cdone, (uint32_t)ti & 1u, P3T_WAIT_LIMIT)) {
+        if (!mbar_wait_sleep_bounded(&cdone, (uint32_t)ti & 1u, P3T_WAIT_LIMIT, P3T_SLEEP_NS)) {
           ok = false;
           break;
         }

@@ -50,10 +50,19 @@ struct RoundConfig {
 // Whether launch_rounds would run every round in one launch for this call
 // (kernel 4 with round width 64, a 16-byte addressable D and more than one round).
 bool single_launch(int dtype, const void *D, int64_t ld, int64_t n, const RoundConfig &cfg);
-// The default Phase-3 kernel for n when nothing was tuned: every round in one
-// launch from n = 3072 (profiles/phase3_variants_gmm16k.md; below it the
-// per-round launches are faster).
-inline int default_phase3(int64_t n) { return n >= 3072 ? 4 : 3; }
+// The default Phase-3 kernel for (n, dtype) when nothing was tuned: every round
+// in one launch for mid-size n, one launch per round below and above
+// (profiles/phase3_variants_gmm16k.md).  Below n = 3072 a round is about one
+// wave of tiles and the launches are cheaper than the single launch's item
+// scheduling; for large n the per-round launches' fixed cost per round is
+// small against the single launch's cost per tile.  Measured crossovers: int32
+// single launch faster at n = 8192, equal at 16384, slower at 32768 and 65536;
+// packed 16-bit (half the tiles per round) faster up to 32768, slower at
+// 65536.  The cuts sit between those points.
+inline int default_phase3(int64_t n, int dtype) {
+  const int64_t hi = dtype == 1 ? 49152 : 24576;
+  return n >= 3072 && n < hi ? 4 : 3;
+}
 
 // flag |= 1 when D (n x n, leading dimension ld) is not symmetric.
 cudaError_t launch_symmetry_check(int dtype, const void *D, int64_t n, int64_t ld, int *flag, cudaStream_t s);

@@ -39,11 +39,35 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return done != 0;
 }
 
+// As mbar_try_wait, but the thread may sleep in the instruction for up to
+// `hint_ns` nanoseconds until the phase completes (suspendTimeHint): a waiting
+// thread that has nothing else to do then issues no instructions meanwhile.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return done != 0;
+}
+
 // Waits for the barrier phase with the given parity; gives up after `limit`
 // polls and returns false (the caller records a timeout and leaves).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t limit) {
   for (uint32_t i = 0; i < limit; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
+  }
+  return false;
+}
+
+// The same with each try allowed to sleep up to hint_ns nanoseconds.
+__device__ __forceinline__ bool mbar_wait_sleep_bounded(uint64_t *bar, uint32_t parity, uint32_t limit,
+                                                        uint32_t hint_ns) {
+  for (uint32_t i = 0; i < limit; ++i) {
+    if (mbar_try_wait_sleep(bar, parity, hint_ns)) return true;
   }
   return false;
 }
