@@ -54,6 +54,7 @@ WORKLOAD_TEXT = {
     "er8k": "n=8192 Erdos-Renyi graph, average degree 16 plus a spanning path (seed 8), int32 weights U{1..1000}",
     "er16k": "n=16384 Erdos-Renyi graph, average degree 16 plus a spanning path (seed 16), int32 weights U{1..1000}",
     "er4k": "n=4096 Erdos-Renyi graph, average degree 16 plus a spanning path (seed 4), int32 weights U{1..1000}",
+    "er32k": "n=32768 Erdos-Renyi graph, average degree 16 plus a spanning path (seed 32), int32 weights U{1..1000}",
 }
 PAPER_CONTEXT = {
     "source": "paper Table 3 (Blocked-CB, Spark, 64 Xeon Gold 6130 cores, n=16384 Erdos-Renyi): 2m50s",
@@ -146,7 +147,7 @@ def ncu_traffic(kernel_key: str):
 
 def load_graph(name):
     if name.startswith("er"):
-        n = {"er4k": 4096, "er8k": 8192, "er16k": 16384}[name]
+        n = {"er4k": 4096, "er8k": 8192, "er16k": 16384, "er32k": 32768}[name]
         s, d, w = gen.er_graph(n, n // 1024)
         return gen.graphs.Graph(name, n, s, d, w, "int32")
     return gen.workload(name)
@@ -580,9 +581,42 @@ def run_reference(args, n_s: int = 2048):
     print(json.dumps(out), flush=True)
 
 
+def run_cpu_sweep(args):
+    """The oracle's single-threaded Floyd-Warshall timed on the host at several n (one JSON line, not the contract
+    line), with an n^3 extrapolation to the full sizes from the largest measured n, the paper's single-core
+    reference (T_1 = 0.022 s at n = 256, SciPy's Floyd-Warshall, Sec. 5.4) beside it, and the multi-threaded
+    Dijkstra verifier's time per source row (verification, not a baseline)."""
+    import platform
+
+    import oracle
+    sizes = (256, 512, 1024, 2048, 4096)
+    rows = []
+    for n_s in sizes:
+        reps = 5 if n_s <= 512 else 1
+        dt = min(oracle_full_fw(args.workload, n_s) for _ in range(reps))
+        rows.append({"n": n_s, "seconds": dt, "grelax_per_s": float(n_s) ** 3 / dt / 1e9})
+    rate = rows[-1]["grelax_per_s"]
+    extrap = {str(n): {"seconds_extrapolated": float(n) ** 3 / (rate * 1e9)} for n in (16384, 65536, 262144)}
+    g = load_graph("gmm16k")
+    threads = max(1, min(os.cpu_count() or 1, 64))
+    src = np.arange(0, g.n, 32)
+    t0 = time.perf_counter()
+    oracle.dijkstra(g.n, g.src, g.dst, g.w, src, threads=threads)
+    dv = time.perf_counter() - t0
+    print(json.dumps({"cpu_sweep": "oracle int64 Floyd-Warshall, one host core", "workload_recipe": args.workload,
+                      "host": {"machine": platform.machine(), "processor": platform.processor(),
+                               "cpu_count": os.cpu_count()},
+                      "measured": rows, "extrapolated_n3": extrap,
+                      "paper_single_core": {"n": 256, "seconds": 0.022, "grelax_per_s": 256 ** 3 / 0.022 / 1e9,
+                                            "source": "Sec. 5.4, SciPy Floyd-Warshall on one core"},
+                      "verifier": {"what": "oracle Dijkstra rows on gmm16k (verification, not a baseline)",
+                                   "rows": int(src.shape[0]), "threads": threads, "seconds": dv,
+                                   "ms_per_row_per_thread": dv / src.shape[0] * threads * 1e3}}), flush=True)
+
+
 def run_round_shapes(args):
-    """Every round shape (round width x Phase-3 kernel) on the workload, int32, one JSON line each (not the
-    contract line): the table the autotuner chooses from, with per-phase times."""
+    """Round shapes (round width x Phase-3 kernel) on the workload in one dtype, one JSON line each (not the
+    contract line): the table the autotuner chooses from and the default by n comes from, with per-phase times."""
     import torch
 
     import paper_1902_04446_gb300 as apsp
@@ -590,23 +624,33 @@ def run_round_shapes(args):
     g = load_graph(args.workload)
     n = g.n
     Wd = dense_on_device(torch, g, torch.int32, 1073741823, 0)
+    if args.dtype == "u16":
+        Wd = torch.where(Wd >= 1073741823, torch.full_like(Wd, 0x7FFF), Wd).to(torch.int16)
+    elif args.dtype == "fp32":
+        Wd = torch.where(Wd >= 1073741823, torch.full(Wd.shape, float("inf"), device=Wd.device), Wd.float())
     Dd = torch.empty_like(Wd)
     names = {1: "one CTA per tile", 2: "TMA, 256 threads", 3: "TMA, 512 threads",
              4: "warp-specialized, one launch per round", 5: "warp-specialized, every round in one launch"}
+    epw = 2 if args.dtype == "u16" else 1
     peak = ADDMIN_LANES_PER_CLK_PER_SM * torch.cuda.get_device_properties(0).multi_processor_count * 2070.0 / 1e3
-    for bk in (32, 64):
-        for v in (1, 2, 3, 4, 5):
-            with apsp.Handle(device=0, block_k=bk, phase3_variant=v) as h:
-                ms, launches, prof = timed_solves(torch, h, "int32", Wd, Dd, args.steps, args.warmup, None,
-                                                  profile=True)
-            ms /= args.steps
-            n3, ms3, r3 = prof[3]
-            print(json.dumps({"workload": args.workload, "round_width": bk, "phase3_variant": v,
-                              "phase3_kernel": names[v], "ms_per_solve": round(ms, 2),
-                              "grelax_per_s": float(n) ** 3 / (ms / 1e3) / 1e9,
-                              "phase_ms": {f"phase{p}": round(prof[p][1] / args.steps, 2) for p in (1, 2, 3)},
-                              "phase3_frac_of_addmin_peak_2070mhz": (r3 / (ms3 / 1e3) / 1e9 / peak) if ms3 else None,
-                              "launches_per_solve": launches // args.steps}), flush=True)
+    shapes = [(bk, v) for bk in (32, 64) for v in (1, 2, 3, 4, 5)]
+    if args.shapes:
+        shapes = [tuple(int(x) for x in sv.split("x")) for sv in args.shapes.split(",")]
+    for bk, v in shapes:
+        with apsp.Handle(device=0, block_k=bk, phase3_variant=v) as h:
+            # the solve time without per-phase events (they cost the per-round launches time), then the phases
+            ms, launches, _ = timed_solves(torch, h, args.dtype, Wd, Dd, args.steps, args.warmup, None)
+            _, _, prof = timed_solves(torch, h, args.dtype, Wd, Dd, args.steps, 0, None, profile=True)
+            status = h.last_status()
+        ms /= args.steps
+        n3, ms3, r3 = prof[3]
+        print(json.dumps({"workload": args.workload, "dtype": args.dtype, "round_width": bk, "phase3_variant": v,
+                          "phase3_kernel": names[v], "ms_per_solve": round(ms, 2),
+                          "grelax_per_s": float(n) ** 3 / (ms / 1e3) / 1e9,
+                          "phase_ms": {f"phase{p}": round(prof[p][1] / args.steps, 2) for p in (1, 2, 3)},
+                          "phase3_frac_of_addmin_peak_2070mhz":
+                              (r3 / (ms3 / 1e3) / 1e9 / (peak * epw)) if ms3 else None,
+                          "launches_per_solve": launches // args.steps, "status": status}), flush=True)
 
 
 def main(argv=None):
@@ -622,8 +666,16 @@ def main(argv=None):
     ap.add_argument("--serving-requests", type=int, default=2000)
     ap.add_argument("--round-shapes", action="store_true",
                     help="time every round shape (round width x Phase-3 kernel) instead of the benchmark line")
+    ap.add_argument("--dtype", default="int32", choices=["int32", "u16", "fp32"],
+                    help="--round-shapes: the element type solved (u16 from the int32 matrix, INF -> 0x7FFF)")
+    ap.add_argument("--shapes", default="",
+                    help="--round-shapes: comma-separated BKxVARIANT list (e.g. 64x4,64x5); default all ten")
+    ap.add_argument("--cpu-sweep", action="store_true",
+                    help="time the CPU oracle at several n (and the Dijkstra verifier) instead of the benchmark line")
     args = ap.parse_args(argv)
-    if args.round_shapes:
+    if args.cpu_sweep:
+        run_cpu_sweep(args)
+    elif args.round_shapes:
         run_round_shapes(args)
     elif args.impl == "reference":
         run_reference(args)
