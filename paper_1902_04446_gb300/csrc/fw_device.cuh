@@ -208,9 +208,12 @@ template <class Op, int BM, int BNW, int BK, int TN = 8>
 __device__ __forceinline__ void tile_minplus(const uint32_t *__restrict__ As, const uint32_t *__restrict__ Bs,
                                              uint32_t (&acc)[8][TN], int ty, int tx) {
   // deeper unrolling for the 8 x 8 block (fewer loop instructions on the
-  // add-min pipe); the 8 x 4 block of the 512-thread kernel must stay within
-  // 128 registers
-  constexpr int UNROLL = TN == 8 ? 8 : 4;
+  // add-min pipe): for the integer ops 16 k-steps per loop trip measured
+  // fastest (8: 1.1 % slower on an n = 16384 int32 solve; 32 and 64: 1.5 % and
+  // 4.7 % slower, the longer bodies costing instruction fetch); fp32, two
+  // instructions per relaxation, was 2.7 % slower at 16 than at 8; the 8 x 4
+  // block of the 512-thread kernel must stay within 128 registers
+  constexpr int UNROLL = TN == 8 ? (Op::DTYPE == 2 ? 8 : 16) : 4;
 #pragma unroll UNROLL
   for (int t = 0; t < BK; ++t) {
     const uint4 a0 = *reinterpret_cast<const uint4 *>(As + t * BM + ty * 4);
