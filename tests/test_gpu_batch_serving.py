@@ -172,6 +172,17 @@ def test_serving_reports_input_errors_per_request(H):
         H.release(t)
 
 
+@pytest.mark.parametrize("dtype,n,p3", [
+    ("int32", 2048, 3), ("int32", 3072, 4), ("int32", 16384, 4), ("int32", 24575, 4), ("int32", 24576, 3),
+    ("int32", 65536, 3), ("fp32", 16384, 4), ("fp32", 32768, 3), ("u16", 3071, 3), ("u16", 32768, 4),
+    ("u16", 49151, 4), ("u16", 49152, 3), ("u16", 262144, 3)])
+def test_default_phase3_kernel_by_n_and_dtype(lib, dtype, n, p3):
+    """Untuned, the handle takes every round in one launch (kernel 4) for mid-size n and one launch per round
+    (kernel 3) below and above; packed 16-bit, with half the tiles per round, keeps the single launch longer."""
+    with lib.Handle(device=0) as h:
+        assert h.tuned_config(dtype, n) == (64, p3)
+
+
 def test_autotune_cache_and_bit_exact_with_every_shape(lib, tmp_path):
     cache = str(tmp_path / "tune.json")
     with lib.Handle(device=0) as h:
