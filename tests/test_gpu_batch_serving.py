@@ -95,7 +95,7 @@ def test_serving_mixed_equals_alone_and_oracle(H):
 
 
 def test_serving_large_requests_on_round_kernels(H):
-    """Requests with n >= 1536 take their own group on the per-round (lookahead) kernels, an undirected one in
+    """Requests with n >= 1536 take their own group on the per-round kernels, an undirected one in
     symmetric mode and a directed one on the general path; mixed with small batched requests, each result equals
     the same matrix solved alone and the oracle's (Dijkstra from every source)."""
     rng = np.random.default_rng(1536)
