@@ -430,11 +430,11 @@ def test_directed_every_phase3_kernel(lib, block_k, variant, dt):
         np.testing.assert_array_equal(D, E)
 
 
-# ------------------------------------------------------------------ lookahead task placement
-# Round k's Phase-3 launch also runs round k+1's Phase 1 / Phase 2 tasks, placed
-# in its work stream a few tile waves after the tiles they depend on; below
-# ~2000 vertices they all fall at the end of the stream, so these sizes are
-# needed to run them between tiles (general and symmetric, directed too).
+# ------------------------------------------------------------------ every round in one launch
+# The single launch runs round k+1's Phase 1 / Phase 2 tasks in its work stream
+# a few tile waves after the tiles they depend on; below ~2000 vertices they
+# all fall at the end of a block, so these sizes are needed to run them between
+# tiles (general and symmetric, directed too).
 @pytest.mark.parametrize("symmetric,directed", [(2, False), (0, False), (0, True)])
 def test_lookahead_midstream_int32_full_matrix(lib, symmetric, directed):
     n = 4100
@@ -477,6 +477,41 @@ def test_lookahead_midstream_u16_sampled_rows(lib):
         assert h.last_status() == 0
         got = D[torch.from_numpy(rows).cuda().long()].cpu().numpy()
     np.testing.assert_array_equal(oracle.unpack_u16(got.view(np.uint16)).astype(np.int64), E)
+
+
+def dense_on_device(n, s, d, w, dtype, inf, directed=False):
+    """The dense matrix built on the device (no n x n host array at the largest sizes)."""
+    tdt = {np.int32: torch.int32, np.int16: torch.int16}[dtype]
+    W = torch.full((n, n), inf, dtype=tdt, device="cuda")
+    src = np.asarray(s) if directed else np.concatenate([s, d])
+    dst = np.asarray(d) if directed else np.concatenate([d, s])
+    ww = np.asarray(w) if directed else np.concatenate([w, w])
+    idx = torch.from_numpy(src.astype(np.int64) * n + dst.astype(np.int64)).cuda()
+    W.view(-1).scatter_reduce_(0, idx, torch.from_numpy(ww).to(device="cuda", dtype=tdt), reduce="amin")
+    W.fill_diagonal_(0)
+    return W
+
+
+@pytest.mark.parametrize("dt,n,directed", [("int32", 24000, False), ("int32", 24000, True), ("u16", 49000, False)])
+def test_single_launch_top_of_default_range_sampled_rows(lib, dt, n, directed):
+    """The largest sizes that take every round in one launch by default (int32 below 24576, packed 16-bit
+    below 49152), ragged against the 128-row tiles: 128 seeded rows equal the oracle's Dijkstra rows, and the
+    diagonal is zero."""
+    s, d, w = er_edges(n, seed=n + directed, deg=4.0, wmax=60, directed=directed)
+    inf = INF if dt == "int32" else 0x7FFF
+    W = dense_on_device(n, s, d, w, np.int32 if dt == "int32" else np.int16, inf, directed)
+    rows = np.sort(np.random.default_rng(n).choice(n, size=128, replace=False))
+    with lib.Handle(device=0) as h:
+        assert h.tuned_config(dt, n)[1] == 4  # every round in one launch
+        h.solve_t(dt, W, W)  # in place
+        assert h.last_status() == 0
+    got = W[torch.from_numpy(rows).cuda().long()].cpu().numpy()
+    assert bool((torch.diagonal(W) == 0).all())
+    del W
+    torch.cuda.empty_cache()
+    if dt == "u16":
+        got = oracle.unpack_u16(got.view(np.uint16))
+    np.testing.assert_array_equal(got.astype(np.int64), oracle.dijkstra(n, s, d, w, rows, directed=directed))
 
 
 # ------------------------------------------------------------------ symmetric mode
