@@ -11,6 +11,7 @@
 // (label(u) << 32) | (dist(u) + w(u,v))) along every edge in both directions.
 // At the fixed point label(v) is the smallest vertex of v's component and
 // dist(v) its distance from that vertex.  Distances saturate at 2^32 - 1.
+#include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -162,31 +163,37 @@ cudaError_t run_bf(const int32_t *src, const int32_t *dst, const WT *w, int64_t 
   *bound = 0;
   *ok = 1;
   if (n <= 0) return cudaSuccess;
+  constexpr int kMaxGroup = 64;  // sweeps between two host checks, at most
   DevBuf keyb(s), aux(s);
   cudaError_t e = keyb.alloc((size_t)n * sizeof(unsigned long long));
   if (e != cudaSuccess) return e;
-  e = aux.alloc(64);
+  e = aux.alloc(64 + kMaxGroup * sizeof(int));
   if (e != cudaSuccess) return e;
   unsigned long long *key = static_cast<unsigned long long *>(keyb.p);
-  int *changed = static_cast<int *>(aux.p);
-  unsigned long long *mx = reinterpret_cast<unsigned long long *>(static_cast<char *>(aux.p) + 32);
+  unsigned long long *mx = static_cast<unsigned long long *>(aux.p);
+  int *changed = reinterpret_cast<int *>(static_cast<char *>(aux.p) + 64);  // one flag per sweep of a group
   const unsigned gb = (unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
   init_keys<<<gb, 256, 0, s>>>(key, n);
   *launches += 1;
   const int64_t eb = (m + 255) / 256;
   const unsigned ge = (unsigned)(eb < 1 ? 1 : (eb > 152 * 8 ? 152 * 8 : eb));
-  int h_changed = 1;
-  // at most n + 1 sweeps are needed (each sweep fixes one more hop of every
-  // shortest-path tree); sweeps run in groups of 4 between host checks
-  for (int64_t sweep = 0; h_changed && sweep <= n + 4; sweep += 4) {
-    e = cudaMemsetAsync(changed, 0, sizeof(int), s);
+  // At most n + 1 sweeps are needed (each sweep fixes one more hop of every
+  // shortest-path tree); a sweep that changes nothing means the keys are final.
+  // Sweeps run in groups between host checks, each sweep with its own flag;
+  // the groups double (4, 8, ..., 64) so that deep graphs need few round trips
+  // while shallow ones stop after a few sweeps.
+  bool converged = false;
+  int h_flags[kMaxGroup];
+  for (int64_t done = 0, group = 4; !converged && done <= n + 1; done += group, group = std::min<int64_t>(2 * group, kMaxGroup)) {
+    e = cudaMemsetAsync(changed, 0, (size_t)group * sizeof(int), s);
     if (e != cudaSuccess) return e;
-    for (int r = 0; r < 4; ++r) bf_sweep<WT><<<ge, 256, 0, s>>>(src, dst, w, m, n, inf, key, changed);
-    *launches += 4;
-    e = cudaMemcpyAsync(&h_changed, changed, sizeof(int), cudaMemcpyDeviceToHost, s);
+    for (int r = 0; r < group; ++r) bf_sweep<WT><<<ge, 256, 0, s>>>(src, dst, w, m, n, inf, key, changed + r);
+    *launches += group;
+    e = cudaMemcpyAsync(h_flags, changed, (size_t)group * sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return e;
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;
+    for (int r = 0; r < group && !converged; ++r) converged = h_flags[r] == 0;
   }
   e = cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
@@ -198,7 +205,7 @@ cudaError_t run_bf(const int32_t *src, const int32_t *dst, const WT *w, int64_t 
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return e;
   *bound = 2 * (int64_t)h_mx;
-  *ok = (*bound < 0x7FFF) && !h_changed;
+  *ok = (*bound < 0x7FFF) && converged;
   return cudaGetLastError();
 }
 
