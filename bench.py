@@ -55,6 +55,7 @@ WORKLOAD_TEXT = {
     "er16k": "n=16384 Erdos-Renyi graph, average degree 16 plus a spanning path (seed 16), int32 weights U{1..1000}",
     "er4k": "n=4096 Erdos-Renyi graph, average degree 16 plus a spanning path (seed 4), int32 weights U{1..1000}",
     "er32k": "n=32768 Erdos-Renyi graph, average degree 16 plus a spanning path (seed 32), int32 weights U{1..1000}",
+    "er64k": "n=65536 Erdos-Renyi graph, average degree 16 plus a spanning path (seed 64), int32 weights U{1..1000}",
 }
 PAPER_CONTEXT = {
     "source": "paper Table 3 (Blocked-CB, Spark, 64 Xeon Gold 6130 cores, n=16384 Erdos-Renyi): 2m50s",
@@ -147,7 +148,7 @@ def ncu_traffic(kernel_key: str):
 
 def load_graph(name):
     if name.startswith("er"):
-        n = {"er4k": 4096, "er8k": 8192, "er16k": 16384, "er32k": 32768}[name]
+        n = {"er4k": 4096, "er8k": 8192, "er16k": 16384, "er32k": 32768, "er64k": 65536}[name]
         s, d, w = gen.er_graph(n, n // 1024)
         return gen.graphs.Graph(name, n, s, d, w, "int32")
     return gen.workload(name)
@@ -454,13 +455,14 @@ def run_gpu(args):
                              "phase3_frac": (a16 / (2 * peak)) if a16 else None, "gpu_launches": int(l16)}
         # structure-obliviousness (the paper's Sec. 5.1: runtime depends only on n):
         # the same solve on an Erdos-Renyi graph with the same n
-        if n == 16384:
-            ge = load_graph("er16k")
+        er_name = {16384: "er16k", 65536: "er64k"}.get(n)
+        if er_name and not args.workload.startswith("er"):
+            ge = load_graph(er_name)
             We = dense_on_device(torch, ge, torch.int32, 1073741823, device)
             mse, _, _ = timed_solves(torch, h, "int32", We, Dd, args.steps, args.warmup, dist)
-            out["structure_check"] = {"er16k_ms_per_step": mse / args.steps, "workload_ms_per_step": ms / args.steps,
+            out["structure_check"] = {"er_ms_per_step": mse / args.steps, "workload_ms_per_step": ms / args.steps,
                                       "ratio": (mse / args.steps) / (ms / args.steps),
-                                      "graph": WORKLOAD_TEXT["er16k"]}
+                                      "graph": WORKLOAD_TEXT[er_name]}
             del We
         gf = gen.workload("gmm16k_f32") if args.workload == "gmm16k" else g
         gf = gen.graphs.Graph(gf.name, gf.n, gf.src, gf.dst, gf.w.astype(np.float32), "fp32")
