@@ -475,7 +475,7 @@ def run_gpu(args):
                        "weights": "raw Euclidean distances as fp32 (same points)", "gpu_launches": int(lf)}
         del Wf, Df
 
-        # the min-plus product as a library primitive (Table 1 MatProd + MatMin; SURVEY NEXT-3)
+        # the min-plus product as a library primitive (Table 1 MatProd + MatMin)
         # and repeated squaring (Alg. 1) as a second workload
         mk = 8192
         gmp = torch.Generator(device="cuda").manual_seed(8192)

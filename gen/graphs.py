@@ -1,6 +1,6 @@
 """Graph and arrival-trace generators (inputs only, no shortest-path arithmetic).
 
-Readings of the workload recipes (recorded in DESIGN.md, "Input recipe"):
+Readings of the workload recipes:
 
 * RNG: ``numpy.random.default_rng(seed)``; draws happen in the order written.
 * Swiss roll: t ~ U[1.5*pi, 4.5*pi] (n draws), then height ~ U[0, 21] (n draws);

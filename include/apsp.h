@@ -139,7 +139,7 @@ apsp_status apsp_solve_edges(apsp_handle *h, int dtype, const int32_t *src, cons
  * apsp_solve_batch, APSP_E_TIMEOUT (a bounded device wait gave up). */
 apsp_status apsp_last_status(apsp_handle *h, void *stream);
 
-/* The 16-bit enable test by itself (north-star "precision selection"): for
+/* The 16-bit enable test by itself (the precision selection): for
  * every connected component c of the graph given by the int32 matrix W, the
  * single-source distances from the smallest vertex r_c of c give
  * ecc(r_c); every finite distance in c is <= 2 ecc(r_c) (triangle inequality
@@ -148,7 +148,7 @@ apsp_status apsp_last_status(apsp_handle *h, void *stream);
 apsp_status apsp_int16_bound(apsp_handle *h, const int32_t *W, int64_t n, int64_t ld, int64_t *bound, int *ok,
                              void *stream);
 
-/* ---- batched solve (north-star "batching") ------------------------------- */
+/* ---- batched solve: many graphs in one launch ----------------------------- */
 /* Solves `count` int32 graphs of uneven n in ONE persistent launch on
  * `stream`: the rounds of every graph (Alg. 3/4 phases) are cut into tasks
  * that resident CTAs pull from a device work queue in dependency order, so
@@ -197,7 +197,7 @@ apsp_status apsp_solve_squaring(apsp_handle *h, int dtype, const void *W, int64_
 apsp_status apsp_pack_u16(const int32_t *src, int64_t lds, uint16_t *dst, int64_t ldd, int64_t n, void *stream);
 apsp_status apsp_unpack_u16(const uint16_t *src, int64_t lds, int32_t *dst, int64_t ldd, int64_t n, void *stream);
 
-/* ---- request loop (north-star "serving") -------------------------------- */
+/* ---- request loop (serving) ---------------------------------------------- */
 typedef enum {
   APSP_QUEUED = 0,   /* accepted, waiting for memory or a batch slot */
   APSP_ADMITTED = 1, /* device matrix allocated and W copied; caller may reuse W */

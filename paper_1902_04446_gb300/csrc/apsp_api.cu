@@ -328,8 +328,8 @@ apsp_status solve_locked(apsp_handle *h, int dtype, const void *W, int64_t n, in
     }
     return run_rounds_locked(h, dtype, D, n, ld, s);
   }
-  // AUTO: int32 in and out; packed 16-bit when the bound allows (north-star
-  // precision selection).  The bound synchronizes the stream.
+  // AUTO: int32 in and out; packed 16-bit when the bound allows (precision
+  // selection).  The bound synchronizes the stream.
   e = apsp::launch_ingest(APSP_I32, W, const_cast<void *>(W), n, ld, h->d_status, s, &l);  // checks only (W == D: no copy)
   if (e != cudaSuccess) {
     h->launches += l;

@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 INF = oracle.INF32
-REL_TOL = 1e-4   # fp32 vs float64 oracle (spec tolerance)
+REL_TOL = 1e-4   # fp32 vs float64 oracle: |d - d64| <= 1e-4 d64
 
 
 @pytest.fixture(scope="module")
