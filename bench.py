@@ -617,7 +617,7 @@ def run_cpu_sweep(args):
     import platform
 
     import oracle
-    sizes = (256, 512, 1024, 2048, 4096)
+    sizes = tuple(int(x) for x in args.cpu_sweep_sizes.split(","))
     rows = []
     for n_s in sizes:
         reps = 5 if n_s <= 512 else 1
@@ -700,6 +700,8 @@ def main(argv=None):
                     help="--round-shapes: comma-separated BKxVARIANT list (e.g. 64x4,64x5); default all ten")
     ap.add_argument("--cpu-sweep", action="store_true",
                     help="time the CPU oracle at several n (and the Dijkstra verifier) instead of the benchmark line")
+    ap.add_argument("--cpu-sweep-sizes", default="256,512,1024,2048,4096",
+                    help="--cpu-sweep: comma-separated n to time the oracle at (16384 takes about 6 minutes)")
     args = ap.parse_args(argv)
     if args.cpu_sweep:
         run_cpu_sweep(args)
