@@ -2,8 +2,9 @@
 
 Each test copies ``oracle/apsp_oracle.c`` to a temporary directory, plants one
 mistake in the copy (a dropped term, a wrong index, a transposed operand, an
-off-by-one, a flipped comparison), compiles it, and checks that the brute-force
-pin no longer agrees.  The committed oracle is never modified.
+off-by-one, a flipped comparison, a wrong heap order), compiles it, and checks
+that the pin guarding that routine no longer agrees; the same harness on an
+unchanged copy agrees with every pin.  The committed oracle is never modified.
 """
 import ctypes
 import os
@@ -70,12 +71,7 @@ def _run(lib, W):
     return d
 
 
-@pytest.mark.skipif(shutil.which("gcc") is None, reason="gcc needed")
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_brute_force_pin_catches_mutant(tmp_path, name):
-    old, new = MUTANTS[name] or (None, None)
-    lib = _compile(tmp_path, name, old, new)
-    caught = False
+def _fw_i64_caught(lib):
     for seed in range(20):
         rng = np.random.default_rng(seed)
         n = int(rng.integers(3, 9))
@@ -83,6 +79,124 @@ def test_brute_force_pin_catches_mutant(tmp_path, name):
         edges = pins.random_graph(rng, n, 0.45, wmax=20, directed=directed)
         W = pins.dense(n, edges, directed)
         if not np.array_equal(_run(lib, W), pins.brute_force(n, edges, directed)):
-            caught = True
-            break
-    assert caught, f"mutant {name} survived the brute-force pin"
+            return True
+    return False
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="gcc needed")
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_brute_force_pin_catches_mutant(tmp_path, name):
+    old, new = MUTANTS[name] or (None, None)
+    lib = _compile(tmp_path, name, old, new)
+    assert _fw_i64_caught(lib), f"mutant {name} survived the brute-force pin"
+
+
+# Mistakes planted in the oracle's other routines, each against the pin that
+# guards it: the min-plus product against its loop definition, Dijkstra and
+# the float Floyd-Warshall against brute-force path enumeration.
+OTHER_MUTANTS = {
+    "minplus_drops_C": ("minplus", "int64_t best = C[i * nn + j];", "int64_t best = inf;"),
+    "minplus_skips_last_t": ("minplus", "for (int64_t t = 0; t < kk; ++t) {\n        int64_t a = A[i * kk + t]",
+                             "for (int64_t t = 0; t + 1 < kk; ++t) {\n        int64_t a = A[i * kk + t]"),
+    "minplus_wrong_B_index": ("minplus", "int64_t a = A[i * kk + t], b = B[t * nn + j];",
+                              "int64_t a = A[i * kk + t], b = B[(j % kk) * nn + (t % nn)];"),
+    "dijkstra_unit_weights": ("dijkstra", "int64_t nd = u.ikey + J->wi[e];", "int64_t nd = u.ikey + 1;"),
+    "dijkstra_max_heap": ("dijkstra", "return h->use_double ? (x->key < y->key) : (x->ikey < y->ikey);",
+                          "return h->use_double ? (x->key < y->key) : (x->ikey > y->ikey);"),
+    "dijkstra_skips_first_edge": ("dijkstra", "for (int64_t e = J->rowptr[u.v]; e < J->rowptr[u.v + 1]; ++e) {",
+                                  "for (int64_t e = J->rowptr[u.v] + 1; e < J->rowptr[u.v + 1]; ++e) {"),
+    "fw_f64_dropped_term": ("fw_f64", "double via = dik + dkj;", "double via = dkj;"),
+}
+
+
+def _minplus_caught(lib):
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    lib.oracle_minplus_i64.argtypes = [i64p, i64p, i64p] + [ctypes.c_int64] * 4
+    lib.oracle_minplus_i64.restype = ctypes.c_int
+    for seed in range(10):
+        rng = np.random.default_rng(100 + seed)
+        m, kk, nn = (int(x) for x in rng.integers(2, 9, size=3))
+        A = rng.integers(0, 50, size=(m, kk)).astype(np.int64)
+        B = rng.integers(0, 50, size=(kk, nn)).astype(np.int64)
+        C = rng.integers(0, 120, size=(m, nn)).astype(np.int64)
+        A[rng.random(A.shape) < 0.3] = pins.INF
+        B[rng.random(B.shape) < 0.3] = pins.INF
+        got = C.copy()
+        lib.oracle_minplus_i64(A.ctypes.data_as(i64p), B.ctypes.data_as(i64p), got.ctypes.data_as(i64p),
+                               m, kk, nn, pins.INF)
+        exp = C.copy()
+        for i in range(m):
+            for j in range(nn):
+                for t in range(kk):
+                    if A[i, t] < pins.INF and B[t, j] < pins.INF:
+                        exp[i, j] = min(exp[i, j], A[i, t] + B[t, j])
+        if not np.array_equal(got, exp):
+            return True
+    return False
+
+
+def _dijkstra_caught(lib):
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    lib.oracle_dijkstra_i64.argtypes = [ctypes.c_int64, i64p, i64p, i64p, i64p, ctypes.c_int64, i64p,
+                                        ctypes.c_int64, ctypes.c_int]
+    lib.oracle_dijkstra_i64.restype = ctypes.c_int
+    for seed in range(20):
+        rng = np.random.default_rng(200 + seed)
+        n = int(rng.integers(3, 9))
+        directed = seed % 2 == 1
+        edges = pins.random_graph(rng, n, 0.45, wmax=20, directed=directed)
+        if not edges:
+            continue
+        s = np.array([e[0] for e in edges]); d = np.array([e[1] for e in edges]); w = np.array([e[2] for e in edges])
+        if not directed:
+            s, d, w = np.concatenate([s, d]), np.concatenate([d, s]), np.concatenate([w, w])
+        order = np.argsort(s, kind="stable")
+        col = np.ascontiguousarray(d[order], dtype=np.int64)
+        ww = np.ascontiguousarray(w[order], dtype=np.int64)
+        rowptr = np.zeros(n + 1, dtype=np.int64)
+        np.add.at(rowptr, s + 1, 1)
+        rowptr = np.ascontiguousarray(np.cumsum(rowptr), dtype=np.int64)
+        src = np.arange(n, dtype=np.int64)
+        out = np.empty((n, n), dtype=np.int64)
+        lib.oracle_dijkstra_i64(n, rowptr.ctypes.data_as(i64p), col.ctypes.data_as(i64p), ww.ctypes.data_as(i64p),
+                                src.ctypes.data_as(i64p), n, out.ctypes.data_as(i64p), pins.INF, 1)
+        if not np.array_equal(out, pins.brute_force(n, edges, directed)):
+            return True
+    return False
+
+
+def _fw_f64_caught(lib):
+    f64p = ctypes.POINTER(ctypes.c_double)
+    lib.oracle_fw_f64.argtypes = [f64p] + [ctypes.c_int64] * 3
+    lib.oracle_fw_f64.restype = ctypes.c_int
+    for seed in range(20):
+        rng = np.random.default_rng(300 + seed)
+        n = int(rng.integers(3, 9))
+        edges = pins.random_graph(rng, n, 0.45, wmax=20)
+        exp = pins.brute_force(n, edges).astype(np.float64) / 4.0  # quarter weights: exact in binary
+        exp[exp >= pins.INF / 4.0] = np.inf
+        W = np.full((n, n), np.inf)
+        np.fill_diagonal(W, 0.0)
+        for u, v, w in edges:
+            W[u, v] = W[v, u] = min(W[u, v], w / 4.0)
+        lib.oracle_fw_f64(W.ctypes.data_as(f64p), n, 0, n)
+        if not np.array_equal(W, exp):
+            return True
+    return False
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="gcc needed")
+@pytest.mark.parametrize("name", sorted(OTHER_MUTANTS))
+def test_pins_catch_mutants_in_other_routines(tmp_path, name):
+    family, old, new = OTHER_MUTANTS[name]
+    lib = _compile(tmp_path, name, old, new)
+    caught = {"minplus": _minplus_caught, "dijkstra": _dijkstra_caught, "fw_f64": _fw_f64_caught}[family](lib)
+    assert caught, f"mutant {name} survived its pin"
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="gcc needed")
+def test_unmutated_copy_passes_every_pin(tmp_path):
+    """The same harness on the committed oracle, unchanged, finds nothing (the pins are not trivially failing)."""
+    lib = _compile(tmp_path, "clean", "int oracle_fw_i64(", "int oracle_fw_i64(")
+    assert not _fw_i64_caught(lib)
+    assert not _minplus_caught(lib) and not _dijkstra_caught(lib) and not _fw_f64_caught(lib)
