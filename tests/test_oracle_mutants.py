@@ -200,3 +200,56 @@ def test_unmutated_copy_passes_every_pin(tmp_path):
     lib = _compile(tmp_path, "clean", "int oracle_fw_i64(", "int oracle_fw_i64(")
     assert not _fw_i64_caught(lib)
     assert not _minplus_caught(lib) and not _dijkstra_caught(lib) and not _fw_f64_caught(lib)
+
+
+# Mistakes planted in a copy of the oracle's Python routines (the module's
+# source with one line changed, executed in a fresh namespace; it loads the
+# same committed C library).
+ORACLE_PY = os.path.join(os.path.dirname(SRC), "__init__.py")
+PY_MUTANTS = {
+    "components_no_union": ("                parent[rb] = ra", "                parent[rb] = rb"),
+    "bound_without_factor_2": ("bound = max(bound, 2 * int(mine.max()))", "bound = max(bound, int(mine.max()))"),
+    "bound_over_whole_row": ("mine = row[lab == r]", "mine = row"),
+}
+
+
+def _py_mutant(name):
+    import types
+    old, new = PY_MUTANTS[name]
+    src = open(ORACLE_PY).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found"
+    ns = {"__file__": ORACLE_PY, "__name__": f"oracle_{name}"}
+    exec(compile(src.replace(old, new), ORACLE_PY, "exec"), ns)
+    return types.SimpleNamespace(**ns)
+
+
+def _py_pins_fail(o):
+    """The CPU pins of components and int16_bound, run against module o; True when one of them fails."""
+    # components: INF exactly across components, against brute force on small graphs
+    for seed in range(10):
+        rng = np.random.default_rng(400 + seed)
+        n = int(rng.integers(3, 9))
+        edges = pins.random_graph(rng, n, 0.3, wmax=9)
+        s = np.array([e[0] for e in edges], dtype=np.int64); d = np.array([e[1] for e in edges], dtype=np.int64)
+        lab = o.components(n, s, d)
+        same = lab[:, None] == lab[None, :]
+        if not np.array_equal(same, pins.brute_force(n, edges) < pins.INF):
+            return True
+    # int16_bound: closed forms on a path and on two disjoint paths
+    s = np.arange(39); d = s + 1
+    if o.int16_bound(40, s, d, np.full(39, 9)) != (2 * 39 * 9, True):
+        return True
+    s = np.array([0, 1, 2, 3, 5, 6, 7]); d = s + 1
+    if o.int16_bound(9, s, d, np.array([3, 3, 3, 3, 7, 7, 7])) != (42, True):
+        return True
+    return False
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_pins_catch_mutants_in_python_routines(name):
+    assert _py_pins_fail(_py_mutant(name)), f"mutant {name} survived its pin"
+
+
+def test_python_pins_pass_on_the_oracle():
+    import oracle
+    assert not _py_pins_fail(oracle)

@@ -241,6 +241,15 @@ def test_int16_bound_closed_form_path():
     assert bound == 2 * 39 * 500 and not ok
 
 
+def test_int16_bound_closed_form_two_components():
+    """Two disjoint weighted paths: the bound is the larger of the two components' 2 ecc(root), each root the
+    component's smallest vertex, and unreachable pairs do not enter it."""
+    s = np.array([0, 1, 2, 3, 5, 6, 7]); d = s + 1
+    w = np.array([3, 3, 3, 3, 7, 7, 7])
+    bound, ok = oracle.int16_bound(9, s, d, w)  # vertex 4 ends path A; vertex 8 ends path B
+    assert bound == max(2 * 4 * 3, 2 * 3 * 7) and ok
+
+
 def test_int16_bound_is_sound_on_er():
     rng = np.random.default_rng(5)
     n = 120
