@@ -120,3 +120,109 @@ def test_source_plan_equals_model_and_keeps_its_invariants(plan_exe, n, epw, sym
         if j >= 1:
             block = max(block, got["total"])
     assert block == cfg.block
+
+
+@pytest.fixture(scope="module")
+def decode_exe(tmp_path_factory):
+    """The producer's item decode of the all-rounds kernel (its cached round, block and tile-row state
+    included), copied out of the kernel's source unchanged and compiled for the host."""
+    if shutil.which("g++") is None:
+        pytest.skip("g++ needed")
+    dev = open(os.path.join(CSRC, "fw_device.cuh")).read()
+    ker = open(os.path.join(CSRC, "fw_kernels.cu")).read()
+    a = ker.index("      SolveRound cr{};")
+    b = ker.index("      // The producer never blocks on another item")
+    chunk = ker[a:b]
+    parts = [
+        _block(dev, "struct TileMap {"),
+        _block(ker, "long long sym_prefix(", with_template=False),
+        _block(ker, "struct LaP2 {"),
+        re.search(r"constexpr int LA_TILE = .*?;\n", ker).group(0),
+        re.search(r"constexpr int LA_FIN_ROWS = .*?;", ker).group(0),
+        _block(ker, "struct SolveRound {", with_template=False),
+        _block(ker, "inline SolveRound solve_round("),
+    ]
+    prog = "\n".join([
+        "#include <cstdint>", "#include <cstdio>", "#include <cstdlib>",
+        "#define __host__", "#define __device__", "#define __forceinline__ inline",
+        "struct OpI32 { static constexpr int EPW = 1; };", "struct OpU16 { static constexpr int EPW = 2; };",
+    ] + parts + ["""
+struct Plan { int q, tiles_x, tiles_y, tiles_total, grid, sym, block, base1; };
+template <class Op>
+static void run(int64_t n, int sym, int grid, bool has_rowP, long long start, int mode, unsigned seed, long long cap) {
+  const int E = Op::EPW;
+  Plan P{};
+  P.q = (int)((n + 63) / 64);
+  P.tiles_x = (int)((n + 128 * E - 1) / (128 * E));
+  P.tiles_y = (int)((n + 127) / 128);
+  for (int y = 0; y < P.tiles_y; ++y) P.tiles_total += sym ? P.tiles_x - (y / E < P.tiles_x ? y / E : P.tiles_x) : P.tiles_x;
+  P.grid = grid < P.tiles_total ? grid : P.tiles_total;
+  P.sym = sym;
+  auto round_info = [&](int j) {
+    return solve_round<Op, 64>(n, P.q, P.tiles_x, P.tiles_y, P.tiles_total, P.grid, P.sym, has_rowP, j);
+  };
+  P.base1 = round_info(0).total;
+  for (int j = 1; j <= P.q; ++j) P.block = P.block > round_info(j).total ? P.block : round_info(j).total;
+"""] + [chunk] + ["""
+  const long long last = P.base1 + (long long)P.block * P.q + 1;
+  unsigned s = seed;
+  long long printed = 0;
+  for (long long item = start; item <= last && printed < cap; ++printed) {
+    int kind, rnd, info;
+    decode(item, kind, rnd, info);
+    printf("D %lld %d %d %d\\n", item, kind, rnd, info);
+    long long step = 1;
+    if (mode == 1) step = 152;
+    if (mode == 2) {  // mostly short gaps, now and then a jump of up to two blocks
+      s = s * 1664525u + 1013904223u;
+      step = (s >> 28) == 0 ? 1 + (long long)((s >> 8) % (2 * (unsigned)P.block + 1)) : 1 + (long long)((s >> 8) % 300);
+    }
+    item += step;
+  }
+}
+int main(int argc, char **argv) {
+  const int64_t n = atoll(argv[1]);
+  const int epw = atoi(argv[2]), sym = atoi(argv[3]), grid = atoi(argv[4]), rowp = atoi(argv[5]);
+  const long long start = atoll(argv[6]);
+  const int mode = atoi(argv[7]);
+  const unsigned seed = (unsigned)atoi(argv[8]);
+  const long long cap = atoll(argv[9]);
+  if (epw == 2) run<OpU16>(n, sym, grid, rowp != 0, start, mode, seed, cap);
+  else run<OpI32>(n, sym, grid, rowp != 0, start, mode, seed, cap);
+  return 0;
+}
+"""])
+    d = tmp_path_factory.mktemp("decode")
+    (d / "decode.cpp").write_text(prog)
+    exe = d / "decode"
+    subprocess.run(["g++", "-std=c++17", "-O1", "-o", str(exe), str(d / "decode.cpp")], check=True)
+    return str(exe)
+
+
+@pytest.mark.parametrize("n,epw,sym", [(300, 1, True), (1000, 2, True), (2049, 1, False), (4100, 1, True),
+                                       (4100, 2, True), (8200, 2, False), (24000, 1, True)])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_kernel_item_decode_equals_model(decode_exe, n, epw, sym, mode):
+    """Every item a CTA may take -- consecutive, every 152nd, or irregular increasing gaps with jumps across
+    blocks -- decodes to the same kind, round and tile (or task index) as the model's plain decode: the kernel's
+    cached round, block and tile-row state never changes an answer."""
+    cfg = model.Cfg(n, epw, sym, grid_cap=152)
+    cap = 60000
+    out = subprocess.run([decode_exe, str(n), str(epw), str(int(sym)), "152", str(int(cfg.has_rowP)), "0",
+                          str(mode), str(n + mode), str(cap)], capture_output=True, text=True, check=True).stdout
+    seen = 0
+    for line in out.split("\n"):
+        if not line.startswith("D "):
+            continue
+        _, item, kind, rnd, info = line.split()
+        item, kind, rnd, info = int(item), int(kind), int(rnd), int(info)
+        ek, er, ei = cfg.decode(item)
+        assert kind == ek, (item, kind, ek)
+        if kind == model.TILE:
+            assert rnd == er and ((info >> 16), info & 0xFFFF) == ei, (item, rnd, info, er, ei)
+        elif kind in (model.P1, model.P2, model.FIN):
+            assert rnd == er and (kind == model.P1 or info == ei), (item, kind, rnd, info, er, ei)
+        elif kind == model.END:
+            assert rnd == er
+        seen += 1
+    assert seen > 0
