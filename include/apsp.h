@@ -95,10 +95,11 @@ typedef struct {
                             symmetric, 2 = never.  Edge-list solves are symmetric by construction. */
 } apsp_config;
 
-/* Fills *cfg with the defaults. */
+/* Fills *cfg with the defaults (library plumbing; no paper counterpart). */
 void apsp_config_default(apsp_config *cfg);
 
-/* Creates a handle on cfg->device (cfg == NULL: defaults).  The library owns
+/* Creates a handle on cfg->device (cfg == NULL: defaults; library plumbing, no
+ * paper counterpart).  The library owns
  * the handle, its device workspace and its serving thread (started on the
  * first apsp_submit).  Errors: APSP_E_INVALID, APSP_E_CUDA. */
 apsp_status apsp_create(apsp_handle **h, const apsp_config *cfg);
@@ -123,7 +124,8 @@ apsp_status apsp_solve_t(apsp_handle *h, int dtype, const void *W, int64_t n, in
                          void *stream);
 
 /* Builds D from an edge list on the device and solves it in place: D_ii = 0,
- * D_uv = D_vu = min over duplicate edges of w, INF elsewhere (a-1 "densify").
+ * D_uv = D_vu = min over duplicate edges of w, INF elsewhere (the adjacency
+ * matrix A of Sec. 3, built on the device).
  * src/dst are int32 device arrays of m vertex ids, w holds m weights of the
  * element type (int32 for APSP_I32/APSP_AUTO, uint16 for APSP_U16, float for
  * APSP_F32).  For APSP_U16 and APSP_AUTO the 16-bit bound is computed from the
@@ -139,7 +141,8 @@ apsp_status apsp_solve_edges(apsp_handle *h, int dtype, const int32_t *src, cons
  * apsp_solve_batch, APSP_E_TIMEOUT (a bounded device wait gave up). */
 apsp_status apsp_last_status(apsp_handle *h, void *stream);
 
-/* The 16-bit enable test by itself (the precision selection): for
+/* The 16-bit enable test by itself (the precision selection; no paper
+ * counterpart, the paper's runs use one precision): for
  * every connected component c of the graph given by the int32 matrix W, the
  * single-source distances from the smallest vertex r_c of c give
  * ecc(r_c); every finite distance in c is <= 2 ecc(r_c) (triangle inequality
@@ -193,11 +196,16 @@ apsp_status apsp_solve_squaring(apsp_handle *h, int dtype, const void *W, int64_
                                 void *stream);
 
 /* int32 -> packed u16 (INF32 -> INF16) and back, n x n with separate leading
- * dimensions; the caller guarantees every finite entry is < APSP_INF_U16. */
+ * dimensions; the caller guarantees every finite entry is < APSP_INF_U16.
+ * (The storage of the packed 16-bit precision; no paper counterpart -- the
+ * paper's runs use one precision.) */
 apsp_status apsp_pack_u16(const int32_t *src, int64_t lds, uint16_t *dst, int64_t ldd, int64_t n, void *stream);
 apsp_status apsp_unpack_u16(const uint16_t *src, int64_t lds, int32_t *dst, int64_t ldd, int64_t n, void *stream);
 
 /* ---- request loop (serving) ---------------------------------------------- */
+/* A stream of independent solve requests (no paper counterpart: the paper's
+ * Spark scheduler runs one solve; Sec. 5.3 tunes its task over-decomposition,
+ * the nearest analogue of grouping requests into one launch). */
 typedef enum {
   APSP_QUEUED = 0,   /* accepted, waiting for memory or a batch slot */
   APSP_ADMITTED = 1, /* device matrix allocated and W copied; caller may reuse W */
@@ -283,7 +291,7 @@ apsp_status apsp_tuned_config(apsp_handle *h, int dtype, int64_t n, int *block_k
  * APSP_NOALLOC_MAX_N), APSP_E_CUDA (a CUDA call failed). */
 apsp_status apsp_solve_i32_noalloc(const int32_t *W, int64_t n, int64_t ld, int32_t *D, void *stream);
 
-/* ---- diagnostics -------------------------------------------------------- */
+/* ---- diagnostics (library plumbing; no paper counterpart) ---------------- */
 const char *apsp_strerror(apsp_status s);
 /* Text of the last failure on this handle (thread-local per handle); never NULL. */
 const char *apsp_last_error(apsp_handle *h);
