@@ -221,6 +221,18 @@ def test_minplus_against_broadcast_definition():
     np.testing.assert_array_equal(oracle.minplus(I0, B, np.full((kk, nn), INF)), B)
 
 
+def test_minplus_fp64_against_broadcast_definition():
+    """The float product with +inf entries, against the definition written with numpy broadcasting."""
+    rng = np.random.default_rng(12)
+    m, kk, nn = 11, 6, 8
+    A = rng.random((m, kk)) * 10; B = rng.random((kk, nn)) * 10; C = rng.random((m, nn)) * 25
+    A[rng.random(A.shape) < 0.3] = np.inf
+    B[rng.random(B.shape) < 0.3] = np.inf
+    C[rng.random(C.shape) < 0.2] = np.inf
+    exp = np.minimum(C, (A[:, :, None] + B[None, :, :]).min(axis=1))
+    np.testing.assert_array_equal(oracle.minplus(A, B, C), exp)
+
+
 def test_fw_k_slices_compose():
     """Running the outer loop in two slices equals one full run (used by the CPU baseline)."""
     g = gen.workload("roll512")
