@@ -2,20 +2,25 @@
 """Benchmark of the blocked Floyd-Warshall APSP library on one GB300.
 
 Metric: APSP relaxations per second, n^3 / t (the paper's "ops" of Sec. 5.4),
-reported in GRelax/s.  One step = one apsp_solve of the whole workload matrix
-(ingest, symmetry check, q rounds of Phase 1 / 2 / 3, mirror pass), inputs
-resident in HBM; the graph is undirected, so the default path runs the
-symmetric mode (about half the relaxations; the general path is reported
-beside it); the matrix
-(1.07 GB at n = 16384) is larger than L2, so no extra flush is needed.
+reported in GRelax/s, for int32 and for packed 16-bit distances.  The default
+workload is roll64k: the n = 65536 Swiss-roll kNN graph (int32 weights
+max(1, rint(4 d))), the size at which both element types are measured.  One
+step = one apsp_solve of the whole workload matrix (ingest, symmetry check,
+q rounds of Phase 1 / 2 / 3, mirror pass), inputs resident in HBM; the graph
+is undirected, so the default path runs the symmetric mode (about half the
+relaxations).  The matrix (17.2 GB) is larger than L2, so no flush is needed.
 
-Printed JSON line (rank 0): the headline int32 number, the packed-16-bit
-(automatic precision selection: bound + pack + u16x2 rounds + unpack) and fp32
-variants, the end-to-end number through host buffers, the live Phase-3
-roofline, the CPU-oracle baseline, clocks sampled during the timed region, and
-the serving replay (p50/p99 latency and solves/s against one-at-a-time solves).
+Printed JSON line (rank 0): the headline int32 number with the live Phase-3
+roofline, the packed-16-bit number on the same graph and steps (automatic
+precision selection: bound + pack + u16x2 rounds + unpack), the end-to-end
+number through host buffers on the same graph and steps, clocks sampled
+during the timed region, the add-min issue rate measured live, a structure
+check (an Erdos-Renyi graph of the same n), the n = 16384 variants (general
+path, fp32 with its own roofline, min-plus product, repeated squaring), the
+serving replay (p50/p99 latency and solves/s against one-at-a-time solves)
+and the CPU-oracle baseline.
 
-  python bench.py [--gpus N --steps K --warmup W] [--workload gmm16k]
+  python bench.py [--gpus N --steps K --warmup W] [--workload roll64k]
   python bench.py --impl reference ...   # the CPU oracle timed as the reference arm
 
 Multi-GPU (torchrun, N > 1): every rank solves its own replica of the workload
@@ -45,7 +50,7 @@ import gen  # noqa: E402
 
 METRIC = "APSP GRelax/s (n³/s) int32 vs packed-int16; serving p50/p99 ms and solves/s"
 UNIT = "GRelax/s"
-ADDMIN_LANES_PER_CLK_PER_SM = 64  # measured add-min issue rate (profiles/addmin_issue_peak.md)
+ADDMIN_LANES_PER_CLK_PER_SM = 64  # add-min lane-ops per clock per SM: 64 INT32 lanes per SM, as apsp_addmin_peak measures
 WORKLOAD_TEXT = {
     "gmm16k": "n=16384 symmetric k=10 kNN graph over a 10-D 8-component Gaussian mixture (seed 1), "
               "int32 weights max(1, rint(50 d)), dense INF-padded adjacency matrix",
@@ -263,12 +268,18 @@ def oracle_full_fw(workload: str, n_s: int):
     return time.perf_counter() - t0
 
 
-def cpu_baseline(workload: str, n_s: int = 4096):
-    """The oracle (single-threaded C Floyd-Warshall), complete run on a bounded sample of the workload."""
+def cpu_baseline(workload: str, n_s: int = 4096, n_full: int | None = None):
+    """The oracle (single-threaded C Floyd-Warshall), complete run on a bounded sample of the workload, with the
+    n^3 extrapolation of its time to the workload's own n (labelled as such: a full run there takes days)."""
     dt = oracle_full_fw(workload, n_s)
-    return {"value": float(n_s) ** 3 / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"the oracle's complete int64 Floyd-Warshall on the same generator recipe at n={n_s} "
-                      f"({dt:.1f} s on one host core); value = n^3 / t"}
+    rate = float(n_s) ** 3 / dt / 1e9
+    out = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"the oracle's complete int64 Floyd-Warshall on the same generator recipe at n={n_s} "
+                     f"({dt:.1f} s on one host core); value = n^3 / t"}
+    if n_full and n_full > n_s:
+        out["extrapolated"] = {"n": n_full, "seconds": float(n_full) ** 3 / (rate * 1e9),
+                               "how": "n^3 extrapolation of the measured rate (not measured)"}
+    return out
 
 
 def _replay_batched(torch, apsp, device, mats, arrival):
@@ -363,170 +374,37 @@ def serving_replay(torch, apsp, device, nreq):
     return out
 
 
-def run_gpu(args):
-    import torch
+def addmin_peaks(apsp, device):
+    """The add-min issue rate of each dtype's add-min form, measured live on this GPU (apsp_addmin_peak)."""
+    import ctypes
+    L = apsp.get_lib()
+    out = {}
+    for name, code in (("int32", apsp.APSP_I32), ("u16x2", apsp.APSP_U16), ("fp32", apsp.APSP_F32)):
+        lanes, rps = ctypes.c_double(), ctypes.c_double()
+        if L.apsp_addmin_peak(device, code, ctypes.byref(lanes), ctypes.byref(rps)) == 0:
+            out[name] = {"lane_ops_per_clk_per_sm": lanes.value, "grelax_per_s_event_timed": rps.value / 1e9}
+    return out
 
-    import paper_1902_04446_gb300 as apsp
 
-    ws, rank, local = dist_info()
-    dist = None
-    if ws > 1:
-        import torch.distributed as tdist
-        torch.cuda.set_device(local)
-        tdist.init_process_group("nccl")
-        dist = tdist
-    device = local
-    torch.cuda.set_device(device)
-    props = torch.cuda.get_device_properties(device)
-    g = load_graph(args.workload)
-    n = g.n
-    Wd = dense_on_device(torch, g, torch.int32, 1073741823, device)
-    Dd = torch.empty_like(Wd)
-    h = apsp.Handle(device=device)
-
-    with ClockSampler(device) as clk:
-        ms, launches, prof = timed_solves(torch, h, "int32", Wd, Dd, args.steps, args.warmup, dist, profile=True)
-    clocks = clk.summary()
-    relax_step = float(n) ** 3
-    value, ms_max = job_value(torch, dist, relax_step * args.steps, ms)
-
-    # roofline of the dominant kernel (Phase 3), from the live event timings
-    sms = props.multi_processor_count
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+def phase3_rate(prof):
+    """Relaxations per second of the Phase-3 launches (the dominant kernel), from the per-launch CUDA events."""
     n3, ms3, r3 = prof[3]
-    achieved = (r3 / n3) / (ms3 / n3 / 1e3) / 1e9 if n3 else None
-    peak = ADDMIN_LANES_PER_CLK_PER_SM * sms * sm_max_mhz * 1e6 / 1e9
-    phase_ms = {f"phase{p}": round(prof[p][1] / args.steps, 3) for p in (1, 2, 3)}
-    if h.tuned_config("int32", n)[1] == 4:
-        kname, kkey = ("fw_solve_ws<int32> (every round in one launch: Phase-3 tiles with each round's Phase 1 and "
-                       "Phase 2 as tasks)"), "fw_solve_ws"
-        work = ("relaxations performed in the launch: Phase 3 (in symmetric mode only the tiles touching the upper "
-                "triangle) plus every round's Phase 1 and Phase 2")
-    else:
-        kname, kkey = "fw_phase3_ws<int32> (warp-specialized Phase 3, one launch per round)", "fw_phase3_ws"
-        work = ("relaxations performed by the Phase-3 launches (in symmetric mode only the tiles touching the upper "
-                "triangle)")
-    roofline = {"bound": "alu", "kernel": kname,
-                "achieved": achieved, "peak": peak, "unit": UNIT, "work": work,
-                "frac": (achieved / peak) if achieved else None,
-                "peak_basis": f"{ADDMIN_LANES_PER_CLK_PER_SM} add-min lanes/clk/SM (measured) x {sms} SMs x "
-                              f"{sm_max_mhz:.0f} MHz (max SM clock)",
-                "traffic": ncu_traffic(f"{kkey}_int32_{args.workload}"),
-                "phase_ms_per_step": phase_ms,
-                "phase3_share_of_step": prof[3][1] / ms if ms else None}
-    if clocks and achieved:
-        roofline["frac_at_median_clock"] = achieved / (ADDMIN_LANES_PER_CLK_PER_SM * sms * clocks["sm_mhz"] / 1e3)
+    return (r3 / (ms3 / 1e3) / 1e9) if n3 and ms3 else None
 
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "int32", "data": "synthetic",
-           "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT.get(args.workload, '')}", "n": n,
-                      "edges": int(g.src.shape[0]), "round_width": 64, "parallelism": f"replicas x{ws}",
-                      "l2": "input matrix larger than L2 (%.2f GB), no flush needed" % (n * n * 4 / 1e9)},
-           "roofline": roofline, "gpu_launches": int(launches), "clocks": clocks,
-           "paper_context": PAPER_CONTEXT}
 
-    # variants: the general (non-symmetric) path, automatic precision (bound +
-    # pack + packed u16x2 rounds + unpack) and fp32
-    if not args.no_variants:
-        with apsp.Handle(device=device, symmetric=2) as hg:
-            msg, lg, profg = timed_solves(torch, hg, "int32", Wd, Dd, args.steps, args.warmup, dist, profile=True)
-        vg, msg = job_value(torch, dist, relax_step * args.steps, msg)
-        n3g, m3g, r3g = profg[3]
-        ag = (r3g / n3g) / (m3g / n3g / 1e3) / 1e9 if n3g else None
-        out["general_int32"] = {"value": vg, "unit": UNIT, "ms_per_step": msg / args.steps,
-                                "path": "symmetric mode off: every Phase-3 tile updated, no mirror pass",
-                                "phase3_achieved": ag, "phase3_frac": (ag / peak) if ag else None,
-                                "gpu_launches": int(lg)}
-        ms16, l16, prof16 = timed_solves(torch, h, "auto", Wd, Dd, args.steps, args.warmup, dist, profile=True)
-        ms16 = max_over_ranks(torch, dist, ms16)
-        v16 = sum_over_ranks(torch, dist, relax_step * args.steps) / (ms16 / 1e3) / 1e9
-        n3, m3, r3 = prof16[3]
-        a16 = (r3 / n3) / (m3 / n3 / 1e3) / 1e9 if n3 else None
-        out["packed_u16"] = {"value": v16, "unit": UNIT, "ms_per_step": ms16 / args.steps,
-                             "speedup_vs_int32": v16 / value, "path": "apsp_solve(APSP_AUTO): bound pass, pack, "
-                             "u16x2 rounds, unpack (all inside the timed region)",
-                             "phase3_achieved": a16, "phase3_peak": 2 * peak,
-                             "phase3_frac": (a16 / (2 * peak)) if a16 else None, "gpu_launches": int(l16)}
-        # structure-obliviousness (the paper's Sec. 5.1: runtime depends only on n):
-        # the same solve on an Erdos-Renyi graph with the same n
-        er_name = {16384: "er16k", 65536: "er64k"}.get(n)
-        if er_name and not args.workload.startswith("er"):
-            ge = load_graph(er_name)
-            We = dense_on_device(torch, ge, torch.int32, 1073741823, device)
-            mse, _, _ = timed_solves(torch, h, "int32", We, Dd, args.steps, args.warmup, dist)
-            out["structure_check"] = {"er_ms_per_step": mse / args.steps, "workload_ms_per_step": ms / args.steps,
-                                      "ratio": (mse / args.steps) / (ms / args.steps),
-                                      "graph": WORKLOAD_TEXT[er_name]}
-            del We
-        gf = gen.workload("gmm16k_f32") if args.workload == "gmm16k" else g
-        gf = gen.graphs.Graph(gf.name, gf.n, gf.src, gf.dst, gf.w.astype(np.float32), "fp32")
-        Wf = dense_on_device(torch, gf, torch.float32, float("inf"), device)
-        Df = torch.empty_like(Wf)
-        msf, lf, _ = timed_solves(torch, h, "fp32", Wf, Df, args.steps, args.warmup, dist)
-        msf = max_over_ranks(torch, dist, msf)
-        out["fp32"] = {"value": sum_over_ranks(torch, dist, relax_step * args.steps) / (msf / 1e3) / 1e9, "unit": UNIT,
-                       "ms_per_step": msf / args.steps,
-                       "weights": "raw Euclidean distances as fp32 (same points)", "gpu_launches": int(lf)}
-        del Wf, Df
-
-        # the min-plus product as a library primitive (Table 1 MatProd + MatMin)
-        # and repeated squaring (Alg. 1) as a second workload
-        mk = 8192
-        gmp = torch.Generator(device="cuda").manual_seed(8192)
-        A = torch.randint(0, 1000, (mk, mk), dtype=torch.int32, device="cuda", generator=gmp)
-        B = torch.randint(0, 1000, (mk, mk), dtype=torch.int32, device="cuda", generator=gmp)
-        C = torch.full((mk, mk), 1073741823, dtype=torch.int32, device="cuda")
-        for _ in range(max(1, args.warmup)):
-            h.minplus(A, B, C)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(args.steps):
-            h.minplus(A, B, C)
-        e1.record()
-        torch.cuda.synchronize()
-        msmp = e0.elapsed_time(e1) / args.steps
-        gr = float(mk) ** 3 / (msmp / 1e3) / 1e9
-        out["minplus"] = {"m": mk, "k": mk, "n": mk, "dtype": "int32", "ms": msmp, "value": gr, "unit": UNIT,
-                          "frac_of_addmin_peak": gr / peak, "inputs": "uniform U{0..999} (torch generator seed 8192)"}
-        del A, B, C
-        gs = load_graph("er4k")
-        Ws = dense_on_device(torch, gs, torch.int32, 1073741823, device)
-        Ds = torch.empty_like(Ws)
-        h.solve_squaring("int32", Ws, Ds)
-        torch.cuda.synchronize()
-        e0.record()
-        for _ in range(args.steps):
-            h.solve_squaring("int32", Ws, Ds)
-        e1.record()
-        torch.cuda.synchronize()
-        mss = e0.elapsed_time(e1) / args.steps
-        msfw, _, _ = timed_solves(torch, h, "int32", Ws, Ds, args.steps, 1, None)
-        nsq = gs.n
-        prods = int(np.ceil(np.log2(nsq - 1)))
-        out["squaring"] = {"graph": WORKLOAD_TEXT["er4k"], "n": nsq, "products": prods,
-                           "ms_per_solve": mss, "products_grelax_per_s": prods * float(nsq) ** 3 / (mss / 1e3) / 1e9,
-                           "floyd_warshall_ms_per_solve": msfw / args.steps,
-                           "path": "apsp_solve_squaring (Alg. 1): ceil(log2(n-1)) in-place min-plus products"}
-        del Ws, Ds
-
-    # end to end through the public API with host buffers (pinned), copies inside the timed region: every
-    # step copies its input in and its result out; one copy stream moves step i+1's input in and another
-    # step i-1's result out while step i solves (two device buffer pairs), so the copy engines work beside
-    # the solve instead of between solves
-    Wh = Wd.cpu().pin_memory()
-    Dh = torch.empty_like(Wh).pin_memory()
+def e2e_measure(torch, h, Wd, Dd, steps, warmup, dist):
+    """End to end through the public API with host buffers (pinned), copies inside the timed region: every step
+    copies its input in and its result out; one copy stream moves step i+1's input in and another step i-1's
+    result out while step i solves (two device buffer pairs), so the copy engines work beside the solve."""
+    device = Wd.device
+    Wh = torch.empty(Wd.shape, dtype=Wd.dtype, pin_memory=True)
+    Wh.copy_(Wd)
+    Dh = torch.empty(Wd.shape, dtype=Wd.dtype, pin_memory=True)
     stream = torch.cuda.current_stream()
     s_in, s_out = torch.cuda.Stream(device), torch.cuda.Stream(device)
     Wb, Db = [Wd, torch.empty_like(Wd)], [Dd, torch.empty_like(Dd)]
 
-    def e2e_steps(k):
+    def run(k):
         solved = [None, None]  # per buffer pair: the event after its last solve
         out_done = [None, None]  # per buffer pair: the event after its last copy out
         for i in range(k):
@@ -549,39 +427,237 @@ def run_gpu(args):
                 out_done[b] = torch.cuda.Event()
                 out_done[b].record(s_out)
 
-    e2e_steps(max(1, args.warmup))
+    run(max(1, warmup))
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    e2e_steps(args.steps)
+    run(steps)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     if dist is not None:
         dist.barrier()
-    if not torch.equal(Dh, Db[(args.steps - 1) & 1].cpu()):
+    # the last result on the host equals the device result (rows sampled: the matrix can be 17 GB)
+    last = Db[(steps - 1) & 1]
+    rows = torch.linspace(0, Wd.shape[0] - 1, 64, dtype=torch.long)
+    if not torch.equal(Dh[rows], last[rows.to(last.device)].cpu()):
         raise RuntimeError("end-to-end result on the host differs from the device result")
-    mse = max_over_ranks(torch, dist, wall * 1e3)
+    nbytes = int(Wh.numel() * Wh.element_size())
+    del Wb, Db, Wh, Dh
+    return wall * 1e3, nbytes
+
+
+def run_gpu(args):
+    import torch
+
+    import paper_1902_04446_gb300 as apsp
+
+    ws, rank, local = dist_info()
+    dist = None
+    if ws > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    device = local
+    torch.cuda.set_device(device)
+    props = torch.cuda.get_device_properties(device)
+    sms = props.multi_processor_count
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    live = addmin_peaks(apsp, device)
+    peak = ADDMIN_LANES_PER_CLK_PER_SM * sms * sm_max_mhz * 1e6 / 1e9  # GRelax/s, int32 (u16x2: twice)
+
+    g = load_graph(args.workload)
+    n = g.n
+    Wd = dense_on_device(torch, g, torch.int32, 1073741823, device)
+    Dd = torch.empty_like(Wd)
+    h = apsp.Handle(device=device)
+    relax_step = float(n) ** 3
+
+    # ---- the headline: int32 solves of the workload, inputs resident in HBM
+    with ClockSampler(device) as clk:
+        ms, launches, prof = timed_solves(torch, h, "int32", Wd, Dd, args.steps, args.warmup, dist, profile=True)
+    clocks = clk.summary()
+    value, ms_max = job_value(torch, dist, relax_step * args.steps, ms)
+
+    # roofline of the dominant kernel (Phase 3), from the live event timings
+    achieved = phase3_rate(prof)
+    phase_ms = {f"phase{p}": round(prof[p][1] / args.steps, 3) for p in (1, 2, 3)}
+    if h.tuned_config("int32", n)[1] == 4:
+        kname, kkey = ("fw_solve_ws<int32> (every round in one launch: Phase-3 tiles with each round's Phase 1 and "
+                       "Phase 2 as tasks)"), "fw_solve_ws"
+        work = ("relaxations performed in the launch: Phase 3 (in symmetric mode only the tiles touching the upper "
+                "triangle) plus every round's Phase 1 and Phase 2")
+    else:
+        kname, kkey = "fw_phase3_ws<int32> (warp-specialized Phase 3, one launch per round)", "fw_phase3_ws"
+        work = ("relaxations performed by the Phase-3 launches (in symmetric mode only the tiles touching the upper "
+                "triangle)")
+    roofline = {"bound": "alu", "kernel": kname,
+                "achieved": achieved, "peak": peak, "unit": UNIT, "work": work,
+                "frac": (achieved / peak) if achieved else None,
+                "peak_basis": f"{ADDMIN_LANES_PER_CLK_PER_SM} add-min lanes/clk/SM (the SM's INT32 lanes; measured "
+                              f"live: {live.get('int32', {}).get('lane_ops_per_clk_per_sm', float('nan')):.1f}) x "
+                              f"{sms} SMs x {sm_max_mhz:.0f} MHz (max SM clock)",
+                "traffic": ncu_traffic(f"{kkey}_int32_{args.workload}"),
+                "traffic_unit": "DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+                "phase_ms_per_step": phase_ms,
+                "phase3_launches_per_step": prof[3][0] // max(1, args.steps),
+                "phase3_share_of_step": prof[3][1] / ms if ms else None}
+    if clocks and achieved:
+        roofline["frac_at_median_clock"] = achieved / (ADDMIN_LANES_PER_CLK_PER_SM * sms * clocks["sm_mhz"] / 1e3)
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "int32", "data": "synthetic",
+           "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT.get(args.workload, '')}", "n": n,
+                      "edges": int(g.src.shape[0]), "round_width": 64, "parallelism": f"replicas x{ws}",
+                      "l2": "input matrix larger than L2 (%.2f GB), no flush needed" % (n * n * 4 / 1e9)},
+           "roofline": roofline, "gpu_launches": int(launches), "clocks": clocks,
+           "addmin_peak_live": live, "paper_context": PAPER_CONTEXT}
+
+    # ---- the packed 16-bit half of the metric, on the same graph and the same steps
+    if not args.no_variants:
+        ms16, l16, prof16 = timed_solves(torch, h, "auto", Wd, Dd, args.steps, args.warmup, dist, profile=True)
+        v16, ms16 = job_value(torch, dist, relax_step * args.steps, ms16)
+        a16 = phase3_rate(prof16)
+        out["packed_u16"] = {"value": v16, "unit": UNIT, "ms_per_step": ms16 / args.steps,
+                             "speedup_vs_int32": v16 / value, "path": "apsp_solve(APSP_AUTO): bound pass, pack, "
+                             "u16x2 rounds, unpack (all inside the timed region)",
+                             "phase3_achieved": a16, "phase3_peak": 2 * peak,
+                             "phase3_frac": (a16 / (2 * peak)) if a16 else None, "gpu_launches": int(l16),
+                             "bytes_per_distance": 2}
+
+    # ---- end to end through host buffers, same graph and steps
+    mse, nbytes = e2e_measure(torch, h, Wd, Dd, args.steps, args.warmup, dist)
+    mse = max_over_ranks(torch, dist, mse)
     out["e2e"] = {"value": sum_over_ranks(torch, dist, relax_step * args.steps) / (mse / 1e3) / 1e9, "unit": UNIT,
-                  "h2d_bytes_per_step": int(Wh.numel() * 4), "d2h_bytes_per_step": int(Dh.numel() * 4),
+                  "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                   "ms_per_step": mse / args.steps,
                   "pipeline": "pinned host buffers; step i+1's copy in and step i-1's copy out overlap step i's "
                               "solve (two copy streams, two device buffer pairs); host wall clock from the first "
                               "copy in to the last copy out"}
-    del Wb, Db
-    del Wh, Dh
+    torch.cuda.empty_cache()
+
+    if not args.no_variants:
+        # structure-obliviousness (the paper's Sec. 5.1: runtime depends only on n): the same solve on an
+        # Erdos-Renyi graph with the same n; fewer repeats at the large sizes
+        er_name = {16384: "er16k", 65536: "er64k"}.get(n)
+        if er_name and not args.workload.startswith("er"):
+            reps = args.steps if n <= 16384 else min(args.steps, 2)
+            ge = load_graph(er_name)
+            We = dense_on_device(torch, ge, torch.int32, 1073741823, device)
+            mse_er, _, _ = timed_solves(torch, h, "int32", We, Dd, reps, 1, dist)
+            ms_w, _, _ = timed_solves(torch, h, "int32", Wd, Dd, reps, 0, dist)
+            out["structure_check"] = {"er_ms_per_step": mse_er / reps, "workload_ms_per_step": ms_w / reps,
+                                      "ratio": (mse_er / reps) / (ms_w / reps), "graph": WORKLOAD_TEXT[er_name],
+                                      "repeats": reps}
+            del We
+        del Wd, Dd
+        torch.cuda.empty_cache()
+        out.update(extras_gmm16k(torch, apsp, h, args, dist, device, peak, live, sms, sm_max_mhz))
+    else:
+        del Wd, Dd
     h.close()
 
     if rank == 0 and not args.no_serving:
         out["serving"] = serving_replay(torch, apsp, device, args.serving_requests)
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.workload)
+        out["cpu_baseline"] = cpu_baseline(args.workload, n_full=n)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def extras_gmm16k(torch, apsp, h, args, dist, device, peak, live, sms, sm_max_mhz):
+    """The other variants, on the n = 16384 workload (one solve takes ~0.1 s there): the general (non-symmetric)
+    path, fp32 weights with their own Phase-3 roofline, the min-plus product and repeated squaring."""
+    out = {}
+    g = load_graph("gmm16k")
+    n = g.n
+    relax_step = float(n) ** 3
+    W = dense_on_device(torch, g, torch.int32, 1073741823, device)
+    D = torch.empty_like(W)
+    with apsp.Handle(device=device, symmetric=2) as hg:
+        msg, lg, profg = timed_solves(torch, hg, "int32", W, D, args.steps, args.warmup, dist, profile=True)
+    vg, msg = job_value(torch, dist, relax_step * args.steps, msg)
+    ag = phase3_rate(profg)
+    out["general_int32"] = {"workload": "gmm16k: " + WORKLOAD_TEXT["gmm16k"], "value": vg, "unit": UNIT,
+                            "ms_per_step": msg / args.steps,
+                            "path": "symmetric mode off: every Phase-3 tile updated, no mirror pass",
+                            "phase3_achieved": ag, "phase3_frac": (ag / peak) if ag else None,
+                            "gpu_launches": int(lg)}
+    del W, D
+    gf = gen.workload("gmm16k_f32")
+    gf = gen.graphs.Graph(gf.name, gf.n, gf.src, gf.dst, gf.w.astype(np.float32), "fp32")
+    Wf = dense_on_device(torch, gf, torch.float32, float("inf"), device)
+    Df = torch.empty_like(Wf)
+    msf, lf, proff = timed_solves(torch, h, "fp32", Wf, Df, args.steps, args.warmup, dist, profile=True)
+    vf, msf = job_value(torch, dist, relax_step * args.steps, msf)
+    af = phase3_rate(proff)
+    f_lanes = live.get("fp32", {}).get("lane_ops_per_clk_per_sm")
+    peak_f = f_lanes * sms * sm_max_mhz / 1e3 if f_lanes else None
+    kf = "fw_solve_ws<fp32> (every round in one launch)" if h.tuned_config("fp32", n)[1] == 4 else \
+        "fw_phase3_ws<fp32> (one launch per round)"
+    out["fp32"] = {"workload": "gmm16k_f32: the gmm16k points, raw Euclidean distances as fp32 weights",
+                   "value": vf, "unit": UNIT, "ms_per_step": msf / args.steps, "gpu_launches": int(lf),
+                   "roofline": {"bound": "alu", "kernel": kf, "achieved": af, "peak": peak_f, "unit": UNIT,
+                                "frac": (af / peak_f) if (af and peak_f) else None,
+                                "peak_basis": f"fp32 add-min (fadd + fmin) lane-ops/clk/SM measured live "
+                                              f"({f_lanes:.1f}) x {sms} SMs x {sm_max_mhz:.0f} MHz"
+                                if f_lanes else None,
+                                "frac_of_int32_peak": (af / peak) if af else None}}
+    del Wf, Df
+
+    # the min-plus product as a library primitive (Table 1 MatProd + MatMin)
+    # and repeated squaring (Alg. 1) as a second workload
+    mk = 8192
+    gmp = torch.Generator(device="cuda").manual_seed(8192)
+    A = torch.randint(0, 1000, (mk, mk), dtype=torch.int32, device="cuda", generator=gmp)
+    B = torch.randint(0, 1000, (mk, mk), dtype=torch.int32, device="cuda", generator=gmp)
+    C = torch.full((mk, mk), 1073741823, dtype=torch.int32, device="cuda")
+    for _ in range(max(1, args.warmup)):
+        h.minplus(A, B, C)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        h.minplus(A, B, C)
+    e1.record()
+    torch.cuda.synchronize()
+    msmp = e0.elapsed_time(e1) / args.steps
+    gr = float(mk) ** 3 / (msmp / 1e3) / 1e9
+    out["minplus"] = {"m": mk, "k": mk, "n": mk, "dtype": "int32", "ms": msmp, "value": gr, "unit": UNIT,
+                      "frac_of_addmin_peak": gr / peak, "inputs": "uniform U{0..999} (torch generator seed 8192)"}
+    del A, B, C
+    gs = load_graph("er4k")
+    Ws = dense_on_device(torch, gs, torch.int32, 1073741823, device)
+    Ds = torch.empty_like(Ws)
+    h.solve_squaring("int32", Ws, Ds)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        h.solve_squaring("int32", Ws, Ds)
+    e1.record()
+    torch.cuda.synchronize()
+    mss = e0.elapsed_time(e1) / args.steps
+    msfw, _, _ = timed_solves(torch, h, "int32", Ws, Ds, args.steps, 1, None)
+    nsq = gs.n
+    prods = int(np.ceil(np.log2(nsq - 1)))
+    out["squaring"] = {"graph": WORKLOAD_TEXT["er4k"], "n": nsq, "products": prods,
+                       "ms_per_solve": mss, "products_grelax_per_s": prods * float(nsq) ** 3 / (mss / 1e3) / 1e9,
+                       "floyd_warshall_ms_per_solve": msfw / args.steps,
+                       "path": "apsp_solve_squaring (Alg. 1): ceil(log2(n-1)) in-place min-plus products"}
+    del Ws, Ds
+    torch.cuda.empty_cache()
+    return out
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -687,7 +763,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="gmm16k", choices=sorted(WORKLOAD_TEXT))
+    ap.add_argument("--workload", default="roll64k", choices=sorted(WORKLOAD_TEXT))
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -702,8 +778,17 @@ def main(argv=None):
                     help="time the CPU oracle at several n (and the Dijkstra verifier) instead of the benchmark line")
     ap.add_argument("--cpu-sweep-sizes", default="256,512,1024,2048,4096",
                     help="--cpu-sweep: comma-separated n to time the oracle at (16384 takes about 6 minutes)")
+    ap.add_argument("--addmin-peak", action="store_true",
+                    help="print the add-min issue rate of each dtype measured on this GPU (apsp_addmin_peak) and exit")
     args = ap.parse_args(argv)
-    if args.cpu_sweep:
+    if args.addmin_peak:
+        import torch
+
+        import paper_1902_04446_gb300 as apsp
+        p = torch.cuda.get_device_properties(0)
+        print(json.dumps({"gpu": p.name, "sms": p.multi_processor_count, "addmin_peak": addmin_peaks(apsp, 0)}),
+              flush=True)
+    elif args.cpu_sweep:
         run_cpu_sweep(args)
     elif args.round_shapes:
         run_round_shapes(args)

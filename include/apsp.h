@@ -195,6 +195,75 @@ apsp_status apsp_minplus(apsp_handle *h, int dtype, const void *A, int64_t lda, 
 apsp_status apsp_solve_squaring(apsp_handle *h, int dtype, const void *W, int64_t n, int64_t ld, void *D,
                                 void *stream);
 
+/* ---- upper-triangular storage ------------------------------------------- */
+/* The paper stores only the upper triangle of blocks of the symmetric
+ * distance matrix; a lower block is the transpose of an upper one (Sec. 4,
+ * the block decomposition; Sec. 3: A_ij = A_ji).  These calls keep an
+ * undirected graph's n x n matrix in about half the memory: it is cut into
+ * S x S super-tiles (S = 128 elements for APSP_I32 / APSP_F32, 256 for
+ * APSP_U16) and only the super-tiles (I, J) with I <= J are stored -- the
+ * diagonal super-tiles in full -- folded into one rectangle of `rows` rows
+ * with a row pitch of `ld` elements (about n^2 / 2 elements plus one
+ * super-tile band; 68.8 GB instead of 137 GB for n = 262144 in packed
+ * 16-bit).  Element (r, c) is stored when floor(c / S) >= floor(r / S);
+ * rows and columns n .. S*ceil(n/S)-1 are padding, whose contents after a
+ * solve are unspecified.  The rectangle ("T" below) is caller-owned device
+ * memory of apsp_tri_layout's `bytes`, 16-byte aligned.
+ * Placement of a super-row I (T = ceil(n / S) super-rows, Th = ceil(T / 2)):
+ * I < Th in rectangle rows I*S.. with columns shifted right by S; I >= Th in
+ * rectangle rows (2 Th - 1 - I)*S.. with columns shifted left by I*S.  This
+ * mapping is the format's definition; apsp_tri_rows and apsp_tri_to_dense
+ * read it back. */
+
+/* Rectangle of the upper-triangular layout for n and dtype (APSP_I32,
+ * APSP_U16 or APSP_F32): *rows, *ld (row pitch, elements) and *bytes (each
+ * nullable, not all).  Host only.  Errors: APSP_E_INVALID. */
+apsp_status apsp_tri_layout(int dtype, int64_t n, int64_t *rows, int64_t *ld, int64_t *bytes);
+
+/* T <- the upper-triangular layout of the symmetric dense n x n matrix W
+ * (device, leading dimension ldw; only its stored part is copied), padding
+ * INF.  The input checks of apsp_solve_t run on the device, plus a symmetry
+ * check (an asymmetric W is APSP_E_INVALID); read them with
+ * apsp_last_status.  Asynchronous on `stream`.  Errors: APSP_E_INVALID,
+ * APSP_E_CUDA. */
+apsp_status apsp_tri_from_dense(apsp_handle *h, int dtype, const void *W, int64_t n, int64_t ldw, void *T,
+                                void *stream);
+
+/* T <- the adjacency matrix of an undirected edge list in the
+ * upper-triangular layout (the conventions of apsp_solve_edges: min over
+ * duplicate edges, 0 on the diagonal, INF elsewhere; checks read by
+ * apsp_last_status).  For APSP_U16 the 16-bit bound is computed from the
+ * edge list first (this synchronizes `stream`) and APSP_E_RANGE is returned
+ * when it fails.  This is the path at sizes where even one dense matrix does
+ * not fit.  Errors: APSP_E_INVALID, APSP_E_RANGE, APSP_E_CUDA. */
+apsp_status apsp_tri_from_edges(apsp_handle *h, int dtype, const int32_t *src, const int32_t *dst, const void *w,
+                                int64_t m, int64_t n, void *T, void *stream);
+
+/* Solves APSP in place on T, which holds an undirected graph's adjacency
+ * matrix in the upper-triangular layout (from apsp_tri_from_dense or
+ * apsp_tri_from_edges): the q rounds of Phase 1 / 2 / 3 (Alg. 3/4) update only
+ * stored super-tiles -- Phase 3 the tiles (I, J) with I <= J, both of its
+ * operands from the round's symmetric panel -- with the warp-specialized
+ * Phase-3 kernel launched once per round; the distances equal apsp_solve_t's
+ * on the dense matrix.  Does not reset the status word: apsp_last_status then
+ * reports the checks of the call that filled T and APSP_E_TIMEOUT if a bounded
+ * device wait gave up.  Asynchronous on `stream`.  Errors: APSP_E_INVALID (T
+ * not 16-byte aligned, bad arguments), APSP_E_NOMEM, APSP_E_CUDA. */
+apsp_status apsp_solve_tri(apsp_handle *h, int dtype, void *T, int64_t n, void *stream);
+
+/* D (dense n x n, device, leading dimension ld) <- the full matrix held in T:
+ * the stored elements, and the lower triangle mirrored from the upper.
+ * Asynchronous on `stream`.  Errors: APSP_E_INVALID, APSP_E_CUDA. */
+apsp_status apsp_tri_to_dense(int dtype, const void *T, int64_t n, void *D, int64_t ld, void *stream);
+
+/* out[i][0..n) <- row rows[i] of the full matrix held in T, for k row indices
+ * (device int64 array, each in [0, n); an index outside is skipped, its output
+ * row left as it was); out is device memory with leading dimension ldo >= n.
+ * The way to read results of a matrix too large to hold densely.
+ * Asynchronous on `stream`.  Errors: APSP_E_INVALID, APSP_E_CUDA. */
+apsp_status apsp_tri_rows(int dtype, const void *T, int64_t n, const int64_t *rows, int64_t k, void *out, int64_t ldo,
+                          void *stream);
+
 /* int32 -> packed u16 (INF32 -> INF16) and back, n x n with separate leading
  * dimensions; the caller guarantees every finite entry is < APSP_INF_U16.
  * (The storage of the packed 16-bit precision; no paper counterpart -- the
@@ -208,8 +277,8 @@ apsp_status apsp_unpack_u16(const uint16_t *src, int64_t lds, int32_t *dst, int6
  * the nearest analogue of grouping requests into one launch). */
 typedef enum {
   APSP_QUEUED = 0,   /* accepted, waiting for memory or a batch slot */
-  APSP_ADMITTED = 1, /* device matrix allocated and W copied; caller may reuse W */
-  APSP_RUNNING = 2,  /* rounds in progress in the persistent batched kernel */
+  APSP_ADMITTED = 1, /* device matrix allocated, the copy of W in flight: W must not change yet */
+  APSP_RUNNING = 2,  /* W copied (the caller may reuse it); rounds in progress on the device */
   APSP_DONE = 3,
   APSP_ERROR = 4
 } apsp_state;
@@ -219,13 +288,18 @@ typedef struct {
   int is_host;     /* 1: W is host memory (copied at admission), 0: device memory */
   int64_t n;
   int64_t ld;
+  int dtype;       /* APSP_I32 (0, the default of a zeroed struct) or APSP_AUTO: the result is int32 either
+                      way; APSP_AUTO solves a request with n >= 1536 in packed 16-bit when the 16-bit
+                      bound holds (the bound synchronizes that request's stream in the serving thread),
+                      smaller requests run in the batched int32 kernel (the same exact result) */
 } apsp_request;
 
 /* Queues a request; non-blocking.  The library copies W into a device matrix
- * it owns when the request is admitted (its n^2 * 4-byte footprint fits the
- * memory budget); the caller may reuse W once apsp_poll reports
- * APSP_ADMITTED or later.  Errors: APSP_E_INVALID, APSP_E_BUSY (queue full),
- * APSP_E_NOMEM (n^2 * 4 bytes exceeds the whole budget). */
+ * it owns when the request is admitted (its n^2 * 4-byte footprint, plus its
+ * share of workspace, fits the memory budget); the caller may reuse W once
+ * apsp_poll reports APSP_RUNNING or later.  Errors: APSP_E_INVALID,
+ * APSP_E_UNSUPPORTED (dtype other than APSP_I32 / APSP_AUTO), APSP_E_BUSY
+ * (queue full), APSP_E_NOMEM (n^2 * 4 bytes exceeds the whole budget). */
 apsp_status apsp_submit(apsp_handle *h, const apsp_request *r, uint64_t *ticket);
 
 /* Non-blocking state query.  On APSP_DONE, *D_dev (if non-NULL) points at the
@@ -271,7 +345,7 @@ apsp_status apsp_tuned_config(apsp_handle *h, int dtype, int64_t n, int *block_k
 #define APSP_NOALLOC_MAX_N 16384
 
 /* An int32 solve (same result as apsp_solve_t with APSP_I32) that allocates
- * no memory at all: no handle, no cudaMalloc, no allocating library call.
+ * no memory of its own: no handle, no cudaMalloc, no allocating library call.
  * The paper has no counterpart; this exists for callers that cannot allocate
  * device memory where they solve -- code that runs inside another
  * framework's memory pool or allocator hooks and must not allocate behind its
@@ -284,12 +358,51 @@ apsp_status apsp_tuned_config(apsp_handle *h, int dtype, int64_t n, int *block_k
  * the library keeps until the process exits.  Every call shares that array:
  * calls that overlap on the GPU (different streams, or different host
  * threads) race on it and give wrong results -- order them on one stream.
- * The first call on each device looks up the array's device address; make
- * that first call before any stream capture.  Inputs are not checked on the
- * device (use apsp_solve for checked solves).
+ * First use on a device: CUDA loads the library's device code and globals
+ * lazily, so the first call on each device (and the first call of a size that
+ * runs a kernel not run before on that device) may load code and create the
+ * array -- memory the driver allocates, possibly with a device
+ * synchronization.  Make one call of each size class you will use (n <= 64,
+ * n <= 128, larger) during set-up, outside the phase that must not allocate
+ * and before any stream capture, or set CUDA_MODULE_LOADING=EAGER before the
+ * process initializes CUDA.  The first call also looks up the array's device
+ * address.  Inputs are not checked on the device (use apsp_solve for checked
+ * solves).  The call returns before the solve has run: a bounded device wait
+ * that gave up (D then incomplete) is reported by apsp_noalloc_status.
  * Errors: APSP_E_INVALID (n < 0, ld < n, null pointer), APSP_E_RANGE (n >
  * APSP_NOALLOC_MAX_N), APSP_E_CUDA (a CUDA call failed). */
 apsp_status apsp_solve_i32_noalloc(const int32_t *W, int64_t n, int64_t ld, int32_t *D, void *stream);
+
+/* Waits for `stream` and reports the device-side outcome of the last
+ * apsp_solve_i32_noalloc on the current device: APSP_OK, or APSP_E_TIMEOUT
+ * when a bounded wait of its Phase-3 kernel gave up (D is then incomplete).
+ * Reads one word of the fixed scratch array into the caller's stack;
+ * allocates nothing.  (Library plumbing; no paper counterpart.)  Errors:
+ * APSP_E_CUDA. */
+apsp_status apsp_noalloc_status(void *stream);
+
+/* ---- the add-min step itself (measurement support) ----------------------- */
+/* The relaxation c = min(c, a + b) is the min-plus step of Table 1 (MatProd
+ * followed by MatMin); Phase 3 is bound by how many of them the SMs issue per
+ * clock.  apsp_addmin_peak measures that rate on `device` for the add-min form
+ * the library uses for `dtype` (APSP_I32: __viaddmin_s32; APSP_U16:
+ * __viaddmin_u16x2, two relaxations per lane-op; APSP_F32: fminf(a + b, c)):
+ * independent chains in registers, one full wave of 4 CTAs x 256 threads per
+ * SM.  *lane_ops_per_clk_per_sm = 32-bit add-min lane-ops per SM clock (by
+ * clock64 of the slowest CTA); *relax_per_s = relaxations per second by event
+ * time (at whatever clock the GPU ran).  Allocates a few KB of device memory
+ * and synchronizes the device.  Errors: APSP_E_INVALID, APSP_E_CUDA. */
+apsp_status apsp_addmin_peak(int device, int dtype, double *lane_ops_per_clk_per_sm, double *relax_per_s);
+
+/* out[i] = the library's add-min of the 32-bit words (a[i], b[i], c[i]) for
+ * `dtype`: APSP_I32 min(a + b, c) as int32; APSP_U16 per 16-bit lane
+ * min(a + b, c) with the add taken modulo 2^16 (the stored values never reach
+ * the wrap: they are <= APSP_INF_U16); APSP_F32 fminf(a + b, c) on the bit
+ * patterns.  Device arrays of m words; asynchronous on `stream`.  Exposes the
+ * primitive so that its lane semantics can be tested.  Errors: APSP_E_INVALID,
+ * APSP_E_CUDA. */
+apsp_status apsp_addmin_eval(int dtype, const uint32_t *a, const uint32_t *b, const uint32_t *c, uint32_t *out,
+                             int64_t m, void *stream);
 
 /* ---- diagnostics (library plumbing; no paper counterpart) ---------------- */
 const char *apsp_strerror(apsp_status s);

@@ -24,7 +24,7 @@ from ._lib import (  # noqa: F401
     get_lib,
     lib_path,
 )
-from .handle import Handle, dtype_code  # noqa: F401
+from .handle import Handle, dtype_code, tri_empty, tri_layout, tri_rows, tri_to_dense  # noqa: F401
 
 
 def __getattr__(name):
@@ -33,5 +33,6 @@ def __getattr__(name):
         return get_lib()
     raise AttributeError(name)
 
-__all__ = ["Handle", "ApspError", "get_lib", "lib_path", "dtype_code", "INF_I32", "INF_U16",
+__all__ = ["Handle", "ApspError", "get_lib", "lib_path", "dtype_code", "tri_layout", "tri_empty", "tri_rows",
+           "tri_to_dense", "INF_I32", "INF_U16",
            "APSP_I32", "APSP_U16", "APSP_F32", "APSP_AUTO", "STATES"]

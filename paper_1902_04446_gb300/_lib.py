@@ -31,7 +31,8 @@ class apsp_config(ctypes.Structure):
 
 
 class apsp_request(ctypes.Structure):
-    _fields_ = [("W", ctypes.c_void_p), ("is_host", ctypes.c_int), ("n", ctypes.c_int64), ("ld", ctypes.c_int64)]
+    _fields_ = [("W", ctypes.c_void_p), ("is_host", ctypes.c_int), ("n", ctypes.c_int64), ("ld", ctypes.c_int64),
+                ("dtype", ctypes.c_int)]
 
 
 def _load():
@@ -69,6 +70,15 @@ def _load():
         "apsp_check_bounded_wait": (st, [H, i64]),
         "apsp_autotune": (st, [H, i32, i64, ctypes.c_char_p]),
         "apsp_solve_i32_noalloc": (st, [vp, i64, i64, vp, vp]),
+        "apsp_noalloc_status": (st, [vp]),
+        "apsp_addmin_peak": (st, [i32, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+        "apsp_addmin_eval": (st, [i32, vp, vp, vp, vp, i64, vp]),
+        "apsp_tri_layout": (st, [i32, i64, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+        "apsp_tri_from_dense": (st, [H, i32, vp, i64, i64, vp, vp]),
+        "apsp_tri_from_edges": (st, [H, i32, vp, vp, vp, i64, i64, vp, vp]),
+        "apsp_solve_tri": (st, [H, i32, vp, i64, vp]),
+        "apsp_tri_to_dense": (st, [i32, vp, i64, vp, i64, vp]),
+        "apsp_tri_rows": (st, [i32, vp, i64, vp, i64, vp, i64, vp]),
         "apsp_tuned_config": (st, [H, i32, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "apsp_profile_read": (st, [H, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double)]),
@@ -96,4 +106,7 @@ ENTRY_POINTS = sorted(["apsp_config_default", "apsp_create", "apsp_destroy", "ap
                        "apsp_unpack_u16", "apsp_submit", "apsp_poll", "apsp_wait", "apsp_fetch", "apsp_release",
                        "apsp_cancel", "apsp_strerror", "apsp_last_error", "apsp_launch_count",
                        "apsp_profile", "apsp_profile_read", "apsp_solve_batch", "apsp_check_bounded_wait",
-                       "apsp_autotune", "apsp_tuned_config", "apsp_solve_i32_noalloc", "apsp_solve_squaring"])
+                       "apsp_autotune", "apsp_tuned_config", "apsp_solve_i32_noalloc", "apsp_noalloc_status",
+                       "apsp_solve_squaring", "apsp_addmin_peak", "apsp_addmin_eval", "apsp_tri_layout",
+                       "apsp_tri_from_dense", "apsp_tri_from_edges", "apsp_solve_tri", "apsp_tri_to_dense",
+                       "apsp_tri_rows"])

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libapsp.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["fw_kernels.cu", "bound.cu", "batch.cu", "apsp_api.cu", "noalloc.cu"]
+SOURCES = ["fw_kernels.cu", "bound.cu", "batch.cu", "apsp_api.cu", "noalloc.cu", "addmin_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", f"-I{INCLUDE}", f"-I{CSRC}"]

@@ -45,6 +45,9 @@ struct Group {
   std::vector<uint64_t> tickets;
   int64_t transient = 0;          // budget bytes returned at completion
   bool finished = false;
+  // set by the serving thread once copy_ev is recorded / every launch is
+  // enqueued (the device work is enqueued outside the serving lock)
+  std::atomic<bool> copy_recorded{false}, enqueued{false};
   ~Group() {
     if (copy_ev) cudaEventDestroy(copy_ev);
     if (done_ev) cudaEventDestroy(done_ev);
@@ -650,6 +653,110 @@ apsp_status apsp_solve_squaring(apsp_handle *h, int dtype, const void *W, int64_
   return APSP_OK;
 }
 
+apsp_status apsp_tri_layout(int dtype, int64_t n, int64_t *rows, int64_t *ld, int64_t *bytes) {
+  if (!valid_dtype(dtype) || n < 0 || (!rows && !ld && !bytes)) return APSP_E_INVALID;
+  int64_t r = 0, l = 0;
+  apsp::tri_shape(n, dtype, &r, &l);
+  if (rows) *rows = r;
+  if (ld) *ld = l;
+  if (bytes) *bytes = r * l * (dtype == APSP_U16 ? 2 : 4);
+  return APSP_OK;
+}
+
+apsp_status apsp_tri_from_dense(apsp_handle *h, int dtype, const void *W, int64_t n, int64_t ldw, void *T,
+                                void *stream) {
+  if (!h) return APSP_E_INVALID;
+  if (!valid_dtype(dtype)) return set_err(h, APSP_E_INVALID, "dtype must be APSP_I32, APSP_U16 or APSP_F32");
+  if (n < 0 || ldw < n || (n > 0 && (!W || !T))) return set_err(h, APSP_E_INVALID, "need n >= 0, ldw >= n, W and T");
+  cudaError_t e = cudaSetDevice(h->cfg.device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> g(h->mu);
+  if ((e = cudaMemsetAsync(h->d_status, 0, sizeof(int), s)) != cudaSuccess) return cuda_fail(h, e, "status reset");
+  int64_t l = 0;
+  e = apsp::launch_tri_fill(dtype, W, ldw, T, n, h->d_status, s, &l);
+  h->launches += l;
+  if (e != cudaSuccess) return cuda_fail(h, e, "tri_from_dense");
+  return APSP_OK;
+}
+
+apsp_status apsp_tri_from_edges(apsp_handle *h, int dtype, const int32_t *src, const int32_t *dst, const void *w,
+                                int64_t m, int64_t n, void *T, void *stream) {
+  if (!h) return APSP_E_INVALID;
+  if (!valid_dtype(dtype)) return set_err(h, APSP_E_INVALID, "dtype must be APSP_I32, APSP_U16 or APSP_F32");
+  if (n < 0 || m < 0 || (n > 0 && !T) || (m > 0 && (!src || !dst || !w)))
+    return set_err(h, APSP_E_INVALID, "bad edge-list arguments");
+  cudaError_t e = cudaSetDevice(h->cfg.device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> g(h->mu);
+  if ((e = cudaMemsetAsync(h->d_status, 0, sizeof(int), s)) != cudaSuccess) return cuda_fail(h, e, "status reset");
+  if (n == 0) return APSP_OK;
+  int64_t l = 0;
+  if (dtype == APSP_U16) {
+    int64_t bound = 0;
+    int ok = 0;
+    e = apsp::bound_from_edges(src, dst, w, 1, m, n, s, &bound, &ok, &l);
+    h->launches += l;
+    l = 0;
+    if (e != cudaSuccess) return cuda_fail(h, e, "16-bit bound");
+    if (!ok) {
+      h->last_error = "16-bit bound fails: 2*eccentricity = " + std::to_string(bound) + " >= 32767";
+      return APSP_E_RANGE;
+    }
+  }
+  e = apsp::launch_tri_from_edges(dtype, src, dst, w, m, T, n, h->d_status, s, &l);
+  h->launches += l;
+  if (e != cudaSuccess) return cuda_fail(h, e, "tri_from_edges");
+  return APSP_OK;
+}
+
+apsp_status apsp_solve_tri(apsp_handle *h, int dtype, void *T, int64_t n, void *stream) {
+  if (!h) return APSP_E_INVALID;
+  if (!valid_dtype(dtype)) return set_err(h, APSP_E_INVALID, "dtype must be APSP_I32, APSP_U16 or APSP_F32");
+  if (n < 0 || (n > 0 && !T)) return set_err(h, APSP_E_INVALID, "need n >= 0 and T");
+  if (n > (int64_t(1) << 31) - 1) return set_err(h, APSP_E_INVALID, "n too large");
+  if (reinterpret_cast<uintptr_t>(T) % 16 != 0) return set_err(h, APSP_E_INVALID, "T must be 16-byte aligned");
+  cudaError_t e = cudaSetDevice(h->cfg.device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> g(h->mu);
+  if (n == 0) return APSP_OK;
+  const int64_t ldT = panel_ld(n);
+  apsp::RoundConfig rc = config_for(h, dtype, n);
+  e = ensure(&h->colT, &h->colT_bytes, apsp::panel_buffer_bytes(n, ldT, false));
+  if (e == cudaSuccess && dtype == APSP_U16) {
+    e = ensure(&h->rowP, &h->rowP_bytes, apsp::row_panel_bytes(ldT, false));
+    rc.rowP = h->rowP;
+  }
+  if (e != cudaSuccess) {
+    h->last_error = std::string("panel workspace: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? APSP_E_NOMEM : APSP_E_CUDA;
+  }
+  int64_t l = 0;
+  e = apsp::launch_rounds_tri(dtype, T, n, h->colT, ldT, s, &l, h->prof.get(), rc, h->d_status);
+  h->launches += l;
+  if (e != cudaSuccess) return cuda_fail(h, e, "rounds (upper-triangular storage)");
+  return APSP_OK;
+}
+
+apsp_status apsp_tri_to_dense(int dtype, const void *T, int64_t n, void *D, int64_t ld, void *stream) {
+  if (!valid_dtype(dtype) || n < 0 || ld < n || (n > 0 && (!T || !D))) return APSP_E_INVALID;
+  return apsp::launch_tri_to_dense(dtype, T, n, D, ld, static_cast<cudaStream_t>(stream), nullptr) == cudaSuccess
+             ? APSP_OK
+             : APSP_E_CUDA;
+}
+
+apsp_status apsp_tri_rows(int dtype, const void *T, int64_t n, const int64_t *rows, int64_t k, void *out, int64_t ldo,
+                          void *stream) {
+  if (!valid_dtype(dtype) || n < 0 || k < 0 || ldo < n || (n > 0 && k > 0 && (!T || !rows || !out)))
+    return APSP_E_INVALID;
+  return apsp::launch_tri_rows(dtype, T, n, rows, k, out, ldo, nullptr, static_cast<cudaStream_t>(stream), nullptr) ==
+                 cudaSuccess
+             ? APSP_OK
+             : APSP_E_CUDA;
+}
+
 apsp_status apsp_pack_u16(const int32_t *src, int64_t lds, uint16_t *dst, int64_t ldd, int64_t n, void *stream) {
   if (n < 0 || lds < n || ldd < n || (n > 0 && (!src || !dst))) return APSP_E_INVALID;
   return apsp::launch_pack(src, lds, dst, ldd, n, static_cast<cudaStream_t>(stream), nullptr) == cudaSuccess
@@ -867,7 +974,7 @@ std::vector<TuneEntry> read_cache(const char *path) {
     e.bk = (int)json_num_field(obj, "bk", 64);
     e.tma = (int)json_num_field(obj, "tma", 1);
     e.ms = json_num_field(obj, "ms", 0);
-    if (!e.gpu.empty() && e.dtype >= 0 && e.n > 0 && (e.bk == 32 || e.bk == 64) && e.tma >= 0 && e.tma <= 2)
+    if (!e.gpu.empty() && e.dtype >= 0 && e.n > 0 && (e.bk == 32 || e.bk == 64) && e.tma >= 0 && e.tma <= 4)
       out.push_back(e);
     p = b + 1;
   }
@@ -1054,6 +1161,16 @@ constexpr int64_t kLargeN = 1536;
 
 int64_t panel_bytes(int64_t n) { return 64 * apsp::batch_panel_ld(n) * 4 + 256; }
 
+// Workspace of a large request's own group beyond panel_bytes: the per-round
+// panel buffer, and for APSP_AUTO the element panel and the packed 16-bit copy.
+int64_t large_extra_bytes(const apsp_request &q) {
+  const int64_t ldT = panel_ld(q.n);
+  int64_t b = (int64_t)apsp::panel_buffer_bytes(q.n, ldT, false);
+  if (q.dtype == APSP_AUTO)
+    b += 256 + (int64_t)apsp::row_panel_bytes(ldT, false) + q.n * round_up(q.n, 8) * 2;
+  return b;
+}
+
 // Marks a finished group's requests DONE or ERROR and frees its transient
 // memory (called with smu held, after done_ev completed).
 void finish_group(apsp_handle *h, const std::shared_ptr<Group> &g) {
@@ -1088,33 +1205,55 @@ void finish_group(apsp_handle *h, const std::shared_ptr<Group> &g) {
 void poll_groups(apsp_handle *h) {
   std::vector<std::shared_ptr<Group>> done;
   for (auto &g : h->groups)
-    if (cudaEventQuery(g->done_ev) == cudaSuccess) done.push_back(g);
+    if (g->enqueued && cudaEventQuery(g->done_ev) == cudaSuccess) done.push_back(g);
   for (auto &g : done) finish_group(h, g);
 }
 
-// Admits `rs` as one group: matrices, input copies, checks, one batched launch.
-apsp_status admit_group(apsp_handle *h, const std::vector<Request *> &rs) {
-  auto g = std::make_shared<Group>();
-  if (!h->free_streams.empty()) {
-    g->stream = h->free_streams.back();
-    h->free_streams.pop_back();
-  } else if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess) {
-    return APSP_E_CUDA;
+// Gives back what a failed admission took -- the requests' matrices and the
+// group's workspace (stream-ordered frees, after the work already queued), the
+// stream, and the requests' share of the budget -- and marks the requests
+// ERROR with `st`.  (smu held.)
+void undo_admission(apsp_handle *h, const std::vector<Request *> &rs, const std::shared_ptr<Group> &g,
+                    apsp_status st) {
+  cudaStream_t s = g->stream;
+  for (Request *r : rs) {
+    if (r->D) cudaFreeAsync(r->D, s);
+    r->D = nullptr;
+    h->used -= r->bytes + r->transient;
+    r->transient = 0;
+    r->group.reset();
+    r->err = st;
+    r->finished = true;
   }
+  if (g->ws) cudaFreeAsync(g->ws, s);
+  if (g->status) cudaFreeAsync(g->status, s);
+  g->ws = nullptr;
+  g->status = nullptr;
+  g->finished = true;
+  if (s) h->free_streams.push_back(s);
+  h->groups.erase(std::remove(h->groups.begin(), h->groups.end(), g), h->groups.end());
+}
+
+// The device work of an admitted group: matrices, input copies, checks, the
+// rounds (one batched launch, or a large request's own rounds).  Runs in the
+// serving thread WITHOUT smu, so that apsp_poll answers (APSP_ADMITTED) while
+// hundreds of launches are enqueued; it touches only the group and its
+// requests' device fields, which other threads read once g->enqueued is set.
+apsp_status admit_group_steps(apsp_handle *h, const std::vector<Request *> &rs, Group *g) {
+  if (!g->stream) return APSP_E_CUDA;
   cudaStream_t s = g->stream;
   std::vector<int32_t *> D;
   std::vector<int64_t> n, ld;
   for (Request *r : rs) {
     const int64_t rn = r->req.n;
-    if (cudaMallocAsync(&r->D, (size_t)std::max<int64_t>(1, rn * rn) * 4, s) != cudaSuccess) return APSP_E_CUDA;
+    if (cudaMallocAsync(&r->D, (size_t)std::max<int64_t>(1, rn * rn) * 4, s) != cudaSuccess) {
+      r->D = nullptr;
+      return APSP_E_CUDA;
+    }
     if (rn > 0 && cudaMemcpy2DAsync(r->D, (size_t)rn * 4, r->req.W, (size_t)r->req.ld * 4, (size_t)rn * 4,
                                     (size_t)rn, r->req.is_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                                     s) != cudaSuccess)
       return APSP_E_CUDA;
-    r->group = g;
-    r->gidx = (int)g->tickets.size();
-    g->tickets.push_back(r->ticket);
-    g->transient += r->transient;
     if (rn > 0) {
       D.push_back(static_cast<int32_t *>(r->D));
       n.push_back(rn);
@@ -1125,10 +1264,13 @@ apsp_status admit_group(apsp_handle *h, const std::vector<Request *> &rs) {
       cudaEventCreateWithFlags(&g->done_ev, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventRecord(g->copy_ev, s) != cudaSuccess)
     return APSP_E_CUDA;
+  g->copy_recorded = true;
   const size_t sbytes = (rs.size() + 1) * sizeof(int);
-  if (cudaMallocAsync((void **)&g->status, sbytes, s) != cudaSuccess ||
-      cudaMemsetAsync(g->status, 0, sbytes, s) != cudaSuccess)
+  if (cudaMallocAsync((void **)&g->status, sbytes, s) != cudaSuccess) {
+    g->status = nullptr;
     return APSP_E_CUDA;
+  }
+  if (cudaMemsetAsync(g->status, 0, sbytes, s) != cudaSuccess) return APSP_E_CUDA;
   int64_t l = 0;
   for (size_t i = 0; i < rs.size(); ++i) {
     const int64_t rn = rs[i]->req.n;
@@ -1140,12 +1282,48 @@ apsp_status admit_group(apsp_handle *h, const std::vector<Request *> &rs) {
     // (symmetric) matrix takes the symmetric mode, decided by a device check
     const int64_t rn = rs[0]->req.n;
     const int64_t ldT = panel_ld(rn);
+    if (rs[0]->req.dtype == APSP_AUTO) {
+      // precision selection: the 16-bit bound (synchronizes the group's
+      // stream), then the rounds in packed 16-bit when it holds
+      int64_t bound = 0;
+      int ok = 0;
+      if (apsp::bound_from_dense(static_cast<const int32_t *>(rs[0]->D), rn, rn,
+                                 std::max<int64_t>(kDefaultMaxEdges, 32 * rn), s, &bound, &ok, &l) != cudaSuccess)
+        return APSP_E_CUDA;
+      if (ok) {
+        apsp::RoundConfig rc = config_for(h, APSP_U16, rn);
+        if (rc.p3 == 4) rc.p3 = 3;
+        rc.sym = true;  // the bound accepts only a symmetric W
+        const int64_t ld16 = round_up(rn, 8);
+        const size_t pb = (apsp::panel_buffer_bytes(rn, ldT, false) + 255) & ~size_t(255);
+        const size_t pbytes = (size_t)rn * ld16 * 2;
+        if (cudaMallocAsync(&g->ws, pb + apsp::row_panel_bytes(ldT, false) + pbytes, s) != cudaSuccess) {
+          g->ws = nullptr;
+          return APSP_E_CUDA;
+        }
+        char *wsb = static_cast<char *>(g->ws);
+        rc.rowP = wsb + pb;
+        uint16_t *P = reinterpret_cast<uint16_t *>(wsb + pb + apsp::row_panel_bytes(ldT, false));
+        int32_t *Dr = static_cast<int32_t *>(rs[0]->D);
+        if (apsp::launch_pack(Dr, rn, P, ld16, rn, s, &l) != cudaSuccess ||
+            apsp::launch_rounds(APSP_U16, P, ld16, rn, g->ws, ldT, s, &l, nullptr, rc, g->status + 1) !=
+                cudaSuccess ||
+            apsp::launch_unpack(P, ld16, Dr, rn, rn, s, &l) != cudaSuccess)
+          return APSP_E_CUDA;
+        h->launches += l;
+        if (cudaEventRecord(g->done_ev, s) != cudaSuccess) return APSP_E_CUDA;
+        g->graphs_dev = nullptr;
+        return APSP_OK;
+      }
+    }
     apsp::RoundConfig rc = config_for(h, APSP_I32, rn);
     // one launch per round here, so that the batched groups on other streams
     // keep running between this request's rounds
     if (rc.p3 == 4) rc.p3 = 3;
-    if (cudaMallocAsync(&g->ws, apsp::panel_buffer_bytes(rn, ldT, false), s) != cudaSuccess)
+    if (cudaMallocAsync(&g->ws, apsp::panel_buffer_bytes(rn, ldT, false), s) != cudaSuccess) {
+      g->ws = nullptr;
       return APSP_E_CUDA;
+    }
     if (h->cfg.symmetric != 2) {
       int flag = 0;
       int *dflag = g->status + 1;  // reused below as the wait-error word (reset first)
@@ -1164,8 +1342,6 @@ apsp_status admit_group(apsp_handle *h, const std::vector<Request *> &rs) {
     h->launches += l;
     if (cudaEventRecord(g->done_ev, s) != cudaSuccess) return APSP_E_CUDA;
     g->graphs_dev = nullptr;
-    rs[0]->admitted = true;
-    h->groups.push_back(g);
     return APSP_OK;
   }
   // only graphs with n > 0 take part; group indices follow the tickets
@@ -1174,7 +1350,10 @@ apsp_status admit_group(apsp_handle *h, const std::vector<Request *> &rs) {
   plan.build(D, n, ld, colT);
   const size_t plan_bytes = plan.workspace_bytes();
   const size_t need = batch_layout(n, nullptr, colT, plan_bytes);
-  if (cudaMallocAsync(&g->ws, need, s) != cudaSuccess) return APSP_E_CUDA;
+  if (cudaMallocAsync(&g->ws, need, s) != cudaSuccess) {
+    g->ws = nullptr;
+    return APSP_E_CUDA;
+  }
   batch_layout(n, static_cast<char *>(g->ws), colT, plan_bytes);
   plan.build(D, n, ld, colT);
   if (!D.empty() &&
@@ -1185,8 +1364,6 @@ apsp_status admit_group(apsp_handle *h, const std::vector<Request *> &rs) {
   if (cudaEventRecord(g->done_ev, s) != cudaSuccess) return APSP_E_CUDA;
   // graphs_dev indexes only n > 0 graphs; map statuses back by skipping n == 0
   if (D.size() != rs.size()) g->graphs_dev = nullptr;
-  for (Request *r : rs) r->admitted = true;
-  h->groups.push_back(g);
   return APSP_OK;
 }
 
@@ -1203,7 +1380,7 @@ void worker_loop(apsp_handle *h) {
         Request *r = h->reqs[h->queue.front()].get();
         const bool large = r->req.n >= kLargeN;
         if (large && !rs.empty()) break;  // a large request starts its own group
-        const int64_t b = r->bytes + panel_bytes(r->req.n) + (large ? (int64_t)apsp::panel_buffer_bytes(r->req.n, panel_ld(r->req.n), false) : 0);
+        const int64_t b = r->bytes + panel_bytes(r->req.n) + (large ? large_extra_bytes(r->req) : 0);
         if (h->used + add + b > h->budget) break;  // wait for memory to free up
         h->queue.pop_front();
         r->transient = b - r->bytes;
@@ -1213,13 +1390,28 @@ void worker_loop(apsp_handle *h) {
       }
       if (!rs.empty()) {
         h->used += add;
-        apsp_status st = admit_group(h, rs);
-        if (st != APSP_OK) {
-          for (Request *r : rs) {
-            r->err = st;
-            r->admitted = r->finished = true;
-          }
+        // admitted: the requests join a group (in flight, not yet enqueued),
+        // then the device work is enqueued without the lock
+        auto grp = std::make_shared<Group>();
+        if (!h->free_streams.empty()) {
+          grp->stream = h->free_streams.back();
+          h->free_streams.pop_back();
+        } else if (cudaStreamCreateWithFlags(&grp->stream, cudaStreamNonBlocking) != cudaSuccess) {
+          grp->stream = nullptr;
         }
+        for (Request *r : rs) {
+          r->group = grp;
+          r->gidx = (int)grp->tickets.size();
+          grp->tickets.push_back(r->ticket);
+          grp->transient += r->transient;
+          r->admitted = true;
+        }
+        h->groups.push_back(grp);
+        g.unlock();
+        const apsp_status st = admit_group_steps(h, rs, grp.get());
+        g.lock();
+        if (st == APSP_OK) grp->enqueued = true;
+        else undo_admission(h, rs, grp, st);
         continue;  // look for more work right away
       }
     }
@@ -1248,6 +1440,8 @@ extern "C" {
 apsp_status apsp_submit(apsp_handle *h, const apsp_request *r, uint64_t *ticket) {
   if (!h || !r || !ticket) return APSP_E_INVALID;
   if (r->n < 0 || r->ld < r->n || (r->n > 0 && !r->W)) return set_err(h, APSP_E_INVALID, "bad request");
+  if (r->dtype != APSP_I32 && r->dtype != APSP_AUTO)
+    return set_err(h, APSP_E_UNSUPPORTED, "requests are APSP_I32 or APSP_AUTO");
   cudaSetDevice(h->cfg.device);
   std::unique_lock<std::mutex> g(h->smu);
   start_worker(h);
@@ -1272,7 +1466,8 @@ apsp_status apsp_poll(apsp_handle *h, uint64_t ticket, apsp_state *st, const voi
   auto it = h->reqs.find(ticket);
   if (it == h->reqs.end()) return APSP_E_NOTFOUND;
   Request *r = it->second.get();
-  if (r->admitted && !r->finished && r->group && cudaEventQuery(r->group->done_ev) == cudaSuccess)
+  if (r->admitted && !r->finished && r->group && r->group->enqueued &&
+      cudaEventQuery(r->group->done_ev) == cudaSuccess)
     finish_group(h, r->group);
   if (r->err != APSP_OK) {
     *st = APSP_ERROR;
@@ -1287,7 +1482,10 @@ apsp_status apsp_poll(apsp_handle *h, uint64_t ticket, apsp_state *st, const voi
     if (D_dev) *D_dev = r->D;
     return APSP_OK;
   }
-  *st = (r->group && cudaEventQuery(r->group->copy_ev) == cudaSuccess) ? APSP_RUNNING : APSP_QUEUED;
+  // admitted: the device work being enqueued or the input copy in flight
+  // (ADMITTED), or the copy done and the rounds running (RUNNING)
+  *st = (r->group && r->group->copy_recorded && cudaEventQuery(r->group->copy_ev) == cudaSuccess) ? APSP_RUNNING
+                                                                                                : APSP_ADMITTED;
   return APSP_OK;
 }
 
@@ -1312,7 +1510,7 @@ apsp_status apsp_fetch(apsp_handle *h, uint64_t ticket, void *dst, int64_t ldd, 
   if (it == h->reqs.end()) return APSP_E_NOTFOUND;
   Request *r = it->second.get();
   if (r->err != APSP_OK) return r->err;
-  if (!r->admitted || !r->group) return APSP_E_NOTREADY;
+  if (!r->admitted || !r->group || !r->group->enqueued) return APSP_E_NOTREADY;
   const int64_t n = r->req.n;
   if (ldd < n) return APSP_E_INVALID;
   if (n == 0) return APSP_OK;
@@ -1331,7 +1529,8 @@ apsp_status apsp_release(apsp_handle *h, uint64_t ticket) {
   if (it == h->reqs.end()) return APSP_E_NOTFOUND;
   Request *r = it->second.get();
   if (r->admitted && !r->finished && r->group) {
-    if (cudaEventQuery(r->group->done_ev) != cudaSuccess) return APSP_E_NOTREADY;  // still running
+    if (!r->group->enqueued || cudaEventQuery(r->group->done_ev) != cudaSuccess)
+      return APSP_E_NOTREADY;  // still being enqueued or running
     finish_group(h, r->group);
   }
   if (!r->admitted) {

@@ -66,6 +66,81 @@ struct OpF32 {
 };
 
 // ---------------------------------------------------------------------------
+// Where element (r, c) of the distance matrix D lives.
+//
+// Dense (the default; an int64_t leading dimension converts to it): row-major,
+// D[r * ld + c].
+//
+// Upper-triangular storage (the paper keeps only the upper triangle of blocks,
+// Sec. 4; the lower blocks are transposes): the matrix is cut into S x S
+// super-tiles, S = 128 * EPW elements (one Phase-3 tile column wide, one or two
+// tile rows tall), T = ceil(n / S) per side, and only the super-tiles (I, J)
+// with I <= J are stored -- the diagonal super-tiles in full.  They are folded
+// into one rectangle of Th * S rows and (2 Th + 1) * S elements per row
+// (Th = ceil(T / 2); about n^2 / 2 elements), so that every stored row is
+// contiguous and the rectangle has one row pitch (one TMA tensor map covers
+// it):
+//   super-row I <  Th: rectangle rows I*S.., columns shifted right by S
+//                      (logical columns [I S, T S) -> [(I+1) S, (T+1) S));
+//   super-row I >= Th: rectangle rows (2 Th - 1 - I)*S.., columns shifted left
+//                      by I S (logical [I S, T S) -> [0, (T - I) S)), in the
+//                      part that the top super-row of that rectangle row
+//                      leaves free.
+// Element (r, c) is stored when c >= S * floor(r / S); rows and columns in
+// [n, T S) are padding.
+struct Layout {
+  int64_t ld;  // dense: leading dimension; upper-triangular: the rectangle's row pitch (elements)
+  int32_t sh;  // upper-triangular: log2(S)
+  int32_t Th;  // upper-triangular: super-rows in the top half (0 = dense)
+  int32_t T;   // upper-triangular: super-tiles per side
+  __host__ __device__ Layout(int64_t ld_ = 0) : ld(ld_), sh(0), Th(0), T(0) {}
+  __host__ __device__ __forceinline__ bool tri() const { return Th != 0; }
+  // rectangle row and column of logical element (r, c) (dense: (r, c) itself)
+  __host__ __device__ __forceinline__ void phys(int64_t r, int64_t c, int64_t &pr, int64_t &pc) const {
+    if (Th == 0) {
+      pr = r;
+      pc = c;
+      return;
+    }
+    const int64_t I = r >> sh;
+    if (I < Th) {
+      pr = r;
+      pc = c + (int64_t(1) << sh);
+    } else {
+      pr = r + ((2 * (int64_t)Th - 1 - 2 * I) << sh);
+      pc = c - (I << sh);
+    }
+  }
+  __host__ __device__ __forceinline__ int64_t off(int64_t r, int64_t c) const {
+    if (Th == 0) return r * ld + c;
+    int64_t pr, pc;
+    phys(r, c, pr, pc);
+    return pr * ld + pc;
+  }
+  // one past the last stored logical column of every row
+  __host__ __device__ __forceinline__ int64_t row_end() const { return Th == 0 ? ld : ((int64_t)T << sh); }
+  // whether logical element (r, c) is stored
+  __host__ __device__ __forceinline__ bool stored(int64_t r, int64_t c) const {
+    return Th == 0 || (c >> sh) >= (r >> sh);
+  }
+};
+
+// The upper-triangular layout of an n x n matrix with `epw` elements per
+// 32-bit word; *rows = the rectangle's rows (its size is rows * L.ld elements).
+inline Layout tri_layout(int64_t n, int epw, int64_t *rows) {
+  const int sh = epw == 2 ? 8 : 7;
+  const int64_t S = int64_t(1) << sh;
+  const int64_t T = ((n > 0 ? n : 1) + S - 1) >> sh;
+  const int64_t Th = (T + 1) / 2;
+  Layout L((2 * Th + 1) * S);
+  L.sh = sh;
+  L.Th = (int32_t)Th;
+  L.T = (int32_t)T;
+  if (rows) *rows = Th * S;
+  return L;
+}
+
+// ---------------------------------------------------------------------------
 // element <-> word helpers
 template <class Op>
 __device__ __forceinline__ uint32_t elem_bits(typename Op::elem e) {
@@ -117,12 +192,12 @@ __device__ __forceinline__ uint4 ld16(const void *p) {
 // unaligned matrix).  Kept out of line: it is rare, and inlining it into every
 // tile loop makes the kernels too large for the instruction cache.
 template <class Op, bool CG>
-__device__ __noinline__ uint4 load_chunk_slow(const typename Op::elem *M, int64_t ld, int64_t ncols, int64_t r,
+__device__ __noinline__ uint4 load_chunk_slow(const typename Op::elem *M, Layout L, int64_t ncols, int64_t r,
                                               int64_t c0, bool vec) {
   constexpr int E = 4 * Op::EPW;
   uint4 v = make_uint4(Op::INF_WORD, Op::INF_WORD, Op::INF_WORD, Op::INF_WORD);
-  const typename Op::elem *p = M + r * ld + c0;
-  if (vec && c0 + E <= ld) {
+  const typename Op::elem *p = M + L.off(r, c0);
+  if (vec && c0 + E <= L.row_end()) {
     v = ld16<CG>(p);
     for (int e = 0; e < E; ++e)
       if (c0 + e >= ncols) chunk_set<Op>(v, e, elem_bits<Op>(Op::inf_elem()));
@@ -137,13 +212,13 @@ __device__ __noinline__ uint4 load_chunk_slow(const typename Op::elem *M, int64_
 }
 
 template <class Op, bool CG = false>
-__device__ __forceinline__ uint4 load_chunk(const typename Op::elem *M, int64_t ld, int64_t nrows, int64_t ncols,
+__device__ __forceinline__ uint4 load_chunk(const typename Op::elem *M, Layout L, int64_t nrows, int64_t ncols,
                                             int64_t r, int64_t c0, bool vec) {
   constexpr int E = 4 * Op::EPW;
   if (r < 0 || r >= nrows || c0 >= ncols)
     return make_uint4(Op::INF_WORD, Op::INF_WORD, Op::INF_WORD, Op::INF_WORD);
-  if (vec && c0 + E <= ncols) return ld16<CG>(M + r * ld + c0);  // the common case: one 16-byte load
-  return load_chunk_slow<Op, CG>(M, ld, ncols, r, c0, vec);
+  if (vec && c0 + E <= ncols) return ld16<CG>(M + L.off(r, c0));  // the common case: one 16-byte load
+  return load_chunk_slow<Op, CG>(M, L, ncols, r, c0, vec);
 }
 
 // Per-element path of store_chunk, out of line for the same reason.
@@ -157,12 +232,12 @@ __device__ __noinline__ void store_chunk_slow(typename Op::elem *p, uint4 v, uin
 // Stores the elements of a 4-word chunk whose mask bit is set (bit e for
 // element e).  A full mask with `vec` is one 16-byte store.
 template <class Op>
-__device__ __forceinline__ void store_chunk(typename Op::elem *M, int64_t ld, int64_t r, int64_t c0, uint4 v,
+__device__ __forceinline__ void store_chunk(typename Op::elem *M, Layout L, int64_t r, int64_t c0, uint4 v,
                                             uint32_t mask, bool vec) {
   constexpr int E = 4 * Op::EPW;
   constexpr uint32_t FULL = (1u << E) - 1u;
   if (mask == 0) return;
-  typename Op::elem *p = M + r * ld + c0;
+  typename Op::elem *p = M + L.off(r, c0);
   if (vec && mask == FULL) *reinterpret_cast<uint4 *>(p) = v;
   else store_chunk_slow<Op>(p, v, mask);
 }
@@ -238,7 +313,7 @@ __device__ __forceinline__ void tile_minplus(const uint32_t *__restrict__ As, co
 // Loads the thread's 8 x 8 word block of the output tile whose top-left
 // element is (row0, col0) from M (INF outside [0,nrows) x [0,ncols)).
 template <class Op, int BM, int BNW, bool CG = false, int TN = 8>
-__device__ __forceinline__ void load_acc(const typename Op::elem *M, int64_t ld, int64_t nrows, int64_t ncols,
+__device__ __forceinline__ void load_acc(const typename Op::elem *M, Layout L, int64_t nrows, int64_t ncols,
                                          int64_t row0, int64_t col0, bool vec, uint32_t (&acc)[8][TN], int ty,
                                          int tx) {
   using Map = TileMap<BM, BNW, TN>;
@@ -246,7 +321,7 @@ __device__ __forceinline__ void load_acc(const typename Op::elem *M, int64_t ld,
   for (int r = 0; r < 8; ++r) {
 #pragma unroll
     for (int h = 0; h < Map::NH; ++h) {
-      const uint4 v = load_chunk<Op, CG>(M, ld, nrows, ncols, row0 + Map::row(ty, r),
+      const uint4 v = load_chunk<Op, CG>(M, L, nrows, ncols, row0 + Map::row(ty, r),
                                          col0 + (int64_t)Map::wcol(tx, h) * Op::EPW, vec);
       acc[r][4 * h + 0] = v.x;
       acc[r][4 * h + 1] = v.y;
@@ -262,12 +337,12 @@ __device__ __forceinline__ void load_acc(const typename Op::elem *M, int64_t ld,
 // Stores an interior tile (every element inside the matrix, none excluded)
 // with unconditional 16-byte stores; needs `vec`.
 template <class Op, int BM, int BNW, int TN = 8>
-__device__ __forceinline__ void store_acc_interior(typename Op::elem *M, int64_t ld, int64_t row0, int64_t col0,
+__device__ __forceinline__ void store_acc_interior(typename Op::elem *M, Layout L, int64_t row0, int64_t col0,
                                                    const uint32_t (&acc)[8][TN], int ty, int tx) {
   using Map = TileMap<BM, BNW, TN>;
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
-    typename Op::elem *rowp = M + (row0 + Map::row(ty, r)) * ld + col0;
+    typename Op::elem *rowp = M + L.off(row0 + Map::row(ty, r), col0);
 #pragma unroll
     for (int h = 0; h < Map::NH; ++h)
       *reinterpret_cast<uint4 *>(rowp + (int64_t)Map::wcol(tx, h) * Op::EPW) =
@@ -276,7 +351,7 @@ __device__ __forceinline__ void store_acc_interior(typename Op::elem *M, int64_t
 }
 
 template <class Op, int BM, int BNW, int TN = 8>
-__device__ __forceinline__ void store_acc(typename Op::elem *M, int64_t ld, int64_t nrows, int64_t ncols,
+__device__ __forceinline__ void store_acc(typename Op::elem *M, Layout L, int64_t nrows, int64_t ncols,
                                           int64_t row0, int64_t col0, int64_t xr0, int64_t xr1, int64_t xc0,
                                           int64_t xc1, bool vec, const uint32_t (&acc)[8][TN], int ty, int tx) {
   using Map = TileMap<BM, BNW, TN>;
@@ -289,7 +364,7 @@ __device__ __forceinline__ void store_acc(typename Op::elem *M, int64_t ld, int6
       const int64_t row = row0 + Map::row(ty, r);
       if (row >= nrows || (row >= xr0 && row < xr1)) continue;
       const uint4 v = make_uint4(acc[r][4 * h + 0], acc[r][4 * h + 1], acc[r][4 * h + 2], acc[r][4 * h + 3]);
-      store_chunk<Op>(M, ld, row, c0, v, cm, vec);
+      store_chunk<Op>(M, L, row, c0, v, cm, vec);
     }
   }
 }
@@ -323,7 +398,7 @@ __device__ __forceinline__ void load_As_colT(uint32_t *As, const uint32_t *__res
 
 // Bs[t][w] = word w of row (r0 + t), element columns c0 .. c0 + BNW*EPW.
 template <class Op, int BNW, int BK, int NT, bool CG = false>
-__device__ __forceinline__ void load_Bs_rows(uint32_t *Bs, const typename Op::elem *__restrict__ M, int64_t ld,
+__device__ __forceinline__ void load_Bs_rows(uint32_t *Bs, const typename Op::elem *__restrict__ M, Layout L,
                                              int64_t nrows, int64_t ncols, int64_t r0, int64_t c0, bool vec,
                                              int tid) {
   constexpr int CH = BK * BNW / 4;
@@ -335,7 +410,7 @@ __device__ __forceinline__ void load_Bs_rows(uint32_t *Bs, const typename Op::el
 #pragma unroll
     for (int k = 0; k < BATCH; ++k) {
       const int c = tid + (k0 + k) * NT;
-      v[k] = load_chunk<Op, CG>(M, ld, nrows, ncols, r0 + c / (BNW / 4), c0 + (int64_t)((c % (BNW / 4)) * 4) * Op::EPW,
+      v[k] = load_chunk<Op, CG>(M, L, nrows, ncols, r0 + c / (BNW / 4), c0 + (int64_t)((c % (BNW / 4)) * 4) * Op::EPW,
                                 vec);
     }
 #pragma unroll
@@ -350,7 +425,7 @@ __device__ __forceinline__ void load_Bs_rows(uint32_t *Bs, const typename Op::el
 // BM x BK block (consecutive threads take consecutive rows, so the scalar
 // shared-memory stores hit consecutive banks).
 template <class Op, int BM, int BK, int NT, bool CG = false>
-__device__ __forceinline__ void load_As_transposed(uint32_t *As, const typename Op::elem *__restrict__ M, int64_t ld,
+__device__ __forceinline__ void load_As_transposed(uint32_t *As, const typename Op::elem *__restrict__ M, Layout L,
                                                    int64_t nrows, int64_t ncols, int64_t i0, int64_t c0, bool vec,
                                                    int tid) {
   constexpr int E = 4 * Op::EPW;
@@ -363,7 +438,7 @@ __device__ __forceinline__ void load_As_transposed(uint32_t *As, const typename 
 #pragma unroll
     for (int k = 0; k < BATCH; ++k) {
       const int c = tid + (k0 + k) * NT;
-      v[k] = load_chunk<Op, CG>(M, ld, nrows, ncols, i0 + c % BM, c0 + (c / BM) * E, vec);
+      v[k] = load_chunk<Op, CG>(M, L, nrows, ncols, i0 + c % BM, c0 + (c / BM) * E, vec);
     }
 #pragma unroll
     for (int k = 0; k < BATCH; ++k) {

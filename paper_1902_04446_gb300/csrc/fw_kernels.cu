@@ -42,10 +42,10 @@ constexpr int P1_THREADS = 256;
 
 // ---------------------------------------------------------------- Phase 1
 template <class Op, int BK>
-__global__ void __launch_bounds__(P1_THREADS) fw_phase1(typename Op::elem *__restrict__ D, int64_t ld, int64_t n,
+__global__ void __launch_bounds__(P1_THREADS) fw_phase1(typename Op::elem *__restrict__ D, Layout L, int64_t n,
                                                         int64_t p0, uint32_t *__restrict__ colT, int64_t ldT) {
   __shared__ P1Smem<Op, BK> s;
-  phase1_body<Op, BK, P1_THREADS, false>(D, ld, n, p0, colT, ldT, s, threadIdx.x);
+  phase1_body<Op, BK, P1_THREADS, false>(D, L, n, p0, colT, ldT, s, threadIdx.x);
 }
 
 // shared-memory loaders: load_As_colT, load_Bs_rows, load_As_transposed (fw_device.cuh)
@@ -76,7 +76,7 @@ struct P2Cfg {
 // mode (see p2_row_task / p2_col_task).
 template <class Op, int BK>
 __global__ void __launch_bounds__(P2Cfg<Op, BK>::THREADS)
-    fw_phase2(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0, int64_t p1,
+    fw_phase2(typename Op::elem *__restrict__ D, Layout L, int64_t n, int64_t p0, int64_t p1,
               uint32_t *__restrict__ colT, int64_t ldT, int nrow_ctas, int vec, int row_chunk0, int sym,
               SymPanel<Op> sp) {
   using C = P2Cfg<Op, BK>;
@@ -84,10 +84,10 @@ __global__ void __launch_bounds__(P2Cfg<Op, BK>::THREADS)
   const SymPanel<Op> *spp = sym ? &sp : nullptr;
   if ((int)blockIdx.x < nrow_ctas)
     p2_row_task<Op, BK, C::ROW_BNW, C::THREADS, false, C::TN>(
-        D, ld, n, p0, p1, colT, ldT, (int64_t)(row_chunk0 + (int)blockIdx.x) * C::ROW_BNW * Op::EPW, vec, smem,
+        D, L, n, p0, p1, colT, ldT, (int64_t)(row_chunk0 + (int)blockIdx.x) * C::ROW_BNW * Op::EPW, vec, smem,
         threadIdx.x, spp);
   else
-    p2_col_task<Op, BK, C::COL_BM, C::THREADS, false, C::TN>(D, ld, n, p0, p1, colT, ldT,
+    p2_col_task<Op, BK, C::COL_BM, C::THREADS, false, C::TN>(D, L, n, p0, p1, colT, ldT,
                                                              (int64_t)(blockIdx.x - nrow_ctas) * C::COL_BM, vec,
                                                              smem, threadIdx.x, spp);
 }
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(P2Cfg<Op, BK>::THREADS)
 // tile band x >= band_start (the only ones that Phase-3 tiles read).
 // Coalesced: one block row per panel row t.
 template <class Op>
-__global__ void panel_finalize(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
+__global__ void panel_finalize(typename Op::elem *__restrict__ D, Layout L, int64_t n, int64_t p0,
                                const uint32_t *__restrict__ colT, int64_t ldT, typename Op::elem *__restrict__ rowP,
                                int64_t band_start) {
   const int t = blockIdx.y;
@@ -109,17 +109,17 @@ __global__ void panel_finalize(typename Op::elem *__restrict__ D, int64_t ld, in
     const uint32_t w = colT[(int64_t)t * ldT + x];
     const typename Op::elem e = bits_elem<Op>(Op::EPW == 2 ? (w & 0xFFFFu) : w);
     if (rowP) rowP[(int64_t)t * ldT + x] = e;
-    if (x >= band_start && row < n) D[row * ld + x] = e;
+    if (x >= band_start && row < n) D[L.off(row, x)] = e;
   }
 }
 
 // Phase 1 kernel with the optional element panel (symmetric mode).
 template <class Op, int BK>
-__global__ void __launch_bounds__(P1_THREADS) fw_phase1_sym(typename Op::elem *__restrict__ D, int64_t ld, int64_t n,
+__global__ void __launch_bounds__(P1_THREADS) fw_phase1_sym(typename Op::elem *__restrict__ D, Layout L, int64_t n,
                                                             int64_t p0, uint32_t *__restrict__ colT, int64_t ldT,
                                                             typename Op::elem *rowP) {
   __shared__ P1Smem<Op, BK> s;
-  phase1_body<Op, BK, P1_THREADS, false>(D, ld, n, p0, colT, ldT, s, threadIdx.x, rowP);
+  phase1_body<Op, BK, P1_THREADS, false>(D, L, n, p0, colT, ldT, s, threadIdx.x, rowP);
 }
 
 // ---------------------------------------------------------------- symmetry
@@ -351,21 +351,32 @@ __global__ void __launch_bounds__(TileMap<128, 128, TN>::THREADS, 1)
 // that moves all data with TMA.  The consumers never wait on each other:
 // full/empty mbarriers hand the two A/B stages back and forth, and the
 // accumulators start at INF, so C is needed only at the end of the tile:
-//   RED (int32): the consumers write acc into the C buffer and the producer
-//     applies it with a TMA min-reduction, D = min(D, acc), carried out in L2.
-//     C is never loaded.  Every tile is reduced, the panel rows and columns
-//     included: there the update reproduces the current values exactly (after
-//     Phase 2 the row panel R' = min(R, D_kk (x) R) with D_kk closed, so
-//     D_kk (x) R' >= R'; likewise for the column panel and D_kk itself), so
-//     other CTAs may read the row panel while it is rewritten.
-//   !RED (packed 16-bit, fp32): the producer loads C by TMA during the tile;
-//     the consumers merge it (min) at the end; interior tiles go back through
+//   RED (int32 and fp32): the consumers write acc into the C buffer and the
+//     producer applies it with a TMA min-reduction, D = min(D, acc), carried
+//     out in L2.  C is never loaded.  fp32 distances are non-negative floats
+//     (ingest rejects negatives and NaN and stores -0.0 as +0.0) or +inf,
+//     whose bit patterns order like the values under a signed int32 compare,
+//     so fp32 tiles reduce through an int32 tensor map over the same bytes.
+//     Every tile is reduced, the panel rows and columns included: there the
+//     int32 update reproduces the current values exactly (after Phase 2 the
+//     row panel R' = min(R, D_kk (x) R) with D_kk closed, so D_kk (x) R' >= R';
+//     likewise for the column panel and D_kk itself), so other CTAs may read
+//     the row panel while it is rewritten.  In fp32 a rounded sum may come out
+//     one unit in the last place lower there: still the rounded length of a
+//     real path, so readers see either value and the result stays within
+//     the rounding tolerance.
+//   !RED (packed 16-bit; no 16-bit-lane min reduction exists for TMA): the
+//     producer loads C by TMA during the tile; the consumers merge it (min)
+//     at the end; interior tiles go back through
 //     the C buffer and a TMA store, edge tiles (panel rows or columns, ragged
 //     edge) by masked stores that leave the panels untouched.
 // Symmetric mode and the tile order are as in fw_phase3_tma.  Every wait is
 // bounded; a CTA that gives up waits (bounded) for its copies in flight and
 // ORs 4 into *err.
 constexpr int P3W_THREADS = 9 * 32;
+// Element types whose Phase-3 tiles leave by the int32 TMA min-reduction.
+template <class Op>
+constexpr bool kRedOp = Op::DTYPE != 1;
 
 // int32 results leave by a TMA min-reduction over a tensor map that ends at
 // n4 = n rounded down to 4 elements (16 bytes): at the tensor's x edge the
@@ -402,7 +413,7 @@ __device__ __forceinline__ void red_tail_store(int32_t *D, int64_t ld, int64_t n
 template <class Op, int BK, bool RED>
 __global__ void __launch_bounds__(P3W_THREADS, 1)
     fw_phase3_ws(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                 const __grid_constant__ CUtensorMap mapC, typename Op::elem *__restrict__ D, int64_t ld, int64_t n,
+                 const __grid_constant__ CUtensorMap mapC, typename Op::elem *__restrict__ D, Layout L, int64_t n,
                  int64_t p0, int64_t p1, int tiles_x, int tiles_total, int *err, int sym, int tiles_y) {
   constexpr int BM = 128, BNW = 128, TN = 8;
   using Map = TileMap<BM, BNW, TN>;
@@ -463,6 +474,16 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
     return r0 + BM <= n && c0 + BNW * Op::EPW <= n && (r0 + BM <= p0 || r0 >= p1) &&
            (c0 + BNW * Op::EPW <= p0 || c0 >= p1);
   };
+  // TMA coordinates of tile (ty, tx) in the storage of D (the rectangle of the
+  // upper-triangular layout, or D itself); the reduction map of a dense D ends
+  // at red_cols(n), that of the upper-triangular rectangle covers its padding
+  auto cxy = [&](int ty_, int tx_, int &x, int &y) {
+    int64_t pr, pc;
+    L.phys((int64_t)ty_ * BM, (int64_t)tx_ * BNW * Op::EPW, pr, pc);
+    x = (int)pc;
+    y = (int)pr;
+  };
+  const int64_t ncr = L.tri() ? INT64_MAX : red_cols(n);
 
   if (warp == NCW) {
     // ------------------------------------------------------------ producer
@@ -477,8 +498,10 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
         else ++n_ab[1];
       };
       auto issue_c = [&](int ty_, int tx_) {
+        int x, y;
+        cxy(ty_, tx_, x, y);
         mbar_arrive_expect_tx(&full_c, P3T_C_BYTES);
-        tma_load_2d(Cs, &mapC, &full_c, tx_ * BNW * Op::EPW, ty_ * BM);
+        tma_load_2d(Cs, &mapC, &full_c, x, y);
         ++n_c;
       };
       int aty = ty0, atx = tx0;  // next A/B tile to load
@@ -505,15 +528,17 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
           break;
         }
         const int r0 = cty * BM, c0 = ctx * BNW * Op::EPW;
+        int cx, cy;
+        cxy(cty, ctx, cx, cy);
         if (RED) {
-          if (c0 < red_cols(n)) {  // mapC ends at red_cols(n) in this mode
-            tma_reduce_min_2d(&mapC, Cs, c0, r0);
+          if (c0 < ncr) {  // a dense D's mapC ends at red_cols(n) in this mode
+            tma_reduce_min_2d(&mapC, Cs, cx, cy);
             bulk_commit();
             bulk_wait_read_all();
           }
           mbar_arrive(&cfree);
         } else if (interior_of(r0, c0)) {
-          tma_store_2d(&mapC, Cs, c0, r0);
+          tma_store_2d(&mapC, Cs, cx, cy);
           bulk_commit();
           bulk_wait_read_all();
         }
@@ -562,9 +587,9 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
             *reinterpret_cast<uint4 *>(Cs + Map::row(ty, r) * BNW + Map::wcol(tx, h)) =
                 make_uint4(acc[r][4 * h], acc[r][4 * h + 1], acc[r][4 * h + 2], acc[r][4 * h + 3]);
         fence_proxy_async_smem();
-        if constexpr (Op::DTYPE == 0)
-          if (c0 + BNW > red_cols(n) && c0 < n)
-            red_tail_store<BM, BNW, TN>(reinterpret_cast<int32_t *>(D), ld, n, n, r0, c0, acc, ty, tx);
+        if constexpr (Op::DTYPE != 1)
+          if (!L.tri() && c0 + BNW > red_cols(n) && c0 < n)
+            red_tail_store<BM, BNW, TN>(reinterpret_cast<int32_t *>(D), L.ld, n, n, r0, c0, acc, ty, tx);
       } else {
         bad = !mbar_wait_bounded(&full_c, (uint32_t)i & 1u, P3T_WAIT_LIMIT);
         if (__any_sync(0xffffffffu, bad)) {
@@ -586,7 +611,7 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
               *cp = make_uint4(acc[r][4 * h], acc[r][4 * h + 1], acc[r][4 * h + 2], acc[r][4 * h + 3]);
           }
         if (interior) fence_proxy_async_smem();
-        else store_acc<Op, BM, BNW, TN>(D, ld, n, n, r0, c0, p0, p1, p0, p1, true, acc, ty, tx);
+        else store_acc<Op, BM, BNW, TN>(D, L, n, n, r0, c0, p0, p1, p0, p1, true, acc, ty, tx);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&cdone);
@@ -739,20 +764,24 @@ __device__ __noinline__ void la_task_fin(typename Op::elem *D, int64_t ld, int64
 // padded to a common size (padding items are skipped).  Each item waits only for items
 // with smaller ids:
 //   tile of round k        <- every task of round k done (P1, P2 chunks,
-//                             publication); packed 16-bit / fp32 also the same
-//                             tile of round k-1 written (its C is loaded, merged
-//                             and stored, which must not overlap)
+//                             publication); packed 16-bit also the same tile
+//                             of round k-1 written (its C is loaded, merged and
+//                             stored, which must not overlap)
 //   P1 of round j          <- round j-1's priority tiles written, and every
 //                             tile of round j-2 written (those read the panel
 //                             buffer that round j overwrites, and carry the last
 //                             contributions the diagonal block needs)
 //   P2 chunks of round j   <- P1 of round j
 //   publication, round j   <- every P2 chunk of round j
-// int32 tiles of rounds k and k+1 may overlap on the same tile: both are TMA
-// min-reductions, which commute; and a tile of round k may read a row-panel
-// value that round k+1 has already lowered.  Every value is always a real path
-// length no larger than the one the sequential order would hold at that point,
-// so the result is the same exact matrix.
+// int32 and fp32 tiles of rounds k and k+1 may overlap on the same tile: both
+// are TMA min-reductions, which commute; and a tile of round k may read a
+// row-panel value that round k+1 has already lowered.  Every value is always a
+// real path length no larger than the one the sequential order would hold at
+// that point, so the int32 result is the same exact matrix.  In fp32 every
+// value is the rounded length of a real path and, rounding being monotone, no
+// larger than the sequential order's; the result is within the rounding
+// tolerance of the exact one, and may differ from another run's in the last
+// bit of an entry.
 template <class Op>
 struct SolvePlan {
   int64_t n, ld, ldT;
@@ -763,7 +792,7 @@ struct SolvePlan {
   unsigned long long *items;  // work items taken (64-bit: blocks x block size can pass 2^31)
   int *cnt;          // 6 per round r: [0] priority tiles for round r, [1] P1(r), [2] P2(r), [3] all tasks of r,
                      // [4] tiles of round r written
-  int *tile_round;   // packed 16-bit / fp32: rounds written per tile
+  int *tile_round;   // packed 16-bit: rounds written per tile
 };
 
 // The plan of each mode ([0] general, [1] symmetric) and, when the host left
@@ -1233,7 +1262,7 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
                 *reinterpret_cast<uint4 *>(Cs + Map::row(ty, r) * BNW + Map::wcol(tx, h)) =
                     make_uint4(acc[r][4 * h], acc[r][4 * h + 1], acc[r][4 * h + 2], acc[r][4 * h + 3]);
             fence_proxy_async_smem();
-            if constexpr (Op::DTYPE == 0)
+            if constexpr (Op::DTYPE != 1)
               if (c0 + BNW > red_cols(n) && c0 < n)
                 red_tail_store<BM, BNW, TN>(reinterpret_cast<int32_t *>(D), ld, n, n, r0, c0, acc, ty, tx);
           }
@@ -1565,16 +1594,24 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
 // ---------------------------------------------------------------- ingest / checks
 // Copies W to D (when they differ) and checks the input: diagonal 0, weights
 // >= 0, finite weights < INF.  status |= 1 (invalid) or 2 (range).
+// fp32: a -0.0 is written as +0.0 (also in place), so that every stored
+// distance is a non-negative float whose bit pattern orders like the value
+// under a signed int32 compare -- the Phase-3 tiles leave by an int32 TMA
+// min-reduction on those bits.
 template <class Op>
 __global__ void ingest_kernel(const typename Op::elem *__restrict__ W, typename Op::elem *__restrict__ D, int64_t n,
                               int64_t ld, int copy, int *status) {
   int bad = 0;
   for (int64_t i = blockIdx.y; i < n; i += gridDim.y) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-      const typename Op::elem e = W[i * ld + j];
+      typename Op::elem e = W[i * ld + j];
       if constexpr (Op::DTYPE == 2) {
         if (!(e >= 0.0f)) bad |= 1;              // negative or NaN
         if (i == j && e != 0.0f) bad |= 1;
+        if (__float_as_uint(e) == 0x80000000u) {  // -0.0
+          e = 0.0f;
+          if (!copy) D[i * ld + j] = e;
+        }
       } else if constexpr (Op::DTYPE == 1) {
         if (e > Op::inf_elem()) bad |= 2;
         if (i == j && e != 0) bad |= 1;
@@ -1636,10 +1673,11 @@ __global__ void scatter_edges_kernel(const int32_t *__restrict__ src, const int3
   int bad = 0;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t u = src[e], v = dst[e];
-    const typename Op::elem x = w[e];
+    typename Op::elem x = w[e];
     if (u < 0 || u >= n || v < 0 || v >= n) { bad |= 1; continue; }
     if constexpr (Op::DTYPE == 2) {
       if (!(x >= 0.0f)) { bad |= 1; continue; }
+      if (x == 0.0f) x = 0.0f;  // -0.0 -> +0.0 (the stored bits order like the values)
     } else if constexpr (Op::DTYPE == 0) {
       if (x < 0) { bad |= 1; continue; }
     }
@@ -1683,6 +1721,112 @@ __global__ void synth_kernel(typename Op::elem *__restrict__ D, int64_t n, int64
       else if (h < thresh) v = (typename Op::elem)(1 + mix32(h) % (Op::DTYPE == 1 ? 16u : 1000u));
       D[i * ld + j] = v;
     }
+}
+
+// ---------------------------------------------------------------- upper-triangular storage
+// Every stored element (r, c) of the layout (rows [0, T S), columns
+// [S floor(r / S), T S)): from the dense W when r, c < n (W == nullptr: 0 on
+// the diagonal, INF elsewhere), INF in the padding.  With W, the input is
+// checked as in ingest_kernel (status |= 1 invalid, 2 range); fp32 -0.0 is
+// stored as +0.0.
+template <class Op>
+__global__ void tri_fill_kernel(const typename Op::elem *__restrict__ W, int64_t ldw, typename Op::elem *__restrict__ D,
+                                Layout L, int64_t n, int *status) {
+  using E = typename Op::elem;
+  const int64_t rows = (int64_t)L.T << L.sh;
+  int bad = 0;
+  for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
+    const int64_t c_first = (r >> L.sh) << L.sh;
+    const int64_t o = L.off(r, c_first) - c_first;  // D[o + c] is element (r, c) for stored c
+    for (int64_t c = c_first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < rows;
+         c += (int64_t)gridDim.x * blockDim.x) {
+      E e = Op::inf_elem();
+      if (r < n && c < n) {
+        if (!W) {
+          e = r == c ? (E)0 : Op::inf_elem();
+        } else {
+          e = W[r * ldw + c];
+          if constexpr (Op::DTYPE == 2) {
+            if (!(e >= 0.0f)) bad |= 1;
+            if (r == c && e != 0.0f) bad |= 1;
+            if (e == 0.0f) e = 0.0f;
+          } else if constexpr (Op::DTYPE == 1) {
+            if (e > Op::inf_elem()) bad |= 2;
+            if (r == c && e != 0) bad |= 1;
+          } else {
+            if (e < 0) bad |= 1;
+            if (e > Op::inf_elem()) bad |= 2;
+            if (r == c && e != 0) bad |= 1;
+          }
+        }
+      }
+      D[o + c] = e;
+    }
+  }
+  if (bad && status) atomicOr(status, bad);
+}
+
+// Scatters an undirected edge list into the layout: min over duplicates into
+// (u, v) and (v, u), whichever of them is stored; checks as scatter_edges_kernel.
+template <class Op>
+__global__ void tri_scatter_edges_kernel(const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+                                         const typename Op::elem *__restrict__ w, int64_t m, typename Op::elem *D,
+                                         Layout L, int64_t n, int *status) {
+  int bad = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t u = src[e], v = dst[e];
+    typename Op::elem x = w[e];
+    if (u < 0 || u >= n || v < 0 || v >= n) { bad |= 1; continue; }
+    if constexpr (Op::DTYPE == 2) {
+      if (!(x >= 0.0f)) { bad |= 1; continue; }
+      if (x == 0.0f) x = 0.0f;
+    } else if constexpr (Op::DTYPE == 0) {
+      if (x < 0) { bad |= 1; continue; }
+    }
+    if (x >= Op::inf_elem()) { if (!(Op::DTYPE == 2 && x == Op::inf_elem())) bad |= 2; continue; }
+    if (u == v) continue;
+    for (int k = 0; k < 2; ++k) {
+      const int64_t a = k ? v : u, b = k ? u : v;
+      if (!L.stored(a, b)) continue;
+      typename Op::elem *p = D + L.off(a, b);
+      if constexpr (Op::DTYPE == 1) atomic_min_u16(p, x);
+      else if constexpr (Op::DTYPE == 2) atomicMin(reinterpret_cast<int *>(p), __float_as_int(x));
+      else atomicMin(reinterpret_cast<int *>(p), (int)x);
+    }
+  }
+  if (bad) atomicOr(status, bad);
+}
+
+// Dense out[r][c] for the stored elements with r, c < n (the lower triangle
+// outside the diagonal super-tiles is filled afterwards by mirror_kernel).
+template <class Op>
+__global__ void tri_to_dense_kernel(const typename Op::elem *__restrict__ D, Layout L, int64_t n,
+                                    typename Op::elem *__restrict__ out, int64_t ldo) {
+  for (int64_t r = blockIdx.y; r < n; r += gridDim.y) {
+    const int64_t c_first = (r >> L.sh) << L.sh;
+    const int64_t o = L.off(r, c_first) - c_first;  // D[o + c] is element (r, c) for stored c
+    for (int64_t c = c_first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x)
+      out[r * ldo + c] = D[o + c];
+  }
+}
+
+// out[i][c] = D(rows[i], c) for c < n: the stored element, or its mirror
+// (c, rows[i]) below the diagonal super-tiles.  A row index outside [0, n)
+// sets status |= 1 and its output row is left untouched.
+template <class Op>
+__global__ void tri_rows_kernel(const typename Op::elem *__restrict__ D, Layout L, int64_t n,
+                                const int64_t *__restrict__ rows, int64_t k, typename Op::elem *__restrict__ out,
+                                int64_t ldo, int *status) {
+  for (int64_t i = blockIdx.y; i < k; i += gridDim.y) {
+    const int64_t r = rows[i];
+    if (r < 0 || r >= n) {
+      if (threadIdx.x == 0 && blockIdx.x == 0 && status) atomicOr(status, 1);
+      continue;
+    }
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
+      out[i * ldo + c] = L.stored(r, c) ? D[L.off(r, c)] : D[L.off(c, r)];
+  }
 }
 
 // ---------------------------------------------------------------- host launchers
@@ -1743,20 +1887,25 @@ static inline unsigned grid_cols(int64_t n, int threads) {
 }
 
 template <class Op, int BK>
-static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int64_t ldT, bool vec, int variant,
+static cudaError_t rounds_impl(void *Dv, Layout L, int64_t n, void *colTv, int64_t ldT, bool vec, int variant,
                                cudaStream_t s, int64_t *launches, PhaseTimer *tm, int *wait_err, bool sym,
                                void *rowPv, const int *sym_flag, const int *gate, uint32_t dep_spins) {
   const bool use_tma = variant != 0;
   using Elem = typename Op::elem;
   using E = Elem;
   E *D = static_cast<E *>(Dv);
+  const int64_t ld = L.ld;
+  const bool tri = L.tri();
   const int64_t q = (n + BK - 1) / BK;
   // lookahead rounds (the warp-specialized Phase 3 with the TMA path and more
   // than one round): two panel buffers used by round parity, then 4 counters
   // per round
   // kernel 4 (every round in one launch) when its conditions hold, else 3
-  bool la_on = kLookaheadWidth<BK> && use_tma && vec && variant == 4 && q > 1;
+  bool la_on = kLookaheadWidth<BK> && use_tma && vec && variant == 4 && q > 1 && !tri;
   if (variant == 4) variant = 3;
+  // upper-triangular storage: symmetric mode on the warp-specialized Phase 3,
+  // one launch per round
+  if (tri && (!sym || !vec || variant != 3)) return cudaErrorNotSupported;
   // the device picks the symmetric mode (single launch only; otherwise the
   // general path, which is exact for any input)
   const bool dev_sym = la_on && !sym && sym_flag != nullptr;
@@ -1802,10 +1951,15 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
     for (int b = 0; b < 2 && dev_sym && tma; ++b)
       tma = make_map(&mBs[b], dt, symB_any(b), (uint64_t)ldT, (uint64_t)BK, (uint64_t)ldT * sizeof(E), 128 * Op::EPW,
                      BK);
-    // int32 (TMA min-reduction epilogue of variant 3): x extent red_cols(n)
-    const uint64_t cx = (Op::DTYPE == 0 && variant == 3) ? (uint64_t)(n & ~(int64_t)3) : (uint64_t)n;
+    // int32 and fp32 (TMA min-reduction epilogue of variant 3): x extent
+    // red_cols(n), and an int32 map (fp32 bits of non-negative values order
+    // like int32); upper-triangular storage: the whole rectangle
+    const bool red_map = kRedOp<Op> && variant == 3;
+    const uint64_t cx = tri ? (uint64_t)ld : red_map ? (uint64_t)(n & ~(int64_t)3) : (uint64_t)n;
+    const uint64_t cy = tri ? ((uint64_t)L.Th << L.sh) : (uint64_t)n;
     tma = tma && cx > 0 &&
-          make_map(&mC, dt, D, cx, (uint64_t)n, (uint64_t)ld * sizeof(E), 128 * Op::EPW, 128);
+          make_map(&mC, red_map ? CU_TENSOR_MAP_DATA_TYPE_INT32 : dt, D, cx, cy, (uint64_t)ld * sizeof(E),
+                   128 * Op::EPW, 128);
     err = tma ? (wait_err ? wait_err : error_word()) : nullptr;
     tma = tma && err != nullptr;
     if (tma) {
@@ -1814,7 +1968,7 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
         e = cudaFuncSetAttribute(fw_phase3_tma<Op, BK, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  P3T<BK>::SMEM);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fw_phase3_ws<Op, BK, Op::DTYPE == 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(fw_phase3_ws<Op, BK, kRedOp<Op>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  P3T<BK>::SMEM);
       if (e != cudaSuccess) return e;
     }
@@ -1846,9 +2000,9 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
     const double w = (double)(p1 - p0), rest = (double)(n - (p1 - p0));
     if (tm) tm->before(0, s);
     if (sym && rP)
-      fw_phase1_sym<Op, BK><<<1, P1_THREADS, 0, s>>>(D, ld, n, p0, cT, ldT, rP);
+      fw_phase1_sym<Op, BK><<<1, P1_THREADS, 0, s>>>(D, L, n, p0, cT, ldT, rP);
     else
-      fw_phase1<Op, BK><<<1, P1_THREADS, 0, s>>>(D, ld, n, p0, cT, ldT);
+      fw_phase1<Op, BK><<<1, P1_THREADS, 0, s>>>(D, L, n, p0, cT, ldT);
     if (launches) *launches += 1;
     if (tm) tm->after(0, s, w * w * w);
     if (q == 1) return;
@@ -1861,7 +2015,7 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
       c_count = (int)((p0 + C2::COL_BM - 1) / C2::COL_BM);
     }
     if (r_count + c_count > 0) {
-      fw_phase2<Op, BK><<<r_count + c_count, C2::THREADS, C2::SMEM, s>>>(D, ld, n, p0, p1, cT, ldT, r_count,
+      fw_phase2<Op, BK><<<r_count + c_count, C2::THREADS, C2::SMEM, s>>>(D, L, n, p0, p1, cT, ldT, r_count,
                                                                         vec ? 1 : 0, r_first, sym ? 1 : 0, sp);
       if (launches) *launches += 1;
     }
@@ -1870,7 +2024,7 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
       const int64_t xs = rP ? p0 : p0 - band_start;  // elements to visit per row
       const unsigned gx = (unsigned)std::min<int64_t>((xs + 255) / 256, 64);
       if (xs > 0) {
-        panel_finalize<Op><<<dim3(gx, BK), 256, 0, s>>>(D, ld, n, p0, cT, ldT, rP, band_start);
+        panel_finalize<Op><<<dim3(gx, BK), 256, 0, s>>>(D, L, n, p0, cT, ldT, rP, band_start);
         if (launches) *launches += 1;
       }
     }
@@ -1892,8 +2046,8 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
       if (q == 1) break;
       if (tm) tm->before(2, s);
       if (tma && variant == 3)
-        fw_phase3_ws<Op, BK, Op::DTYPE == 0><<<grid_tma, P3W_THREADS, P3T<BK>::SMEM, s>>>(
-            mA[0], mB[0], mC, D, ld, n, p0, p1, tiles_x, tiles_total, err, sym ? 1 : 0, tiles_y);
+        fw_phase3_ws<Op, BK, kRedOp<Op>><<<grid_tma, P3W_THREADS, P3T<BK>::SMEM, s>>>(
+            mA[0], mB[0], mC, D, L, n, p0, p1, tiles_x, tiles_total, err, sym ? 1 : 0, tiles_y);
       else if (tma && variant == 2)
         fw_phase3_tma<Op, BK, 4><<<grid_tma, TileMap<128, 128, 4>::THREADS, P3T<BK>::SMEM, s>>>(
             mA[0], mB[0], mC, D, ld, n, p0, p1, tiles_x, tiles_total, err, sym ? 1 : 0, tiles_y);
@@ -1907,7 +2061,7 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
     }
   } else if constexpr (kLookaheadWidth<BK>) {
     // every round in one persistent launch (fw_solve_ws)
-    constexpr bool RED = Op::DTYPE == 0;
+    constexpr bool RED = kRedOp<Op>;
     int tiles_sym = 0;  // tiles with tx >= ty / EPW
     for (int y = 0; y < tiles_y; ++y) tiles_sym += tiles_x - std::min(tiles_x, y / Op::EPW);
     const int grid = std::min(sm_count(), tiles_sym);  // one launch grid for either mode
@@ -1970,7 +2124,7 @@ static cudaError_t rounds_impl(void *Dv, int64_t ld, int64_t n, void *colTv, int
       else tm->after(2, s, work[sym ? 1 : 0]);
     }
   }
-  if ((sym || dev_sym) && q > 1) {  // the lower triangle from the upper
+  if ((sym || dev_sym) && q > 1 && !tri) {  // the lower triangle from the upper (not stored when tri)
     const dim3 gm((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
     mirror_kernel<Op><<<gm, dim3(32, 8), 0, s>>>(D, n, ld, dev_sym ? sym_flag : nullptr);
     if (launches) *launches += 1;
@@ -1983,14 +2137,14 @@ static bool aligned16(const void *p, int64_t ld, size_t esz) {
 }
 
 template <class Op>
-static cudaError_t rounds_bk(const RoundConfig &cfg, void *D, int64_t ld, int64_t n, void *colT, int64_t ldT,
+static cudaError_t rounds_bk(const RoundConfig &cfg, void *D, Layout L, int64_t n, void *colT, int64_t ldT,
                              cudaStream_t s, int64_t *launches, PhaseTimer *tm, int *wait_err) {
-  const bool vec = aligned16(D, ld, sizeof(typename Op::elem));
+  const bool vec = aligned16(D, L.ld, sizeof(typename Op::elem));
   if (cfg.bk == 32)
-    return rounds_impl<Op, 32>(D, ld, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err, cfg.sym, cfg.rowP,
+    return rounds_impl<Op, 32>(D, L, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err, cfg.sym, cfg.rowP,
                                cfg.sym_flag, cfg.gate, cfg.dep_spins);
   if (cfg.bk == 64)
-    return rounds_impl<Op, 64>(D, ld, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err, cfg.sym, cfg.rowP,
+    return rounds_impl<Op, 64>(D, L, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err, cfg.sym, cfg.rowP,
                                cfg.sym_flag, cfg.gate, cfg.dep_spins);
   return cudaErrorInvalidValue;
 }
@@ -2016,9 +2170,125 @@ cudaError_t launch_rounds(int dtype, void *D, int64_t ld, int64_t n, void *colT,
                           int64_t *launches, PhaseTimer *tm, const RoundConfig &cfg, int *wait_err) {
   if (n <= 0) return cudaSuccess;
   switch (dtype) {
-    case 0: return rounds_bk<OpI32>(cfg, D, ld, n, colT, ldT, s, launches, tm, wait_err);
-    case 1: return rounds_bk<OpU16>(cfg, D, ld, n, colT, ldT, s, launches, tm, wait_err);
-    case 2: return rounds_bk<OpF32>(cfg, D, ld, n, colT, ldT, s, launches, tm, wait_err);
+    case 0: return rounds_bk<OpI32>(cfg, D, Layout(ld), n, colT, ldT, s, launches, tm, wait_err);
+    case 1: return rounds_bk<OpU16>(cfg, D, Layout(ld), n, colT, ldT, s, launches, tm, wait_err);
+    case 2: return rounds_bk<OpF32>(cfg, D, Layout(ld), n, colT, ldT, s, launches, tm, wait_err);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+void tri_shape(int64_t n, int dtype, int64_t *rows, int64_t *ld) {
+  const Layout L = tri_layout(n, dtype == 1 ? 2 : 1, rows);
+  if (ld) *ld = L.ld;
+}
+
+cudaError_t launch_rounds_tri(int dtype, void *T, int64_t n, void *colT, int64_t ldT, cudaStream_t s,
+                              int64_t *launches, PhaseTimer *tm, RoundConfig cfg, int *wait_err) {
+  if (n <= 0) return cudaSuccess;
+  const Layout L = tri_layout(n, dtype == 1 ? 2 : 1, nullptr);
+  cfg.sym = true;
+  cfg.p3 = 3;
+  cfg.sym_flag = nullptr;
+  switch (dtype) {
+    case 0: return rounds_bk<OpI32>(cfg, T, L, n, colT, ldT, s, launches, tm, wait_err);
+    case 1: return rounds_bk<OpU16>(cfg, T, L, n, colT, ldT, s, launches, tm, wait_err);
+    case 2: return rounds_bk<OpF32>(cfg, T, L, n, colT, ldT, s, launches, tm, wait_err);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <class Op>
+static cudaError_t tri_fill_impl(const void *W, int64_t ldw, void *T, int64_t n, int *status, cudaStream_t s,
+                                 int64_t *launches) {
+  using E = typename Op::elem;
+  const Layout L = tri_layout(n, Op::EPW, nullptr);
+  const int64_t rows = (int64_t)L.T << L.sh;
+  tri_fill_kernel<Op><<<dim3(grid_cols(rows, 256), grid_rows(rows)), 256, 0, s>>>(static_cast<const E *>(W), ldw,
+                                                                                  static_cast<E *>(T), L, n, status);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tri_fill(int dtype, const void *W, int64_t ldw, void *T, int64_t n, int *status, cudaStream_t s,
+                            int64_t *launches) {
+  if (n <= 0) return cudaSuccess;
+  if (W) {  // an asymmetric W has no upper-triangular form: status |= 1
+    cudaError_t e = launch_symmetry_check(dtype, W, n, ldw, status, s);
+    if (e != cudaSuccess) return e;
+    if (launches) *launches += 1;
+  }
+  switch (dtype) {
+    case 0: return tri_fill_impl<OpI32>(W, ldw, T, n, status, s, launches);
+    case 1: return tri_fill_impl<OpU16>(W, ldw, T, n, status, s, launches);
+    case 2: return tri_fill_impl<OpF32>(W, ldw, T, n, status, s, launches);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <class Op>
+static cudaError_t tri_scatter_impl(const int32_t *src, const int32_t *dst, const void *w, int64_t m, void *T,
+                                    int64_t n, int *status, cudaStream_t s, int64_t *launches) {
+  using E = typename Op::elem;
+  cudaError_t e = tri_fill_impl<Op>(nullptr, 0, T, n, status, s, launches);
+  if (e != cudaSuccess || m <= 0) return e;
+  const Layout L = tri_layout(n, Op::EPW, nullptr);
+  int64_t blocks = (m + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  tri_scatter_edges_kernel<Op><<<(unsigned)blocks, 256, 0, s>>>(src, dst, static_cast<const E *>(w), m,
+                                                                static_cast<E *>(T), L, n, status);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tri_from_edges(int dtype, const int32_t *src, const int32_t *dst, const void *w, int64_t m,
+                                  void *T, int64_t n, int *status, cudaStream_t s, int64_t *launches) {
+  if (n <= 0) return cudaSuccess;
+  switch (dtype) {
+    case 0: return tri_scatter_impl<OpI32>(src, dst, w, m, T, n, status, s, launches);
+    case 1: return tri_scatter_impl<OpU16>(src, dst, w, m, T, n, status, s, launches);
+    case 2: return tri_scatter_impl<OpF32>(src, dst, w, m, T, n, status, s, launches);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <class Op>
+static cudaError_t tri_out_impl(const void *T, int64_t n, void *D, int64_t ld, const int64_t *rows, int64_t k,
+                                int *status, cudaStream_t s, int64_t *launches) {
+  using E = typename Op::elem;
+  const Layout L = tri_layout(n, Op::EPW, nullptr);
+  if (rows) {
+    if (k <= 0) return cudaSuccess;
+    tri_rows_kernel<Op><<<dim3(grid_cols(n, 256), grid_rows(k)), 256, 0, s>>>(
+        static_cast<const E *>(T), L, n, rows, k, static_cast<E *>(D), ld, status);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+  }
+  tri_to_dense_kernel<Op><<<dim3(grid_cols(n, 256), grid_rows(n)), 256, 0, s>>>(static_cast<const E *>(T), L, n,
+                                                                              static_cast<E *>(D), ld);
+  const dim3 gm((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
+  mirror_kernel<Op><<<gm, dim3(32, 8), 0, s>>>(static_cast<E *>(D), n, ld, nullptr);
+  if (launches) *launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tri_to_dense(int dtype, const void *T, int64_t n, void *D, int64_t ld, cudaStream_t s,
+                                int64_t *launches) {
+  if (n <= 0) return cudaSuccess;
+  switch (dtype) {
+    case 0: return tri_out_impl<OpI32>(T, n, D, ld, nullptr, 0, nullptr, s, launches);
+    case 1: return tri_out_impl<OpU16>(T, n, D, ld, nullptr, 0, nullptr, s, launches);
+    case 2: return tri_out_impl<OpF32>(T, n, D, ld, nullptr, 0, nullptr, s, launches);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_tri_rows(int dtype, const void *T, int64_t n, const int64_t *rows, int64_t k, void *out,
+                            int64_t ldo, int *status, cudaStream_t s, int64_t *launches) {
+  if (n <= 0 || k <= 0) return cudaSuccess;
+  switch (dtype) {
+    case 0: return tri_out_impl<OpI32>(T, n, out, ldo, rows, k, status, s, launches);
+    case 1: return tri_out_impl<OpU16>(T, n, out, ldo, rows, k, status, s, launches);
+    case 2: return tri_out_impl<OpF32>(T, n, out, ldo, rows, k, status, s, launches);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -51,8 +51,8 @@ struct RoundConfig {
 // (kernel 4 with round width 64, a 16-byte addressable D and more than one round).
 bool single_launch(int dtype, const void *D, int64_t ld, int64_t n, const RoundConfig &cfg);
 // The default Phase-3 kernel for (n, dtype) when nothing was tuned: every round
-// in one launch for mid-size n, one launch per round below and above
-// (profiles/phase3_variants_gmm16k.md).  Below n = 3072 a round is about one
+// in one launch for mid-size n, one launch per round below and above (timed
+// per n and dtype on GB300 with bench.py --round-shapes).  Below n = 3072 a round is about one
 // wave of tiles and the launches are cheaper than the single launch's item
 // scheduling; for large n the per-round launches' fixed cost per round is
 // small against the single launch's cost per tile.  Measured crossovers: int32
@@ -95,6 +95,31 @@ inline size_t row_panel_bytes(int64_t ldT, bool all_rounds) {
 cudaError_t launch_rounds(int dtype, void *D, int64_t ld, int64_t n, void *colT, int64_t ldT, cudaStream_t s,
                           int64_t *launches, PhaseTimer *timer = nullptr, const RoundConfig &cfg = RoundConfig(),
                           int *wait_err = nullptr);
+// Upper-triangular storage (the Layout of fw_device.cuh): only the S x S
+// super-tiles (I, J) with I <= J of the n x n matrix are stored (S = 128
+// elements per word lane: 128 for int32/fp32, 256 for packed 16-bit), folded
+// into a rectangle of *rows rows with row pitch *ld elements.
+void tri_shape(int64_t n, int dtype, int64_t *rows, int64_t *ld);
+// q rounds on T in that layout, symmetric mode, warp-specialized Phase 3 one
+// launch per round (cfg.bk and cfg.rowP are used; the other fields are set here).
+cudaError_t launch_rounds_tri(int dtype, void *T, int64_t n, void *colT, int64_t ldT, cudaStream_t s,
+                              int64_t *launches, PhaseTimer *timer, RoundConfig cfg, int *wait_err);
+// T <- the stored part of the symmetric dense W (checked as launch_ingest, plus
+// status |= 1 when W is not symmetric), or with W == nullptr 0 on the diagonal
+// and INF elsewhere; the padding is INF.
+cudaError_t launch_tri_fill(int dtype, const void *W, int64_t ldw, void *T, int64_t n, int *status, cudaStream_t s,
+                            int64_t *launches);
+// T <- the adjacency matrix of an undirected edge list (as launch_densify).
+cudaError_t launch_tri_from_edges(int dtype, const int32_t *src, const int32_t *dst, const void *w, int64_t m,
+                                  void *T, int64_t n, int *status, cudaStream_t s, int64_t *launches);
+// Dense n x n D (leading dimension ld) from T, both triangles.
+cudaError_t launch_tri_to_dense(int dtype, const void *T, int64_t n, void *D, int64_t ld, cudaStream_t s,
+                                int64_t *launches);
+// out[i][0..n) = row rows[i] of the matrix in T (rows: k device int64; a bad
+// index sets status |= 1).
+cudaError_t launch_tri_rows(int dtype, const void *T, int64_t n, const int64_t *rows, int64_t k, void *out,
+                            int64_t ldo, int *status, cudaStream_t s, int64_t *launches);
+
 // Copies W to D when they differ and checks the input (status |= 1 invalid, 2 range).
 cudaError_t launch_ingest(int dtype, const void *W, void *D, int64_t n, int64_t ld, int *status, cudaStream_t s,
                           int64_t *launches);

@@ -41,7 +41,7 @@ struct P1Smem {
 };
 
 template <class Op, int BK, int NT, bool CG, class Bar = CtaBar>
-__device__ __forceinline__ void phase1_body(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
+__device__ __forceinline__ void phase1_body(typename Op::elem *__restrict__ D, Layout L, int64_t n, int64_t p0,
                                             uint32_t *__restrict__ colT, int64_t ldT, P1Smem<Op, BK> &sm, int tid,
                                             typename Op::elem *__restrict__ rowP = nullptr) {
   using S = typename Op::scalar;
@@ -59,7 +59,7 @@ __device__ __forceinline__ void phase1_body(typename Op::elem *__restrict__ D, i
     for (int k = 0; k < IT; ++k) {
       const int idx = tid + k * NT;
       const int64_t r = p0 + idx / BK, c = p0 + idx % BK;
-      tmp[k] = (r < n && c < n) ? Op::to_s(ld_elem<CG>(D + r * ld + c)) : INF;
+      tmp[k] = (r < n && c < n) ? Op::to_s(ld_elem<CG>(D + L.off(r, c))) : INF;
     }
 #pragma unroll
     for (int k = 0; k < IT; ++k) {
@@ -135,7 +135,7 @@ __device__ __forceinline__ void phase1_body(typename Op::elem *__restrict__ D, i
   for (int idx = tid; idx < BK * BK; idx += NT) {
     const int i = idx / BK, j = idx % BK;
     const int64_t r = p0 + i, c = p0 + j;
-    if (r < n && c < n) D[r * ld + c] = Op::from_s(s[i][j]);
+    if (r < n && c < n) D[L.off(r, c)] = Op::from_s(s[i][j]);
   }
   for (int idx = tid; idx < BK * BK; idx += NT) {
     const int t = idx / BK, i = idx % BK;
@@ -166,7 +166,7 @@ struct SymPanel {
 
 // Per-element publication of a chunk that straddles p1 or n (out of line: rare).
 template <class Op>
-__device__ __noinline__ void sym_publish_slow(typename Op::elem *D, int64_t ld, int64_t n, int64_t p0, int64_t p1,
+__device__ __noinline__ void sym_publish_slow(typename Op::elem *D, Layout L, int64_t n, int64_t p0, int64_t p1,
                                               uint32_t *colT, int64_t ldT, const SymPanel<Op> *sym, int t,
                                               int64_t x0, uint4 w4) {
   constexpr int E = 4 * Op::EPW;
@@ -176,22 +176,22 @@ __device__ __noinline__ void sym_publish_slow(typename Op::elem *D, int64_t ld, 
     const typename Op::elem v = bits_elem<Op>(chunk_get<Op>(w4, e));
     colT[(int64_t)t * ldT + x] = Op::dup(v);
     if (sym->rowP) sym->rowP[(int64_t)t * ldT + x] = v;
-    if (x < sym->band_end && p0 + t < n) D[x * ld + p0 + t] = v;
+    if (x < sym->band_end && p0 + t < n) D[L.off(x, p0 + t)] = v;
   }
 }
 
 // Lower-triangle band elements D[x][p0+t] of a full chunk (out of line: only
 // the chunks next to the diagonal block have any).
 template <class Op>
-__device__ __noinline__ void sym_band_store(typename Op::elem *D, int64_t ld, int64_t col, int64_t band_end, int64_t x0,
+__device__ __noinline__ void sym_band_store(typename Op::elem *D, Layout L, int64_t col, int64_t band_end, int64_t x0,
                                             uint4 w4) {
   constexpr int E = 4 * Op::EPW;
   for (int e = 0; e < E; ++e)
-    if (x0 + e < band_end) D[(x0 + e) * ld + col] = bits_elem<Op>(chunk_get<Op>(w4, e));
+    if (x0 + e < band_end) D[L.off(x0 + e, col)] = bits_elem<Op>(chunk_get<Op>(w4, e));
 }
 
 template <class Op, int BK, int BNW, int NT, bool CG, int TN = 8, class Bar = CtaBar>
-__device__ __forceinline__ void p2_row_task(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
+__device__ __forceinline__ void p2_row_task(typename Op::elem *__restrict__ D, Layout L, int64_t n, int64_t p0,
                                             int64_t p1, uint32_t *__restrict__ colT, int64_t ldT, int64_t col0,
                                             bool vec, uint32_t *smem, int tid, const SymPanel<Op> *sym = nullptr) {
   using Map = TileMap<BK, BNW, TN>;
@@ -201,15 +201,15 @@ __device__ __forceinline__ void p2_row_task(typename Op::elem *__restrict__ D, i
   const int tx = tid % Map::TX, ty = tid / Map::TX;
   uint32_t acc[8][TN];
   load_As_colT<BK, BK, NT, CG>(As, colT, ldT, p0, tid);
-  load_Bs_rows<Op, BNW, BK, NT, CG>(Bs, D, ld, n, n, p0, col0, vec, tid);
-  load_acc<Op, BK, BNW, CG, TN>(D, ld, n, n, p0, col0, vec, acc, ty, tx);
+  load_Bs_rows<Op, BNW, BK, NT, CG>(Bs, D, L, n, n, p0, col0, vec, tid);
+  load_acc<Op, BK, BNW, CG, TN>(D, L, n, n, p0, col0, vec, acc, ty, tx);
   Bar::sync();
   tile_minplus<Op, BK, BNW, BK, TN>(As, Bs, acc, ty, tx);
   if (!sym) {
-    store_acc<Op, BK, BNW, TN>(D, ld, n, n, p0, col0, 0, 0, p0, p1, vec, acc, ty, tx);
+    store_acc<Op, BK, BNW, TN>(D, L, n, n, p0, col0, 0, 0, p0, p1, vec, acc, ty, tx);
     return;
   }
-  store_acc<Op, BK, BNW, TN>(D, ld, n, n, p0, col0, 0, 0, 0, p1, vec, acc, ty, tx);
+  store_acc<Op, BK, BNW, TN>(D, L, n, n, p0, col0, 0, 0, 0, p1, vec, acc, ty, tx);
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
     const int t = Map::row(ty, r);
@@ -230,9 +230,9 @@ __device__ __forceinline__ void p2_row_task(typename Op::elem *__restrict__ D, i
                                                           Op::dup(w4.w & 0xFFFFu), Op::dup(w4.w >> 16));
           *reinterpret_cast<uint4 *>(sym->rowP + (int64_t)t * ldT + x0) = w4;
         }
-        if (x0 < sym->band_end && p0 + t < n) sym_band_store<Op>(D, ld, p0 + t, sym->band_end, x0, w4);
+        if (x0 < sym->band_end && p0 + t < n) sym_band_store<Op>(D, L, p0 + t, sym->band_end, x0, w4);
       } else if (x0 + E > p1 && x0 < n) {
-        sym_publish_slow<Op>(D, ld, n, p0, p1, colT, ldT, sym, t, x0, w4);
+        sym_publish_slow<Op>(D, L, n, p0, p1, colT, ldT, sym, t, x0, w4);
       }
     }
   }
@@ -250,7 +250,7 @@ static __device__ __noinline__ void colT_store_partial(uint32_t *dst, int64_t rb
 }
 
 template <class Op, int BK, int BM, int NT, bool CG, int TN = 8, class Bar = CtaBar>
-__device__ __forceinline__ void p2_col_task(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
+__device__ __forceinline__ void p2_col_task(typename Op::elem *__restrict__ D, Layout L, int64_t n, int64_t p0,
                                             int64_t p1, uint32_t *__restrict__ colT, int64_t ldT, int64_t row0,
                                             bool vec, uint32_t *smem, int tid, const SymPanel<Op> *sym = nullptr) {
   constexpr int BNW = BK / Op::EPW;
@@ -260,14 +260,14 @@ __device__ __forceinline__ void p2_col_task(typename Op::elem *__restrict__ D, i
   uint32_t *Bs = smem + BK * BM;
   const int tx = tid % Map::TX, ty = tid / Map::TX;
   uint32_t acc[8][TN];
-  load_As_transposed<Op, BM, BK, NT, CG>(As, D, ld, n, n, row0, p0, vec, tid);
-  load_Bs_rows<Op, BNW, BK, NT, CG>(Bs, D, ld, n, n, p0, p0, vec, tid);
-  load_acc<Op, BM, BNW, CG, TN>(D, ld, n, n, row0, p0, vec, acc, ty, tx);
+  load_As_transposed<Op, BM, BK, NT, CG>(As, D, L, n, n, row0, p0, vec, tid);
+  load_Bs_rows<Op, BNW, BK, NT, CG>(Bs, D, L, n, n, p0, p0, vec, tid);
+  load_acc<Op, BM, BNW, CG, TN>(D, L, n, n, row0, p0, vec, acc, ty, tx);
   Bar::sync();
   tile_minplus<Op, BM, BNW, BK, TN>(As, Bs, acc, ty, tx);
   // symmetric mode stores rows < p0 only
   const int64_t xr1 = sym ? INT64_MAX : p1;
-  store_acc<Op, BM, BNW, TN>(D, ld, n, n, row0, p0, p0, xr1, 0, 0, vec, acc, ty, tx);
+  store_acc<Op, BM, BNW, TN>(D, L, n, n, row0, p0, p0, xr1, 0, 0, vec, acc, ty, tx);
   // transposed copy: colT[t][row0 + i] = word(D_Ik[i][t]) for rows outside [p0, p1)
 #pragma unroll
   for (int h = 0; h < Map::NH; ++h) {
@@ -304,7 +304,7 @@ __device__ __forceinline__ void p2_col_task(typename Op::elem *__restrict__ D, i
 // symB (nullable): symmetric mode, B rows come from this BK x ldT panel of
 // elements instead of D's row panel.
 template <class Op, int BK, bool CG>
-__device__ __forceinline__ void p3_task(typename Op::elem *__restrict__ D, int64_t ld, int64_t n, int64_t p0,
+__device__ __forceinline__ void p3_task(typename Op::elem *__restrict__ D, Layout L, int64_t n, int64_t p0,
                                         int64_t p1, const uint32_t *__restrict__ colT, int64_t ldT, int64_t row0,
                                         int64_t col0, bool vec, uint32_t *smem, int tid,
                                         const typename Op::elem *symB = nullptr) {
@@ -318,11 +318,11 @@ __device__ __forceinline__ void p3_task(typename Op::elem *__restrict__ D, int64
   if (symB)
     load_Bs_rows<Op, BNW, BK, NT, CG>(Bs, symB, ldT, BK, ldT, 0, col0, true, tid);
   else
-    load_Bs_rows<Op, BNW, BK, NT, CG>(Bs, D, ld, n, n, p0, col0, vec, tid);
-  load_acc<Op, BM, BNW, CG>(D, ld, n, n, row0, col0, vec, acc, ty, tx);
+    load_Bs_rows<Op, BNW, BK, NT, CG>(Bs, D, L, n, n, p0, col0, vec, tid);
+  load_acc<Op, BM, BNW, CG>(D, L, n, n, row0, col0, vec, acc, ty, tx);
   __syncthreads();
   tile_minplus<Op, BM, BNW, BK>(As, Bs, acc, ty, tx);
-  store_acc<Op, BM, BNW>(D, ld, n, n, row0, col0, p0, p1, p0, p1, vec, acc, ty, tx);
+  store_acc<Op, BM, BNW>(D, L, n, n, row0, col0, p0, p1, p0, p1, vec, acc, ty, tx);
 }
 
 }  // namespace apsp

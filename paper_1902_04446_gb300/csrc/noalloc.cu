@@ -11,7 +11,10 @@
 // Its only scratch memory (the round's panel buffer and one word for the
 // bounded-wait flag) is a fixed array in this file, in device global memory,
 // sized for n <= APSP_NOALLOC_MAX_N.  Every GPU that loads the library holds
-// that array until the process exits.
+// that array until the process exits.  The flag word of the last call stays
+// in the array after the call; apsp_noalloc_status reads it back (a copy
+// into the caller's stack, no allocation), so a caller learns when a bounded
+// wait of the Phase-3 kernel gave up and left D incomplete.
 #include <cstdint>
 #include <mutex>
 
@@ -73,4 +76,16 @@ extern "C" apsp_status apsp_solve_i32_noalloc(const int32_t *W, int64_t n, int64
   if (apsp::launch_rounds(APSP_I32, D, ld, n, panel, ldT, s, nullptr, nullptr, rc, wait_flag) != cudaSuccess)
     return APSP_E_CUDA;
   return APSP_OK;
+}
+
+extern "C" apsp_status apsp_noalloc_status(void *stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return APSP_E_CUDA;
+  // the flag word sits right after the panel words; a copy from the symbol
+  // into a host int (pageable: the copy completes before the call returns)
+  int flag = 0;
+  if (cudaMemcpyFromSymbol(&flag, g_noalloc_scratch, sizeof(int), kPanelWords * sizeof(uint32_t),
+                           cudaMemcpyDeviceToHost) != cudaSuccess)
+    return APSP_E_CUDA;
+  return (flag & 4) ? APSP_E_TIMEOUT : APSP_OK;
 }

@@ -54,6 +54,57 @@ def _L():
     return get_lib()
 
 
+_TORCH_DT = {APSP_I32: "int32", APSP_U16: "int16", APSP_F32: "float32"}
+
+
+def tri_layout(dtype, n: int):
+    """apsp_tri_layout: (rows, ld, bytes) of the upper-triangular layout's rectangle for n."""
+    r, l, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    st = _L().apsp_tri_layout(dtype_code(dtype), n, ctypes.byref(r), ctypes.byref(l), ctypes.byref(b))
+    if st != 0:
+        raise ApspError(st, "apsp_tri_layout")
+    return int(r.value), int(l.value), int(b.value)
+
+
+def tri_empty(dtype, n: int, device=0):
+    """A device tensor shaped as the upper-triangular layout's rectangle (rows, ld) for n."""
+    import torch
+    code = dtype_code(dtype)
+    rows, ld, _ = tri_layout(code, n)
+    return torch.empty((rows, ld), dtype=getattr(torch, _TORCH_DT[code]), device=device)
+
+
+def tri_to_dense(dtype, T, n: int, D=None, stream=None):
+    """apsp_tri_to_dense: the full n x n matrix held in T (allocated when D is None)."""
+    import torch
+    code = dtype_code(dtype)
+    if D is None:
+        D = torch.empty((n, n), dtype=T.dtype, device=T.device)
+    nd, ld = _mat(D, "D")
+    st = _L().apsp_tri_to_dense(code, T.data_ptr(), n, D.data_ptr(), ld, _stream(stream, T.device))
+    if st != 0:
+        raise ApspError(st, "apsp_tri_to_dense")
+    return D
+
+
+def tri_rows(dtype, T, n: int, rows, out=None, stream=None):
+    """apsp_tri_rows: rows `rows` (a 1-D int64 CUDA tensor) of the full matrix held in T."""
+    import torch
+    code = dtype_code(dtype)
+    if rows.dtype != torch.int64 or not rows.is_cuda or not rows.is_contiguous():
+        raise TypeError("rows must be a contiguous int64 CUDA tensor")
+    k = rows.numel()
+    if out is None:
+        out = torch.empty((k, n), dtype=T.dtype, device=T.device)
+    if out.dim() != 2 or out.stride(1) != 1 or out.shape[0] < k or out.shape[1] < n:
+        raise ValueError("out must be a row-major (k, >=n) matrix")
+    st = _L().apsp_tri_rows(code, T.data_ptr(), n, rows.data_ptr(), k, out.data_ptr(), out.stride(0),
+                            _stream(stream, T.device))
+    if st != 0:
+        raise ApspError(st, "apsp_tri_rows")
+    return out
+
+
 class Handle:
     """Owns one ``apsp_handle`` (workspace, serving thread) on one device."""
 
@@ -150,6 +201,39 @@ class Handle:
         self._check(_L().apsp_solve_squaring(self._h, code, W.data_ptr(), n, ld, D.data_ptr(),
                                              _stream(stream, W.device)), "apsp_solve_squaring")
         return D
+
+    def tri_from_dense(self, dtype, W, T=None, stream=None):
+        """apsp_tri_from_dense: T (allocated when None) <- the upper-triangular layout of the symmetric W."""
+        code = dtype_code(dtype)
+        n, ld = _mat(W, "W")
+        _elem_ok(W, code)
+        if T is None:
+            T = tri_empty(code, n, W.device)
+        self._check(_L().apsp_tri_from_dense(self._h, code, W.data_ptr(), n, ld, T.data_ptr(),
+                                             _stream(stream, W.device)), "apsp_tri_from_dense")
+        return T
+
+    def tri_from_edges(self, dtype, src, dst, w, n, T=None, stream=None):
+        """apsp_tri_from_edges: T (allocated when None) <- an undirected edge list's adjacency matrix."""
+        import torch
+        code = dtype_code(dtype)
+        if T is None:
+            T = tri_empty(code, n, src.device)
+        m = src.numel()
+        for t in (src, dst):
+            if t.dtype != torch.int32 or not t.is_cuda or not t.is_contiguous():
+                raise TypeError("src/dst must be contiguous int32 CUDA tensors")
+        if not w.is_contiguous() or not w.is_cuda or w.numel() != m:
+            raise TypeError("w must be a contiguous CUDA tensor of m weights")
+        self._check(_L().apsp_tri_from_edges(self._h, code, src.data_ptr(), dst.data_ptr(), w.data_ptr(), m, n,
+                                             T.data_ptr(), _stream(stream, T.device)), "apsp_tri_from_edges")
+        return T
+
+    def solve_tri(self, dtype, T, n: int, stream=None):
+        """apsp_solve_tri: APSP in place on T (upper-triangular layout); returns T."""
+        self._check(_L().apsp_solve_tri(self._h, dtype_code(dtype), T.data_ptr(), n, _stream(stream, T.device)),
+                    "apsp_solve_tri")
+        return T
 
     def solve(self, W, D=None, stream=None):
         """apsp_solve with the handle's dtype."""
@@ -253,12 +337,13 @@ class Handle:
         return C
 
     # ------------------------------------------------------------ request loop
-    def submit(self, W) -> int:
-        """apsp_submit: W is an int32 (n, >=n) tensor on the host (pinned or not) or the device."""
+    def submit(self, W, dtype="int32") -> int:
+        """apsp_submit: W is an int32 (n, >=n) tensor on the host (pinned or not) or the device; dtype "int32" or
+        "auto" (packed 16-bit rounds for a large request when the bound holds; the result is int32)."""
         if W.dim() != 2 or W.stride(1) != 1 or W.shape[1] < W.shape[0]:
             raise ValueError("W must be a row-major (n, >=n) matrix")
         _elem_ok(W, APSP_I32)
-        r = apsp_request(W.data_ptr(), 0 if W.is_cuda else 1, W.shape[0], W.stride(0))
+        r = apsp_request(W.data_ptr(), 0 if W.is_cuda else 1, W.shape[0], W.stride(0), dtype_code(dtype))
         t = ctypes.c_uint64()
         self._check(_L().apsp_submit(self._h, ctypes.byref(r), ctypes.byref(t)), "apsp_submit")
         self._hold[int(t.value)] = W

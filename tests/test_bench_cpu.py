@@ -45,3 +45,17 @@ def test_traffic_entries_are_keyed_by_source():
     assert bench.ncu_traffic("no_such_kernel_gmm16k") is None
     h = bench.source_hash()
     assert len(h) == 16 and int(h, 16) >= 0
+
+
+def test_cpu_baseline_reports_its_extrapolation_as_such():
+    b = bench.cpu_baseline("roll64k", n_s=128, n_full=65536)
+    assert b["kind"] == "oracle" and b["cores"] == 1 and b["value"] > 0
+    assert b["extrapolated"]["n"] == 65536 and "not measured" in b["extrapolated"]["how"]
+    assert abs(b["extrapolated"]["seconds"] - 65536 ** 3 / (b["value"] * 1e9)) < 1e-6 * b["extrapolated"]["seconds"]
+
+
+def test_default_workload_is_the_n65536_roll():
+    import argparse  # noqa: F401
+    assert "roll64k" in bench.WORKLOAD_TEXT
+    src = open(bench.__file__).read()
+    assert 'ap.add_argument("--workload", default="roll64k"' in src

@@ -222,3 +222,61 @@ def test_block_k_32_matches_oracle(lib, n):
         E = oracle.fw(W.astype(np.int64)).astype(np.float64)
         E[E >= INF] = np.inf
         np.testing.assert_array_equal(Df.astype(np.float64), E)  # small integers: exact in fp32
+
+
+def test_serving_states_admitted_then_running(lib):
+    """apsp_poll walks QUEUED -> ADMITTED (input copy in flight) -> RUNNING (W copied, rounds running) -> DONE, never
+    backwards.  Large pinned host inputs make the copy long enough to be seen; the handle skips the symmetry check
+    (symmetric = 2), which would otherwise wait for the copy inside admission."""
+    seen_admitted = False
+    with lib.Handle(device=0, symmetric=2) as h:
+        for i in range(4):
+            W = torch.from_numpy(er_dense(4000, 40 + i)).pin_memory()
+            t = h.submit(W)
+            states = []
+            while True:
+                st, _, rc = h.poll(t)
+                assert rc == 0
+                if not states or states[-1] != st:
+                    states.append(st)
+                if st == 3:
+                    break
+            assert states == sorted(states), states
+            seen_admitted |= 1 in states
+            assert 2 in states or states[-1] == 3
+            out = torch.empty((4000, 4000), dtype=torch.int32, device="cuda")
+            h.fetch(t, out)
+            torch.cuda.synchronize()
+            assert h.release(t) == 0
+            assert torch.equal(out, h.solve_t("int32", W.cuda()))
+    assert seen_admitted
+
+
+def test_serving_auto_requests_equal_int32_and_oracle(H):
+    """apsp_request.dtype = APSP_AUTO: a large request whose 16-bit bound holds runs its rounds in packed 16-bit,
+    one whose bound fails (a long heavy path) and the small ones run in int32; every result is the int32 matrix,
+    equal to the same graph solved alone and to the oracle."""
+    cases = []
+    for n, seed, wmax in ((2000, 71, 100), (400, 72, 1000), (1700, 73, 100)):
+        s, d, w = gen.er_graph(n, seed, avg_degree=8.0, wmax=wmax)
+        cases.append((gen.dense_matrix(n, s, d, w, dtype=np.int32), s, d, w))
+    n = 1600  # path with weight 1000: distances up to 1.6e6, the 16-bit bound fails
+    s = np.arange(n - 1)
+    d = s + 1
+    w = np.full(n - 1, 1000)
+    cases.append((gen.dense_matrix(n, s, d, w, dtype=np.int32), s, d, w))
+    W0 = dev(cases[0][0])
+    b, ok = H.int16_bound(W0)
+    assert ok, b  # the first large request does take the packed path
+    tickets = [H.submit(dev(W), dtype="auto") for W, *_ in cases]
+    for t, (W, s, d, w) in zip(tickets, cases):
+        n = W.shape[0]
+        assert H.wait(t, 120000) == 0
+        out = torch.empty((n, n), dtype=torch.int32, device="cuda")
+        H.fetch(t, out)
+        torch.cuda.synchronize()
+        assert H.release(t) == 0
+        assert torch.equal(out, H.solve_t("int32", dev(W)))
+        np.testing.assert_array_equal(out.cpu().numpy().astype(np.int64), oracle.dijkstra(n, s, d, w, np.arange(n)))
+    with pytest.raises(Exception):
+        H.submit(dev(cases[1][0]), dtype="fp32")

@@ -348,44 +348,69 @@ def test_input_checks_reported(H, lib):
 
 
 # ------------------------------------------------------------------ full-size workloads (sampled rows)
-def _sampled_rows_check(D_dev, g, nsample, seed, fp=False):
-    rng = np.random.default_rng(seed)
-    rows = np.sort(rng.choice(g.n, size=nsample, replace=False))
-    got = D_dev[torch.from_numpy(rows).cuda()].cpu().numpy()
-    if fp:
-        w = g.w.astype(np.float32).astype(np.float64)
-        exp = oracle.dijkstra(g.n, g.src, g.dst, w, rows)
-        got = got.astype(np.float64)
-        np.testing.assert_array_equal(np.isinf(got), np.isinf(exp))
-        f = np.isfinite(exp) & (exp > 0)
-        assert (np.abs(got[f] - exp[f]) <= REL_TOL * exp[f]).all()
-    else:
-        exp = oracle.dijkstra(g.n, g.src, g.dst, g.w, rows)
-        np.testing.assert_array_equal(got.astype(np.int64), exp)
+def _whole_matrix_check(D_dev, g, fp=False, chunk=2048):
+    """Every row of the solved matrix against the oracle's Dijkstra from that source (row chunks bound the host
+    memory): bit-exact for integer weights; for fp32 weights the +inf set is identical and every finite entry is
+    within REL_TOL of the float64 distance."""
+    n = g.n
+    w = g.w.astype(np.float32).astype(np.float64) if fp else g.w
+    for r0 in range(0, n, chunk):
+        rows = np.arange(r0, min(n, r0 + chunk))
+        got = D_dev[r0:r0 + rows.shape[0]].cpu().numpy()
+        exp = oracle.dijkstra(n, g.src, g.dst, w, rows)
+        if fp:
+            got = got.astype(np.float64)
+            np.testing.assert_array_equal(np.isinf(got), np.isinf(exp))
+            f = np.isfinite(exp)
+            assert (np.abs(got[f] - exp[f]) <= REL_TOL * exp[f]).all()
+        else:
+            np.testing.assert_array_equal(got.astype(np.int64), exp)
 
 
-def test_gmm16k_int32_sampled(H):
+def test_gmm16k_int32_and_auto_whole_matrix(H):
+    """gmm16k (n = 16384, 8 components): the int32 solve and the automatic-precision solve (bound, packed 16-bit
+    rounds) equal the oracle's Dijkstra from every source, element by element."""
     g = gen.workload("gmm16k")
     W = dev(gen.dense_matrix(g.n, g.src, g.dst, g.w, dtype=np.int32))
     D = H.solve_t("int32", W)
-    _sampled_rows_check(D, g, 256, seed=1)
-    # symmetry and zero diagonal over the whole matrix (a property at any size)
-    assert torch.equal(D, D.T) and bool((torch.diagonal(D) == 0).all())
+    assert H.last_status() == 0
+    A = H.solve_t("auto", W)
+    assert H.last_status() == 0
+    assert torch.equal(A, D)
+    del A
+    _whole_matrix_check(D, g)
 
 
-def test_gmm16k_fp32_sampled(H):
+def test_gmm16k_fp32_whole_matrix(H):
+    """gmm16k with raw Euclidean fp32 weights: every row within 1e-4 relative of the float64 Dijkstra distances,
+    the +inf set (pairs in different components) identical."""
     g = gen.workload("gmm16k_f32")
     W = dev(gen.dense_matrix(g.n, g.src, g.dst, g.w.astype(np.float32), dtype=np.float32))
     D = H.solve_t("fp32", W)
-    _sampled_rows_check(D, g, 128, seed=2, fp=True)
+    assert H.last_status() == 0
+    _whole_matrix_check(D, g, fp=True)
 
 
-def test_gmm16k_auto_equals_int32(H):
-    g = gen.workload("gmm16k")
-    W = dev(gen.dense_matrix(g.n, g.src, g.dst, g.w, dtype=np.int32))
-    A = H.solve_t("auto", W)
-    B = H.solve_t("int32", W)
-    assert torch.equal(A, B)
+def test_fp32_negative_zero_weights_are_canonical(H):
+    """A -0.0 weight is a zero-weight edge: stored as +0.0 by the input pass (the Phase-3 reduction compares fp32
+    bit patterns as int32), so the result equals the same graph with +0.0 weights, in place and copied."""
+    n = 300
+    s, d, w = er_edges(n, seed=7, deg=4.0, wmax=30)
+    wf = w.astype(np.float32)
+    wf[::5] = 0.0
+    Wp = gen.dense_matrix(n, s, d, wf, dtype=np.float32)
+    Wn = Wp.copy()
+    Wn[Wn == 0.0] = -0.0
+    assert (np.signbit(Wn) & (Wn == 0)).sum() > n  # diagonal and the zero-weight edges are -0.0
+    ref = H.solve_t("fp32", dev(Wp)).cpu().numpy()
+    got = H.solve_t("fp32", dev(Wn)).cpu().numpy()
+    assert H.last_status() == 0
+    np.testing.assert_array_equal(got.view(np.uint32), ref.view(np.uint32))
+    Wi = dev(Wn)
+    H.solve_t("fp32", Wi, Wi)  # in place
+    np.testing.assert_array_equal(Wi.cpu().numpy().view(np.uint32), ref.view(np.uint32))
+    E = oracle.fw(Wp.astype(np.float64))
+    np.testing.assert_array_equal(ref.astype(np.float64), E)  # integer-valued weights: exact
 
 
 # ------------------------------------------------------------------ every round shape
@@ -594,3 +619,98 @@ def test_single_vertex(H, dt):
     np_dt = {"int32": np.int32, "auto": np.int32, "u16": np.int16, "fp32": np.float32}[dt]
     D = H.solve_t(dt, dev(np.zeros((1, 1), dtype=np_dt))).cpu().numpy()
     assert D.shape == (1, 1) and D[0, 0] == 0
+
+
+# ------------------------------------------------------------------ pack / unpack through the C ABI
+@pytest.mark.parametrize("n,lds,ldd", [(1, 1, 1), (5, 7, 8), (300, 301, 304), (1000, 1000, 1003)])
+def test_pack_unpack_abi_match_oracle(lib, n, lds, ldd):
+    """apsp_pack_u16 / apsp_unpack_u16 against oracle.pack_u16 / unpack_u16 with separate leading dimensions and
+    the edge values 0, 1, 32766 (the largest finite 16-bit distance) and INF; padding columns stay untouched."""
+    import ctypes
+    rng = np.random.default_rng(n + lds + ldd)
+    D32 = rng.integers(0, 32767, size=(n, n)).astype(np.int64)
+    D32[rng.random((n, n)) < 0.2] = INF
+    edge = np.array([0, 1, 32766, INF], dtype=np.int64)
+    D32.reshape(-1)[: min(4, n * n)] = edge[: min(4, n * n)]
+    src = np.full((n, lds), -5, dtype=np.int32)
+    src[:, :n] = D32
+    s_dev = dev(src)
+    d_dev = torch.full((n, ldd), -3, dtype=torch.int16, device="cuda")
+    L = lib.get_lib()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert L.apsp_pack_u16(ctypes.c_void_p(s_dev.data_ptr()), lds, ctypes.c_void_p(d_dev.data_ptr()), ldd, n,
+                           stream) == 0
+    got16 = d_dev.cpu().numpy().view(np.uint16)
+    np.testing.assert_array_equal(got16[:, :n], oracle.pack_u16(D32.astype(np.int32)))
+    assert (d_dev[:, n:] == -3).all()
+    back = torch.full((n, lds), -9, dtype=torch.int32, device="cuda")
+    assert L.apsp_unpack_u16(ctypes.c_void_p(d_dev.data_ptr()), ldd, ctypes.c_void_p(back.data_ptr()), lds, n,
+                             stream) == 0
+    got32 = back.cpu().numpy()
+    np.testing.assert_array_equal(got32[:, :n], oracle.unpack_u16(got16[:, :n]))
+    np.testing.assert_array_equal(got32[:, :n], D32)
+    assert (back[:, n:] == -9).all()
+
+
+# ------------------------------------------------------------------ upper-triangular storage
+def _tri_dense_input(n, dt, seed):
+    s, d, w = er_edges(n, seed=seed, deg=4.0, wmax=40)
+    if dt == "int32":
+        return gen.dense_matrix(n, s, d, w, dtype=np.int32), s, d, w
+    if dt == "u16":
+        return gen.dense_matrix(n, s, d, w, dtype=np.int16, inf=0x7FFF), s, d, w
+    return gen.dense_matrix(n, s, d, w, dtype=np.float32), s, d, w
+
+
+def _as_oracle_units(D, dt):
+    if dt == "u16":
+        return oracle.unpack_u16(D.view(np.uint16)).astype(np.int64)
+    if dt == "fp32":
+        return np.where(np.isinf(D), INF, D.astype(np.float64)).astype(np.int64)  # small integers: exact
+    return D.astype(np.int64)
+
+
+@pytest.mark.parametrize("dt", ["int32", "u16", "fp32"])
+@pytest.mark.parametrize("n", [1, 2, 65, 129, 255, 257, 300, 700, 1300])
+def test_tri_storage_solve_matches_oracle(lib, dt, n):
+    """apsp_tri_from_dense -> apsp_solve_tri -> apsp_tri_to_dense / apsp_tri_rows: the full matrix equals the
+    oracle's (Floyd-Warshall on the dense input), for sizes around the 128 / 256-element super-tiles."""
+    W, *_ = _tri_dense_input(n, dt, seed=n + 17)
+    E = expect_fw(_as_oracle_units(W, dt))
+    with lib.Handle(device=0) as h:
+        T = h.tri_from_dense(dt, dev(W))
+        rows, ld, nbytes = lib.tri_layout(dt, n)
+        assert tuple(T.shape) == (rows, ld) and T.numel() * T.element_size() == nbytes
+        h.solve_tri(dt, T, n)
+        assert h.last_status() == 0
+        D = lib.tri_to_dense(dt, T, n).cpu().numpy()
+        np.testing.assert_array_equal(_as_oracle_units(D, dt), E)
+        pick = torch.tensor(sorted({0, n // 3, n // 2, n - 1}), dtype=torch.int64, device="cuda")
+        R = lib.tri_rows(dt, T, n, pick).cpu().numpy()
+        np.testing.assert_array_equal(_as_oracle_units(R, dt), E[pick.cpu().numpy()])
+
+
+def test_tri_storage_from_edges_equals_dense_solve(lib):
+    """The same graph from its edge list into upper-triangular storage and into a dense matrix: identical results
+    (int32 and packed 16-bit), at a size with many super-tile rows in both halves of the folded rectangle."""
+    n = 3000
+    s, d, w = gen.er_graph(n, 77, avg_degree=8.0, wmax=200)
+    with lib.Handle(device=0) as h:
+        for dt, wdt in (("int32", np.int32), ("u16", np.int16)):
+            src = torch.from_numpy(s.astype(np.int32)).cuda()
+            dst = torch.from_numpy(d.astype(np.int32)).cuda()
+            ww = torch.from_numpy(w.astype(wdt)).cuda()
+            Dd = h.solve_edges(dt, src, dst, ww, n)
+            T = h.tri_from_edges(dt, src, dst, ww, n)
+            h.solve_tri(dt, T, n)
+            assert h.last_status() == 0
+            assert torch.equal(lib.tri_to_dense(dt, T, n), Dd)
+
+
+def test_tri_storage_refuses_asymmetric_input(lib):
+    n = 200
+    s, d, w = er_edges(n, seed=5, deg=4.0, wmax=40, directed=True)
+    W = dense_directed(n, s, d, w)
+    with lib.Handle(device=0) as h:
+        h.tri_from_dense("int32", dev(W))
+        assert h.last_status() == lib.APSP_I32 + 1  # APSP_E_INVALID
