@@ -380,9 +380,9 @@ def addmin_peaks(apsp, device):
     L = apsp.get_lib()
     out = {}
     for name, code in (("int32", apsp.APSP_I32), ("u16x2", apsp.APSP_U16), ("fp32", apsp.APSP_F32)):
-        lanes, rps = ctypes.c_double(), ctypes.c_double()
-        if L.apsp_addmin_peak(device, code, ctypes.byref(lanes), ctypes.byref(rps)) == 0:
-            out[name] = {"lane_ops_per_clk_per_sm": lanes.value, "grelax_per_s_event_timed": rps.value / 1e9}
+        rpc, rps = ctypes.c_double(), ctypes.c_double()
+        if L.apsp_addmin_peak(device, code, ctypes.byref(rpc), ctypes.byref(rps)) == 0:
+            out[name] = {"relax_per_clk_per_sm": rpc.value, "grelax_per_s_event_timed": rps.value / 1e9}
     return out
 
 
@@ -502,7 +502,7 @@ def run_gpu(args):
                 "achieved": achieved, "peak": peak, "unit": UNIT, "work": work,
                 "frac": (achieved / peak) if achieved else None,
                 "peak_basis": f"{ADDMIN_LANES_PER_CLK_PER_SM} add-min lanes/clk/SM (the SM's INT32 lanes; measured "
-                              f"live: {live.get('int32', {}).get('lane_ops_per_clk_per_sm', float('nan')):.1f}) x "
+                              f"live: {live.get('int32', {}).get('relax_per_clk_per_sm', float('nan')):.1f}) x "
                               f"{sms} SMs x {sm_max_mhz:.0f} MHz (max SM clock)",
                 "traffic": ncu_traffic(f"{kkey}_int32_{args.workload}"),
                 "traffic_unit": "DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
@@ -602,17 +602,17 @@ def extras_gmm16k(torch, apsp, h, args, dist, device, peak, live, sms, sm_max_mh
     msf, lf, proff = timed_solves(torch, h, "fp32", Wf, Df, args.steps, args.warmup, dist, profile=True)
     vf, msf = job_value(torch, dist, relax_step * args.steps, msf)
     af = phase3_rate(proff)
-    f_lanes = live.get("fp32", {}).get("lane_ops_per_clk_per_sm")
-    peak_f = f_lanes * sms * sm_max_mhz / 1e3 if f_lanes else None
+    f_rpc = live.get("fp32", {}).get("relax_per_clk_per_sm")
+    peak_f = f_rpc * sms * sm_max_mhz / 1e3 if f_rpc else None
     kf = "fw_solve_ws<fp32> (every round in one launch)" if h.tuned_config("fp32", n)[1] == 4 else \
         "fw_phase3_ws<fp32> (one launch per round)"
     out["fp32"] = {"workload": "gmm16k_f32: the gmm16k points, raw Euclidean distances as fp32 weights",
                    "value": vf, "unit": UNIT, "ms_per_step": msf / args.steps, "gpu_launches": int(lf),
                    "roofline": {"bound": "alu", "kernel": kf, "achieved": af, "peak": peak_f, "unit": UNIT,
                                 "frac": (af / peak_f) if (af and peak_f) else None,
-                                "peak_basis": f"fp32 add-min (fadd + fmin) lane-ops/clk/SM measured live "
-                                              f"({f_lanes:.1f}) x {sms} SMs x {sm_max_mhz:.0f} MHz"
-                                if f_lanes else None,
+                                "peak_basis": f"relaxations/clk/SM of the fp32 tile's instruction form (packed pair "
+                                              f"add + three-input min) measured live ({f_rpc:.1f}) x {sms} SMs x "
+                                              f"{sm_max_mhz:.0f} MHz" if f_rpc else None,
                                 "frac_of_int32_peak": (af / peak) if af else None}}
     del Wf, Df
 

@@ -385,14 +385,16 @@ apsp_status apsp_noalloc_status(void *stream);
 /* The relaxation c = min(c, a + b) is the min-plus step of Table 1 (MatProd
  * followed by MatMin); Phase 3 is bound by how many of them the SMs issue per
  * clock.  apsp_addmin_peak measures that rate on `device` for the add-min form
- * the library uses for `dtype` (APSP_I32: __viaddmin_s32; APSP_U16:
- * __viaddmin_u16x2, two relaxations per lane-op; APSP_F32: fminf(a + b, c)):
- * independent chains in registers, one full wave of 4 CTAs x 256 threads per
- * SM.  *lane_ops_per_clk_per_sm = 32-bit add-min lane-ops per SM clock (by
- * clock64 of the slowest CTA); *relax_per_s = relaxations per second by event
- * time (at whatever clock the GPU ran).  Allocates a few KB of device memory
- * and synchronizes the device.  Errors: APSP_E_INVALID, APSP_E_CUDA. */
-apsp_status apsp_addmin_peak(int device, int dtype, double *lane_ops_per_clk_per_sm, double *relax_per_s);
+ * the library's Phase-3 tiles use for `dtype` (APSP_I32: __viaddmin_s32;
+ * APSP_U16: __viaddmin_u16x2, two relaxations per 32-bit lane-op; APSP_F32:
+ * two k-steps at a time, a packed pair add for two neighbouring columns and
+ * one three-input minimum for each output's two sums): independent chains in
+ * registers, one full wave of 4 CTAs x 256 threads per SM.
+ * *relax_per_clk_per_sm = relaxations per SM clock (by clock64 of the slowest
+ * CTA); *relax_per_s = relaxations per second by event time (at whatever
+ * clock the GPU ran).  Allocates a few KB of device memory and synchronizes
+ * the device.  Errors: APSP_E_INVALID, APSP_E_CUDA. */
+apsp_status apsp_addmin_peak(int device, int dtype, double *relax_per_clk_per_sm, double *relax_per_s);
 
 /* out[i] = the library's add-min of the 32-bit words (a[i], b[i], c[i]) for
  * `dtype`: APSP_I32 min(a + b, c) as int32; APSP_U16 per 16-bit lane

@@ -5,11 +5,14 @@
 // The relaxation c = min(c, a + b) is the min-plus step of the paper's Table 1
 // (MatProd followed by MatMin).  Phase 3 is bound by how many of these the SMs
 // issue per clock, so the roofline denominator is that rate:
-//   APSP_I32  __viaddmin_s32            one relaxation per lane-op
-//   APSP_U16  __viaddmin_u16x2          two relaxations per lane-op
-//   APSP_F32  fminf(a + b, c)           one relaxation per lane-op (two instructions)
+//   APSP_I32  __viaddmin_s32: one relaxation per 32-bit lane-op
+//   APSP_U16  __viaddmin_u16x2: two relaxations per 32-bit lane-op
+//   APSP_F32  the Phase-3 tile's form: two k-steps at a time, the sums of two
+//             neighbouring columns by one packed pair add (add.rn.f32x2) and
+//             each output's two sums taken by one three-input minimum
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -20,6 +23,12 @@ namespace {
 
 constexpr int kChains = 16;  // independent add-min chains per thread
 
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+  float d;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
 template <int DT>
 __device__ __forceinline__ uint32_t addmin_op(uint32_t a, uint32_t b, uint32_t c) {
   if constexpr (DT == APSP_I32) return (uint32_t)__viaddmin_s32((int)a, (int)b, (int)c);
@@ -28,7 +37,12 @@ __device__ __forceinline__ uint32_t addmin_op(uint32_t a, uint32_t b, uint32_t c
 }
 
 // kChains independent chains per thread: c_j <- addmin(c_j, a_j, c_{j+1}); the
-// slowest CTA's clock64 span gives lane-ops per clock per SM.
+// slowest CTA's clock64 span gives lane-ops per clock per SM.  fp32: kChains
+// accumulators as 2 rows x 8 columns of a tile, two k-steps per iteration:
+// the row values (taken from the accumulators, so that nothing is
+// loop-invariant) duplicated into packed pairs, added to the columns' packed
+// pairs, and each accumulator lowered by its two sums with one three-input
+// minimum -- 2 kChains relaxations per iteration.
 template <int DT>
 __global__ void addmin_rate_kernel(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int iters,
                                    unsigned long long *__restrict__ cycles) {
@@ -40,12 +54,41 @@ __global__ void addmin_rate_kernel(const uint32_t *__restrict__ in, uint32_t *__
     a[j] = in[(3 * t + j) & 1023];
   }
   const unsigned long long t0 = clock64();
-  for (int it = 0; it < iters; ++it) {
-    uint32_t nx[kChains];
+  if constexpr (DT == APSP_F32) {
+    uint64_t bp[2][4];  // the columns' values, packed in neighbouring pairs, for two k-steps
 #pragma unroll
-    for (int j = 0; j < kChains; ++j) nx[j] = addmin_op<DT>(a[j], c[j], c[(j + 1) % kChains]);
+    for (int k = 0; k < 2; ++k)
 #pragma unroll
-    for (int j = 0; j < kChains; ++j) c[j] = nx[j];
+      for (int p = 0; p < 4; ++p) bp[k][p] = (uint64_t)a[8 * k + 2 * p] | ((uint64_t)a[8 * k + 2 * p + 1] << 32);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        uint64_t ad[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+          asm("mov.b64 %0, {%1, %1};" : "=l"(ad[k]) : "r"(c[(8 * r + 8 + k) % kChains]));
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          uint64_t s0, s1;
+          asm("add.rn.f32x2 %0, %1, %2;" : "=l"(s0) : "l"(ad[0]), "l"(bp[0][p]));
+          asm("add.rn.f32x2 %0, %1, %2;" : "=l"(s1) : "l"(ad[1]), "l"(bp[1][p]));
+          float x0, y0, x1, y1;
+          asm("mov.b64 {%0, %1}, %2;" : "=f"(x0), "=f"(y0) : "l"(s0));
+          asm("mov.b64 {%0, %1}, %2;" : "=f"(x1), "=f"(y1) : "l"(s1));
+          const int j = 8 * r + 2 * p;
+          c[j] = __float_as_uint(min3f(__uint_as_float(c[j]), x0, x1));
+          c[j + 1] = __float_as_uint(min3f(__uint_as_float(c[j + 1]), y0, y1));
+        }
+      }
+    }
+  } else {
+    for (int it = 0; it < iters; ++it) {
+      uint32_t nx[kChains];
+#pragma unroll
+      for (int j = 0; j < kChains; ++j) nx[j] = addmin_op<DT>(a[j], c[j], c[(j + 1) % kChains]);
+#pragma unroll
+      for (int j = 0; j < kChains; ++j) c[j] = nx[j];
+    }
   }
   const unsigned long long t1 = clock64();
   uint32_t s = 0;
@@ -60,6 +103,11 @@ __global__ void addmin_eval_kernel(const uint32_t *a, const uint32_t *b, const u
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
     o[i] = addmin_op<DT>(a[i], b[i], c[i]);
 }
+
+// Relaxations per kernel-iteration step of one chain: 1 per 32-bit lane-op, 2
+// for packed 16-bit and for the fp32 form (two k-steps per accumulator).
+template <int DT>
+constexpr double relax_per_chain_step() { return DT == APSP_I32 ? 1.0 : 2.0; }
 
 template <int DT>
 cudaError_t measure(int sms, uint32_t *din, uint32_t *dout, unsigned long long *dcyc, int grid, int threads,
@@ -85,17 +133,16 @@ cudaError_t measure(int sms, uint32_t *din, uint32_t *dout, unsigned long long *
   if (e1) cudaEventDestroy(e1);
   if (e != cudaSuccess) return e;
   const unsigned long long span = *std::max_element(cyc.begin(), cyc.end());
-  const double ops = (double)grid * threads * iters * kChains;
-  *lanes = span ? ops / sms / (double)span : 0.0;
+  const double relax = (double)grid * threads * iters * kChains * relax_per_chain_step<DT>();
+  *lanes = span ? relax / sms / (double)span : 0.0;
   *ms_out = ms;
   return cudaSuccess;
 }
 
 }  // namespace
 
-extern "C" apsp_status apsp_addmin_peak(int device, int dtype, double *lane_ops_per_clk_per_sm,
-                                        double *relax_per_s) {
-  if (!lane_ops_per_clk_per_sm || !relax_per_s) return APSP_E_INVALID;
+extern "C" apsp_status apsp_addmin_peak(int device, int dtype, double *relax_per_clk_per_sm, double *relax_per_s) {
+  if (!relax_per_clk_per_sm || !relax_per_s) return APSP_E_INVALID;
   if (dtype != APSP_I32 && dtype != APSP_U16 && dtype != APSP_F32) return APSP_E_INVALID;
   if (cudaSetDevice(device) != cudaSuccess) return APSP_E_CUDA;
   int sms = 0;
@@ -103,7 +150,14 @@ extern "C" apsp_status apsp_addmin_peak(int device, int dtype, double *lane_ops_
     return APSP_E_CUDA;
   const int threads = 256, grid = 4 * sms;  // one full wave: 4 CTAs of 256 threads per SM
   std::vector<uint32_t> h(1024);
-  for (int i = 0; i < 1024; ++i) h[i] = (uint32_t)(i * 2654435761u) & 0x00FF00FFu;
+  for (int i = 0; i < 1024; ++i) {
+    if (dtype == APSP_F32) {  // ordinary non-negative floats (distances), not bit patterns of tiny ones
+      const float v = 1.0f + 0.25f * (float)(i % 977);
+      std::memcpy(&h[i], &v, sizeof(v));
+    } else {
+      h[i] = (uint32_t)(i * 2654435761u) & 0x00FF00FFu;
+    }
+  }
   uint32_t *din = nullptr, *dout = nullptr;
   unsigned long long *dcyc = nullptr;
   cudaError_t e = cudaMalloc(&din, 1024 * sizeof(uint32_t));
@@ -120,9 +174,9 @@ extern "C" apsp_status apsp_addmin_peak(int device, int dtype, double *lane_ops_
   if (dout) cudaFree(dout);
   if (dcyc) cudaFree(dcyc);
   if (e != cudaSuccess) return APSP_E_CUDA;
-  const double per_lane = dtype == APSP_U16 ? 2.0 : 1.0;
-  *lane_ops_per_clk_per_sm = lanes;
-  *relax_per_s = ms > 0 ? (double)grid * threads * (double)(1 << 14) * kChains * per_lane / (ms * 1e-3) : 0.0;
+  const double per_step = dtype == APSP_I32 ? 1.0 : 2.0;
+  *relax_per_clk_per_sm = lanes;
+  *relax_per_s = ms > 0 ? (double)grid * threads * (double)(1 << 14) * kChains * per_step / (ms * 1e-3) : 0.0;
   return APSP_OK;
 }
 

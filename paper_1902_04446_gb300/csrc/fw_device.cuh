@@ -279,9 +279,81 @@ struct TileMap {
   __device__ __forceinline__ static int wcol(int tx, int h) { return h == 0 ? tx * 4 : BNW / 2 + tx * 4; }
 };
 
-template <class Op, int BM, int BNW, int BK, int TN = 8>
+// Three-input minimum of fp32 values (sm_100 and later).
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+  float d;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+// fp32 min-plus tile, two k-steps at a time: acc = min(acc, a_t + b_t,
+// a_t+1 + b_t+1) with one three-input minimum, the sums for two neighbouring
+// columns formed by one packed pair add -- the same sums (each rounded to
+// nearest) and the same minimum as one add and one minimum per relaxation,
+// in fewer instructions.
+// U = k-step pairs per unrolled loop trip, chosen per kernel (measured on
+// GB300: every round in one launch 4, the per-round Phase 3 2, the min-plus
+// product 1; their register use and schedules differ).
+template <int BM, int BNW, int BK, int TN, int U>
+__device__ __forceinline__ void tile_minplus_f32(const uint32_t *__restrict__ As, const uint32_t *__restrict__ Bs,
+                                                 uint32_t (&acc)[8][TN], int ty, int tx) {
+  static_assert(BK % 2 == 0, "k-steps in pairs");
+  float f[8][TN];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < TN; ++c) f[r][c] = __uint_as_float(acc[r][c]);
+  constexpr int UNROLL = TN == 8 ? U : 2;
+#pragma unroll UNROLL
+  for (int t = 0; t < BK; t += 2) {
+    float a[2][8];
+    uint64_t b[2][TN / 2];  // neighbouring columns (c, c + 1) as one packed pair
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const uint4 a0 = *reinterpret_cast<const uint4 *>(As + (t + k) * BM + ty * 4);
+      const uint4 a1 = *reinterpret_cast<const uint4 *>(As + (t + k) * BM + BM / 2 + ty * 4);
+      a[k][0] = __uint_as_float(a0.x); a[k][1] = __uint_as_float(a0.y);
+      a[k][2] = __uint_as_float(a0.z); a[k][3] = __uint_as_float(a0.w);
+      a[k][4] = __uint_as_float(a1.x); a[k][5] = __uint_as_float(a1.y);
+      a[k][6] = __uint_as_float(a1.z); a[k][7] = __uint_as_float(a1.w);
+#pragma unroll
+      for (int h = 0; h < TN / 4; ++h) {
+        const ulonglong2 bv =
+            *reinterpret_cast<const ulonglong2 *>(Bs + (t + k) * BNW + (h == 0 ? tx * 4 : BNW / 2 + tx * 4));
+        b[k][2 * h + 0] = bv.x;
+        b[k][2 * h + 1] = bv.y;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      uint64_t ad[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) asm("mov.b64 %0, {%1, %1};" : "=l"(ad[k]) : "f"(a[k][r]));
+#pragma unroll
+      for (int p = 0; p < TN / 2; ++p) {
+        uint64_t s0, s1;
+        asm("add.rn.f32x2 %0, %1, %2;" : "=l"(s0) : "l"(ad[0]), "l"(b[0][p]));
+        asm("add.rn.f32x2 %0, %1, %2;" : "=l"(s1) : "l"(ad[1]), "l"(b[1][p]));
+        float x0, y0, x1, y1;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(x0), "=f"(y0) : "l"(s0));
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(x1), "=f"(y1) : "l"(s1));
+        f[r][2 * p] = fmin3(f[r][2 * p], x0, x1);
+        f[r][2 * p + 1] = fmin3(f[r][2 * p + 1], y0, y1);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < TN; ++c) acc[r][c] = __float_as_uint(f[r][c]);
+}
+
+template <class Op, int BM, int BNW, int BK, int TN = 8, int F32U = 2>
 __device__ __forceinline__ void tile_minplus(const uint32_t *__restrict__ As, const uint32_t *__restrict__ Bs,
                                              uint32_t (&acc)[8][TN], int ty, int tx) {
+  if constexpr (Op::DTYPE == 2) {
+    tile_minplus_f32<BM, BNW, BK, TN, F32U>(As, Bs, acc, ty, tx);
+    return;
+  }
   // deeper unrolling for the 8 x 8 block (fewer loop instructions on the
   // add-min pipe): for the integer ops 16 k-steps per loop trip measured
   // fastest (8: 1.1 % slower on an n = 16384 int32 solve; 32 and 64: 1.5 % and

@@ -1247,7 +1247,7 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
         for (int r = 0; r < 8; ++r)
 #pragma unroll
           for (int c = 0; c < TN; ++c) acc[r][c] = Op::INF_WORD;
-        tile_minplus<Op, BM, BNW, BK, TN>(stA(s), stB(s), acc, ty, tx);
+        tile_minplus<Op, BM, BNW, BK, TN, 4>(stA(s), stB(s), acc, ty, tx);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty_ab[s]);
         const int64_t r0 = (int64_t)cty * BM, c0 = (int64_t)ctx * BNW * Op::EPW;
@@ -1539,7 +1539,7 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
         if (lane == 0) abort_flag = 1;
         break;
       }
-      tile_minplus<Op, BM, BNW, BK, TN>(stA(s), stB(s), acc, ty, tx);
+      tile_minplus<Op, BM, BNW, BK, TN, 1>(stA(s), stB(s), acc, ty, tx);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty_ab[s]);
       if (c != nk - 1) continue;
