@@ -282,10 +282,10 @@ def cpu_baseline(workload: str, n_s: int = 4096, n_full: int | None = None):
     return out
 
 
-def _replay_batched(torch, apsp, device, mats, arrival):
+def _replay_batched(torch, apsp, device, mats, arrival, **cfg):
     """Submits request i at arrival[i] (seconds from start) and polls to completion."""
     nreq = len(mats)
-    with apsp.Handle(device=device) as h:
+    with apsp.Handle(device=device, **cfg) as h:
         for W in mats[:8]:  # warm-up
             t = h.submit(W)
             h.wait(t)
@@ -335,7 +335,7 @@ def _replay_single(torch, apsp, device, mats, arrival):
         return lat, time.perf_counter() - t_start
 
 
-def serving_replay(torch, apsp, device, nreq):
+def serving_replay(torch, apsp, device, nreq, **cfg):
     """The Poisson trace through the request loop (continuous batching into the
     batched persistent kernel) and through one-at-a-time solves; then the same
     requests all submitted at once (saturation throughput)."""
@@ -362,10 +362,10 @@ def serving_replay(torch, apsp, device, nreq):
     out = {"requests": nreq, "offered_req_per_s": 200.0,
            "n": "log-uniform [128, 4096], ER avg degree 16 + spanning path, int32 weights U{1..1000}",
            "inputs": "adjacency matrices resident on the device at arrival"}
-    out["batched"] = summary(*_replay_batched(torch, apsp, device, mats, arrival))
+    out["batched"] = summary(*_replay_batched(torch, apsp, device, mats, arrival, **cfg))
     out["one_at_a_time"] = summary(*_replay_single(torch, apsp, device, mats, arrival))
     zero = np.zeros_like(arrival)
-    sat_b = summary(*_replay_batched(torch, apsp, device, mats, zero))
+    sat_b = summary(*_replay_batched(torch, apsp, device, mats, zero, **cfg))
     sat_s = summary(*_replay_single(torch, apsp, device, mats, zero))
     out["saturated"] = {"batched_solves_per_s": sat_b["solves_per_s"], "one_at_a_time_solves_per_s":
                         sat_s["solves_per_s"], "batched_grelax_per_s": sat_b["grelax_per_s"],
@@ -532,6 +532,41 @@ def run_gpu(args):
                              "phase3_achieved": a16, "phase3_peak": 2 * peak,
                              "phase3_frac": (a16 / (2 * peak)) if a16 else None, "gpu_launches": int(l16),
                              "bytes_per_distance": 2}
+
+    # ---- the same graph in upper-triangular storage (half the bytes): edge list -> storage -> rounds, fewer
+    # repeats (each step rebuilds the matrix from the edge list, as the dense path's step copies W in)
+    if not args.no_variants:
+        reps = min(args.steps, 2)
+        src = torch.from_numpy(g.src.astype(np.int32)).to(device)
+        dst = torch.from_numpy(g.dst.astype(np.int32)).to(device)
+        ww = torch.from_numpy(g.w.astype(np.int32)).to(device)
+        rows_, ld_, tbytes = apsp.tri_layout("int32", n)
+        T = apsp.tri_empty("int32", n, device)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(1):
+            h.tri_from_edges("int32", src, dst, ww, n, T)
+            h.solve_tri("int32", T, n)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            h.tri_from_edges("int32", src, dst, ww, n, T)
+            h.solve_tri("int32", T, n)
+        e1.record()
+        torch.cuda.synchronize()
+        if h.last_status() != 0:
+            raise RuntimeError("upper-triangular solve: input check or bounded wait failed")
+        mst = e0.elapsed_time(e1)
+        pick = torch.linspace(0, n - 1, 16, dtype=torch.long, device=Dd.device)
+        if not torch.equal(apsp.tri_rows("int32", T, n, pick), Dd[pick]):
+            raise RuntimeError("upper-triangular result differs from the dense solve")
+        vt, mst = job_value(torch, dist, relax_step * reps, mst)
+        out["upper_triangular_int32"] = {
+            "value": vt, "unit": UNIT, "ms_per_step": mst / reps, "repeats": reps,
+            "storage_bytes": tbytes, "dense_storage_bytes": n * n * 4, "storage_ratio": tbytes / (n * n * 4),
+            "path": "apsp_tri_from_edges + apsp_solve_tri: only the super-tiles (I <= J) stored, folded into one "
+                    "rectangle; rows checked against the dense solve"}
+        del T, src, dst, ww
+        torch.cuda.empty_cache()
 
     # ---- end to end through host buffers, same graph and steps
     mse, nbytes = e2e_measure(torch, h, Wd, Dd, args.steps, args.warmup, dist)
@@ -725,7 +760,11 @@ def run_round_shapes(args):
 
     import paper_1902_04446_gb300 as apsp
 
-    g = load_graph(args.workload)
+    if args.er_n:
+        s_, d_, w_ = gen.er_graph(args.er_n, args.er_n)
+        g = gen.graphs.Graph(f"er n={args.er_n}", args.er_n, s_, d_, w_, "int32")
+    else:
+        g = load_graph(args.workload)
     n = g.n
     Wd = dense_on_device(torch, g, torch.int32, 1073741823, 0)
     if args.dtype == "u16":
@@ -748,7 +787,8 @@ def run_round_shapes(args):
             status = h.last_status()
         ms /= args.steps
         n3, ms3, r3 = prof[3]
-        print(json.dumps({"workload": args.workload, "dtype": args.dtype, "round_width": bk, "phase3_variant": v,
+        print(json.dumps({"workload": g.name if args.er_n else args.workload, "n": n, "dtype": args.dtype,
+                          "round_width": bk, "phase3_variant": v,
                           "phase3_kernel": names[v], "ms_per_solve": round(ms, 2),
                           "grelax_per_s": float(n) ** 3 / (ms / 1e3) / 1e9,
                           "phase_ms": {f"phase{p}": round(prof[p][1] / args.steps, 2) for p in (1, 2, 3)},
@@ -774,6 +814,9 @@ def main(argv=None):
                     help="--round-shapes: the element type solved (u16 from the int32 matrix, INF -> 0x7FFF)")
     ap.add_argument("--shapes", default="",
                     help="--round-shapes: comma-separated BKxVARIANT list (e.g. 64x4,64x5); default all ten")
+    ap.add_argument("--er-n", type=int, default=0,
+                    help="--round-shapes: an Erdos-Renyi graph of this n (average degree 16 plus a spanning path, "
+                         "seed n, weights U{1..1000}) instead of --workload")
     ap.add_argument("--cpu-sweep", action="store_true",
                     help="time the CPU oracle at several n (and the Dijkstra verifier) instead of the benchmark line")
     ap.add_argument("--cpu-sweep-sizes", default="256,512,1024,2048,4096",

@@ -80,8 +80,8 @@ typedef struct {
   int queue_depth;       /* serving: pending requests before APSP_E_BUSY (default 4096) */
   int64_t memory_budget; /* serving: bytes of device memory for admitted requests (0 = free HBM - reserve) */
   int64_t spin_limit;    /* bounded device waits: iterations before APSP_E_TIMEOUT (0 = default) */
-  int phase3_variant;    /* Phase-3 kernel: 0 = tuned, else by n and dtype (5 for 3072 <= n < 24576,
-                            or < 49152 for packed 16-bit; 4 otherwise), 1 = one
+  int phase3_variant;    /* Phase-3 kernel: 0 = tuned, else by n and dtype (5 for 5120 <= n < 24576,
+                            7168 <= n < 49152 for packed 16-bit; 4 otherwise), 1 = one
                             CTA per tile, 2 = persistent TMA kernel with 256 threads, 3 = persistent TMA
                             kernel with 512 threads, 4 = warp-specialized persistent kernel (TMA producer
                             warp; int32 results leave by a TMA min-reduction), one launch per round,
@@ -93,6 +93,11 @@ typedef struct {
                             half the relaxations.  0 = use it when a device check finds W symmetric
                             (one stream synchronization per solve), 1 = the caller guarantees W is
                             symmetric, 2 = never.  Edge-list solves are symmetric by construction. */
+  int64_t serving_large_n; /* serving: a request with n >= this runs alone in its own group on the per-round
+                              kernels; smaller ones share the batched persistent kernel (0 = default 1536) */
+  int serving_large_grid;  /* serving: CTAs of a large request's persistent Phase-3 kernel (0 = one per SM, one
+                              launch per round); a smaller grid lets several large requests run side by side on
+                              disjoint SMs, and then every round of a request runs in one launch */
 } apsp_config;
 
 /* Fills *cfg with the defaults (library plumbing; no paper counterpart). */

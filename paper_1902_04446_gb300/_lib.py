@@ -27,7 +27,7 @@ class apsp_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("dtype", ctypes.c_int), ("block_k", ctypes.c_int),
                 ("max_batch", ctypes.c_int), ("queue_depth", ctypes.c_int),
                 ("memory_budget", ctypes.c_int64), ("spin_limit", ctypes.c_int64), ("phase3_variant", ctypes.c_int),
-                ("symmetric", ctypes.c_int)]
+                ("symmetric", ctypes.c_int), ("serving_large_n", ctypes.c_int64), ("serving_large_grid", ctypes.c_int)]
 
 
 class apsp_request(ctypes.Structure):

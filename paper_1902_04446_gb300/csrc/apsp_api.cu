@@ -411,6 +411,7 @@ apsp_status apsp_create(apsp_handle **out, const apsp_config *cfg) {
   if (c.block_k != 0 && c.block_k != 32 && c.block_k != 64) return APSP_E_INVALID;
   if (c.phase3_variant < 0 || c.phase3_variant > 5) return APSP_E_INVALID;
   if (c.symmetric < 0 || c.symmetric > 2) return APSP_E_INVALID;
+  if (c.serving_large_n < 0 || c.serving_large_grid < 0) return APSP_E_INVALID;
   if (c.max_batch <= 0) c.max_batch = 64;
   if (c.queue_depth <= 0) c.queue_depth = 4096;
   int ndev = 0;
@@ -424,6 +425,11 @@ apsp_status apsp_create(apsp_handle **out, const apsp_config *cfg) {
     if (cudaDeviceGetDefaultMemPool(&pool, c.device) == cudaSuccess) {
       uint64_t keep = UINT64_MAX;
       cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      // memory freed on one group's stream is not handed to another group by
+      // making that group's stream wait for the first (which would chain
+      // independent requests one after another)
+      int no = 0;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
     }
   }
   if (cudaMalloc(&h->d_status, 64) != cudaSuccess) return APSP_E_CUDA;
@@ -1155,19 +1161,35 @@ apsp_status apsp_profile_read(apsp_handle *h, int64_t launches[3], double ms[3],
 namespace {
 
 constexpr int kMaxGroupsInFlight = 16;
-// A request this large fills the GPU by itself: it gets its own group and
-// the per-round kernels (persistent TMA Phase 3) instead of the batched kernel.
+// Default size from which a request gets its own group and the per-round
+// kernels (persistent TMA Phase 3) instead of the batched kernel
+// (apsp_config.serving_large_n).
 constexpr int64_t kLargeN = 1536;
+int64_t large_n(const apsp_handle *h) { return h->cfg.serving_large_n > 0 ? h->cfg.serving_large_n : kLargeN; }
 
 int64_t panel_bytes(int64_t n) { return 64 * apsp::batch_panel_ld(n) * 4 + 256; }
 
-// Workspace of a large request's own group beyond panel_bytes: the per-round
-// panel buffer, and for APSP_AUTO the element panel and the packed 16-bit copy.
-int64_t large_extra_bytes(const apsp_request &q) {
+// Round shape of a large request: with the whole GPU (serving_large_grid 0)
+// one launch per round, so that the batched groups on other streams keep
+// running between its rounds; with a capped grid every round in one launch
+// (the cap leaves SMs to the other groups).
+apsp::RoundConfig large_round_config(apsp_handle *h, int dtype, int64_t n) {
+  apsp::RoundConfig rc = config_for(h, dtype, n);
+  rc.grid_cap = h->cfg.serving_large_grid;
+  if (rc.p3 == 4 && rc.grid_cap == 0) rc.p3 = 3;
+  if (rc.grid_cap > 0 && rc.bk == 64 && rc.p3 >= 3) rc.p3 = 4;
+  return rc;
+}
+
+// Workspace of a large request's own group beyond panel_bytes: the panel
+// buffer (doubled, with counters, when every round runs in one launch), and for
+// APSP_AUTO the element panel and the packed 16-bit copy.
+int64_t large_extra_bytes(apsp_handle *h, const apsp_request &q) {
   const int64_t ldT = panel_ld(q.n);
-  int64_t b = (int64_t)apsp::panel_buffer_bytes(q.n, ldT, false);
+  const bool all = h->cfg.serving_large_grid > 0;
+  int64_t b = (int64_t)apsp::panel_buffer_bytes(q.n, ldT, all);
   if (q.dtype == APSP_AUTO)
-    b += 256 + (int64_t)apsp::row_panel_bytes(ldT, false) + q.n * round_up(q.n, 8) * 2;
+    b += 512 + (int64_t)apsp::row_panel_bytes(ldT, all) + q.n * round_up(q.n, 8) * 2;
   return b;
 }
 
@@ -1265,7 +1287,9 @@ apsp_status admit_group_steps(apsp_handle *h, const std::vector<Request *> &rs, 
       cudaEventRecord(g->copy_ev, s) != cudaSuccess)
     return APSP_E_CUDA;
   g->copy_recorded = true;
-  const size_t sbytes = (rs.size() + 1) * sizeof(int);
+  // [i] input checks of request i, [count] kernel errors, [count + 1] a large
+  // request's symmetry flag
+  const size_t sbytes = (rs.size() + 2) * sizeof(int);
   if (cudaMallocAsync((void **)&g->status, sbytes, s) != cudaSuccess) {
     g->status = nullptr;
     return APSP_E_CUDA;
@@ -1277,7 +1301,7 @@ apsp_status admit_group_steps(apsp_handle *h, const std::vector<Request *> &rs, 
     if (rn > 0 && apsp::launch_ingest(APSP_I32, rs[i]->D, rs[i]->D, rn, rn, g->status + i, s, &l) != cudaSuccess)
       return APSP_E_CUDA;
   }
-  if (rs.size() == 1 && rs[0]->req.n >= kLargeN) {
+  if (rs.size() == 1 && rs[0]->req.n >= large_n(h)) {
     // one large graph: per-round kernels on the group's stream; an undirected
     // (symmetric) matrix takes the symmetric mode, decided by a device check
     const int64_t rn = rs[0]->req.n;
@@ -1291,19 +1315,20 @@ apsp_status admit_group_steps(apsp_handle *h, const std::vector<Request *> &rs, 
                                  std::max<int64_t>(kDefaultMaxEdges, 32 * rn), s, &bound, &ok, &l) != cudaSuccess)
         return APSP_E_CUDA;
       if (ok) {
-        apsp::RoundConfig rc = config_for(h, APSP_U16, rn);
-        if (rc.p3 == 4) rc.p3 = 3;
+        apsp::RoundConfig rc = large_round_config(h, APSP_U16, rn);
         rc.sym = true;  // the bound accepts only a symmetric W
         const int64_t ld16 = round_up(rn, 8);
-        const size_t pb = (apsp::panel_buffer_bytes(rn, ldT, false) + 255) & ~size_t(255);
+        const bool all = rc.p3 == 4;
+        const size_t pb = (apsp::panel_buffer_bytes(rn, ldT, all) + 255) & ~size_t(255);
         const size_t pbytes = (size_t)rn * ld16 * 2;
-        if (cudaMallocAsync(&g->ws, pb + apsp::row_panel_bytes(ldT, false) + pbytes, s) != cudaSuccess) {
+        const size_t rpb = (apsp::row_panel_bytes(ldT, all) + 255) & ~size_t(255);
+        if (cudaMallocAsync(&g->ws, pb + rpb + pbytes, s) != cudaSuccess) {
           g->ws = nullptr;
           return APSP_E_CUDA;
         }
         char *wsb = static_cast<char *>(g->ws);
         rc.rowP = wsb + pb;
-        uint16_t *P = reinterpret_cast<uint16_t *>(wsb + pb + apsp::row_panel_bytes(ldT, false));
+        uint16_t *P = reinterpret_cast<uint16_t *>(wsb + pb + rpb);
         int32_t *Dr = static_cast<int32_t *>(rs[0]->D);
         if (apsp::launch_pack(Dr, rn, P, ld16, rn, s, &l) != cudaSuccess ||
             apsp::launch_rounds(APSP_U16, P, ld16, rn, g->ws, ldT, s, &l, nullptr, rc, g->status + 1) !=
@@ -1316,25 +1341,26 @@ apsp_status admit_group_steps(apsp_handle *h, const std::vector<Request *> &rs, 
         return APSP_OK;
       }
     }
-    apsp::RoundConfig rc = config_for(h, APSP_I32, rn);
-    // one launch per round here, so that the batched groups on other streams
-    // keep running between this request's rounds
-    if (rc.p3 == 4) rc.p3 = 3;
-    if (cudaMallocAsync(&g->ws, apsp::panel_buffer_bytes(rn, ldT, false), s) != cudaSuccess) {
+    apsp::RoundConfig rc = large_round_config(h, APSP_I32, rn);
+    if (cudaMallocAsync(&g->ws, apsp::panel_buffer_bytes(rn, ldT, rc.p3 == 4), s) != cudaSuccess) {
       g->ws = nullptr;
       return APSP_E_CUDA;
     }
-    if (h->cfg.symmetric != 2) {
-      int flag = 0;
-      int *dflag = g->status + 1;  // reused below as the wait-error word (reset first)
-      if (h->cfg.symmetric == 1) {
-        rc.sym = true;
-      } else if (apsp::launch_symmetry_check(APSP_I32, rs[0]->D, rn, rn, dflag, s) == cudaSuccess &&
-                 cudaMemcpyAsync(&flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
-                 cudaStreamSynchronize(s) == cudaSuccess) {
+    if (h->cfg.symmetric == 1) {
+      rc.sym = true;
+    } else if (h->cfg.symmetric == 0) {
+      int *dflag = g->status + 2;  // zeroed with the status words
+      if (apsp::launch_symmetry_check(APSP_I32, rs[0]->D, rn, rn, dflag, s) != cudaSuccess) return APSP_E_CUDA;
+      if (apsp::single_launch(APSP_I32, rs[0]->D, rn, rn, rc)) {
+        rc.sym_flag = dflag;  // every round in one launch: the kernel reads the answer itself
+      } else {
+        // one launch per round: the answer is read back before the rounds are enqueued
+        int flag = 0;
+        if (cudaMemcpyAsync(&flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+          return APSP_E_CUDA;
         rc.sym = flag == 0;
       }
-      if (cudaMemsetAsync(dflag, 0, sizeof(int), s) != cudaSuccess) return APSP_E_CUDA;
     }
     if (apsp::launch_rounds(APSP_I32, rs[0]->D, rn, rn, g->ws, ldT, s, &l, nullptr, rc, g->status + 1) !=
         cudaSuccess)
@@ -1378,9 +1404,9 @@ void worker_loop(apsp_handle *h) {
       int64_t add = 0;
       while (!h->queue.empty() && (int)rs.size() < h->cfg.max_batch) {
         Request *r = h->reqs[h->queue.front()].get();
-        const bool large = r->req.n >= kLargeN;
+        const bool large = r->req.n >= large_n(h);
         if (large && !rs.empty()) break;  // a large request starts its own group
-        const int64_t b = r->bytes + panel_bytes(r->req.n) + (large ? large_extra_bytes(r->req) : 0);
+        const int64_t b = r->bytes + panel_bytes(r->req.n) + (large ? large_extra_bytes(h, r->req) : 0);
         if (h->used + add + b > h->budget) break;  // wait for memory to free up
         h->queue.pop_front();
         r->transient = b - r->bytes;

@@ -1889,8 +1889,10 @@ static inline unsigned grid_cols(int64_t n, int threads) {
 template <class Op, int BK>
 static cudaError_t rounds_impl(void *Dv, Layout L, int64_t n, void *colTv, int64_t ldT, bool vec, int variant,
                                cudaStream_t s, int64_t *launches, PhaseTimer *tm, int *wait_err, bool sym,
-                               void *rowPv, const int *sym_flag, const int *gate, uint32_t dep_spins) {
+                               void *rowPv, const int *sym_flag, const int *gate, uint32_t dep_spins,
+                               int grid_cap) {
   const bool use_tma = variant != 0;
+  const int sms = grid_cap > 0 ? std::min(sm_count(), grid_cap) : sm_count();
   using Elem = typename Op::elem;
   using E = Elem;
   E *D = static_cast<E *>(Dv);
@@ -1985,7 +1987,7 @@ static cudaError_t rounds_impl(void *Dv, Layout L, int64_t n, void *colTv, int64
     tiles_total = 0;
     for (int y = 0; y < tiles_y; ++y) tiles_total += tiles_x - std::min(tiles_x, y / Op::EPW);
   }
-  const int grid_tma = std::min(sm_count(), tiles_total);
+  const int grid_tma = std::min(sms, tiles_total);
   const int nrow = (int)((n + C2::ROW_BNW * Op::EPW - 1) / (C2::ROW_BNW * Op::EPW));
   const int ncol = (int)((n + C2::COL_BM - 1) / C2::COL_BM);
   const dim3 g3((unsigned)((n + C3::BNW * Op::EPW - 1) / (C3::BNW * Op::EPW)), (unsigned)((n + C3::BM - 1) / C3::BM));
@@ -2064,7 +2066,7 @@ static cudaError_t rounds_impl(void *Dv, Layout L, int64_t n, void *colTv, int64
     constexpr bool RED = kRedOp<Op>;
     int tiles_sym = 0;  // tiles with tx >= ty / EPW
     for (int y = 0; y < tiles_y; ++y) tiles_sym += tiles_x - std::min(tiles_x, y / Op::EPW);
-    const int grid = std::min(sm_count(), tiles_sym);  // one launch grid for either mode
+    const int grid = std::min(sms, tiles_sym);  // one launch grid for either mode
     char *cbase = reinterpret_cast<char *>(colT) + lookahead_counter_offset(ldT);
     double work[2] = {0.0, 0.0};
     auto plan = [&](bool msym) {
@@ -2142,10 +2144,10 @@ static cudaError_t rounds_bk(const RoundConfig &cfg, void *D, Layout L, int64_t 
   const bool vec = aligned16(D, L.ld, sizeof(typename Op::elem));
   if (cfg.bk == 32)
     return rounds_impl<Op, 32>(D, L, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err, cfg.sym, cfg.rowP,
-                               cfg.sym_flag, cfg.gate, cfg.dep_spins);
+                               cfg.sym_flag, cfg.gate, cfg.dep_spins, cfg.grid_cap);
   if (cfg.bk == 64)
     return rounds_impl<Op, 64>(D, L, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err, cfg.sym, cfg.rowP,
-                               cfg.sym_flag, cfg.gate, cfg.dep_spins);
+                               cfg.sym_flag, cfg.gate, cfg.dep_spins, cfg.grid_cap);
   return cudaErrorInvalidValue;
 }
 

@@ -46,22 +46,27 @@ struct RoundConfig {
   const int *sym_flag = nullptr;
   const int *gate = nullptr;  // kernel 4 only: round 0's Phase 1 also waits for *gate >= 1
   uint32_t dep_spins = 0;     // kernel 4 only: limit of each wait on another work item (0 = default)
+  int grid_cap = 0;           // persistent Phase-3 kernels: at most this many CTAs (0 = one per SM), so that
+                              // solves on other streams can run on the remaining SMs
 };
 // Whether launch_rounds would run every round in one launch for this call
 // (kernel 4 with round width 64, a 16-byte addressable D and more than one round).
 bool single_launch(int dtype, const void *D, int64_t ld, int64_t n, const RoundConfig &cfg);
 // The default Phase-3 kernel for (n, dtype) when nothing was tuned: every round
-// in one launch for mid-size n, one launch per round below and above (timed
-// per n and dtype on GB300 with bench.py --round-shapes).  Below n = 3072 a round is about one
-// wave of tiles and the launches are cheaper than the single launch's item
-// scheduling; for large n the per-round launches' fixed cost per round is
-// small against the single launch's cost per tile.  Measured crossovers: int32
-// single launch faster at n = 8192, equal at 16384, slower at 32768 and 65536;
-// packed 16-bit (half the tiles per round) faster up to 32768, slower at
-// 65536.  The cuts sit between those points.
+// in one launch for mid-size n, one launch per round below and above (timed per
+// n and dtype on GB300).  Below the lower cut a round is at most a few waves of
+// tiles and the per-round launches are cheaper than the single launch's item
+// scheduling; above the upper cut the per-round launches' fixed cost per round
+// is small against the single launch's cost per tile.  Measured (symmetric
+// mode, ms per solve, one launch per round / single launch): int32 n = 4096
+// 4.53 / 4.95, 5120 7.04 / 6.81, 8192 20.6 / 16.5, 16384 128.4 / 125.6, 32768
+// 954 / 975; packed 16-bit n = 6144 7.56 / 7.61, 7168 10.64 / 9.63, 65536 3922
+// / 3983 (its rounds have half the tiles); fp32 n = 4096 4.41 / 4.97, 5120
+// 6.87 / 6.75.
 inline int default_phase3(int64_t n, int dtype) {
+  const int64_t lo = dtype == 1 ? 7168 : 5120;
   const int64_t hi = dtype == 1 ? 49152 : 24576;
-  return n >= 3072 && n < hi ? 4 : 3;
+  return n >= lo && n < hi ? 4 : 3;
 }
 
 // flag |= 1 when D (n x n, leading dimension ld) is not symmetric.

@@ -110,7 +110,7 @@ class Handle:
 
     def __init__(self, device: int = 0, dtype="int32", max_batch: int = 64, queue_depth: int = 4096,
                  memory_budget: int = 0, spin_limit: int = 0, block_k: int = 0, phase3_variant: int = 0,
-                 symmetric: int = 0):
+                 symmetric: int = 0, serving_large_n: int = 0, serving_large_grid: int = 0):
         cfg = apsp_config()
         _L().apsp_config_default(ctypes.byref(cfg))
         cfg.device = device
@@ -122,6 +122,8 @@ class Handle:
         cfg.block_k = block_k
         cfg.phase3_variant = phase3_variant
         cfg.symmetric = symmetric
+        cfg.serving_large_n = serving_large_n
+        cfg.serving_large_grid = serving_large_grid
         h = ctypes.c_void_p()
         st = _L().apsp_create(ctypes.byref(h), ctypes.byref(cfg))
         if st != 0:
