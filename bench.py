@@ -448,6 +448,53 @@ def e2e_measure(torch, h, Wd, Dd, steps, warmup, dist):
     return wall * 1e3, nbytes
 
 
+def serving_breakdown(torch, apsp, device, nreq=2000):
+    """Where the serving trace's GPU time goes (one JSON line, not the contract line): its matrices solved back to
+    back on one stream (all, the n >= 1536 ones, the smaller ones), the smaller ones in batched launches of 64,
+    and all of them spread over four streams."""
+    arrival, ns, seeds = gen.serving_trace(num=nreq)
+    mats = []
+    for sd in seeds:
+        r = gen.graphs.serving_request(int(sd))
+        mats.append(dense_on_device(torch, gen.graphs.Graph("req", r.n, r.src, r.dst, r.w, "int32"), torch.int32,
+                                    apsp.INF_I32, device))
+    outs = [torch.empty_like(W) for W in mats]
+    ns = np.array([W.shape[0] for W in mats])
+    big = [i for i in range(nreq) if ns[i] >= 1536]
+    small = [i for i in range(nreq) if ns[i] < 1536]
+    res = {"requests": nreq, "n_ge_1536": len(big), "n_lt_1536": len(small),
+           "relax_share_n_ge_1536": float(np.sum(ns[big].astype(float) ** 3) / np.sum(ns.astype(float) ** 3))}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    with apsp.Handle(device=device) as h:
+        for i in range(20):
+            h.solve_t("int32", mats[i], outs[i])
+        res["one_stream_all_s"] = timed(lambda: [h.solve_t("int32", mats[i], outs[i]) for i in range(nreq)])
+        res["one_stream_n_ge_1536_s"] = timed(lambda: [h.solve_t("int32", mats[i], outs[i]) for i in big])
+        res["one_stream_n_lt_1536_s"] = timed(lambda: [h.solve_t("int32", mats[i], outs[i]) for i in small])
+        res["batched_64_n_lt_1536_s"] = timed(
+            lambda: [h.solve_batch([mats[i] for i in small[k:k + 64]], [outs[i] for i in small[k:k + 64]])
+                     for k in range(0, len(small), 64)])
+    hs = [apsp.Handle(device=device) for _ in range(4)]
+    sts = [torch.cuda.Stream(device) for _ in range(4)]
+    t0 = time.perf_counter()
+    for i in range(nreq):
+        hs[i % 4].solve_t("int32", mats[i], outs[i], stream=sts[i % 4])
+    torch.cuda.synchronize()
+    res["four_streams_all_s"] = time.perf_counter() - t0
+    for h in hs:
+        h.close()
+    print(json.dumps({"serving_breakdown": res}), flush=True)
+
+
 def run_gpu(args):
     import torch
 
@@ -823,8 +870,15 @@ def main(argv=None):
                     help="--cpu-sweep: comma-separated n to time the oracle at (16384 takes about 6 minutes)")
     ap.add_argument("--addmin-peak", action="store_true",
                     help="print the add-min issue rate of each dtype measured on this GPU (apsp_addmin_peak) and exit")
+    ap.add_argument("--serving-breakdown", action="store_true",
+                    help="print where the serving trace's GPU time goes (solves back to back, batched, four streams)")
     args = ap.parse_args(argv)
-    if args.addmin_peak:
+    if args.serving_breakdown:
+        import torch
+
+        import paper_1902_04446_gb300 as apsp
+        serving_breakdown(torch, apsp, 0, args.serving_requests)
+    elif args.addmin_peak:
         import torch
 
         import paper_1902_04446_gb300 as apsp
