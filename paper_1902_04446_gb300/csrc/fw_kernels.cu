@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <utility>
 
 #include <cudaTypedefs.h>
 
@@ -45,6 +46,8 @@ template <class Op, int BK>
 __global__ void __launch_bounds__(P1_THREADS) fw_phase1(typename Op::elem *__restrict__ D, Layout L, int64_t n,
                                                         int64_t p0, uint32_t *__restrict__ colT, int64_t ldT) {
   __shared__ P1Smem<Op, BK> s;
+  pdl_trigger();
+  pdl_wait();
   phase1_body<Op, BK, P1_THREADS, false>(D, L, n, p0, colT, ldT, s, threadIdx.x);
 }
 
@@ -82,6 +85,8 @@ __global__ void __launch_bounds__(P2Cfg<Op, BK>::THREADS)
   using C = P2Cfg<Op, BK>;
   extern __shared__ __align__(16) uint32_t smem[];
   const SymPanel<Op> *spp = sym ? &sp : nullptr;
+  pdl_trigger();
+  pdl_wait();
   if ((int)blockIdx.x < nrow_ctas)
     p2_row_task<Op, BK, C::ROW_BNW, C::THREADS, false, C::TN>(
         D, L, n, p0, p1, colT, ldT, (int64_t)(row_chunk0 + (int)blockIdx.x) * C::ROW_BNW * Op::EPW, vec, smem,
@@ -102,6 +107,8 @@ template <class Op>
 __global__ void panel_finalize(typename Op::elem *__restrict__ D, Layout L, int64_t n, int64_t p0,
                                const uint32_t *__restrict__ colT, int64_t ldT, typename Op::elem *__restrict__ rowP,
                                int64_t band_start) {
+  pdl_trigger();
+  pdl_wait();
   const int t = blockIdx.y;
   const int64_t row = p0 + t;
   const int64_t x0 = rowP ? 0 : band_start;  // without an element panel only the band is needed
@@ -119,6 +126,8 @@ __global__ void __launch_bounds__(P1_THREADS) fw_phase1_sym(typename Op::elem *_
                                                             int64_t p0, uint32_t *__restrict__ colT, int64_t ldT,
                                                             typename Op::elem *rowP) {
   __shared__ P1Smem<Op, BK> s;
+  pdl_trigger();
+  pdl_wait();
   phase1_body<Op, BK, P1_THREADS, false>(D, L, n, p0, colT, ldT, s, threadIdx.x, rowP);
 }
 
@@ -432,6 +441,7 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
   const int per = tiles_total / (int)gridDim.x, extra = tiles_total % (int)gridDim.x;
   const int t_begin = (int)blockIdx.x * per + min((int)blockIdx.x, extra);
   const int t_end = t_begin + per + ((int)blockIdx.x < extra ? 1 : 0);
+  pdl_trigger();
   if (t_begin >= t_end) return;
   if (tid == 0) {
     for (int i = 0; i < 2; ++i) {
@@ -448,6 +458,7 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
     abort_flag = 0;
   }
   __syncthreads();
+  pdl_wait();  // the round's panels (previous launches) are complete from here on
 
   // first tile of this CTA and the row-major step over the (symmetric) tile set
   int ty0, tx0;
@@ -1886,6 +1897,24 @@ static inline unsigned grid_cols(int64_t n, int threads) {
   return (unsigned)(g < 1 ? 1 : (g > 64 ? 64 : g));
 }
 
+// Launches kernel k on s with programmatic dependent launch (see pdl_trigger /
+// pdl_wait): the per-round kernels' launch latency overlaps the previous
+// kernel instead of adding to every round.
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);  // errors surface in cudaGetLastError
+}
+
 template <class Op, int BK>
 static cudaError_t rounds_impl(void *Dv, Layout L, int64_t n, void *colTv, int64_t ldT, bool vec, int variant,
                                cudaStream_t s, int64_t *launches, PhaseTimer *tm, int *wait_err, bool sym,
@@ -2002,9 +2031,9 @@ static cudaError_t rounds_impl(void *Dv, Layout L, int64_t n, void *colTv, int64
     const double w = (double)(p1 - p0), rest = (double)(n - (p1 - p0));
     if (tm) tm->before(0, s);
     if (sym && rP)
-      fw_phase1_sym<Op, BK><<<1, P1_THREADS, 0, s>>>(D, L, n, p0, cT, ldT, rP);
+      launch_pdl(fw_phase1_sym<Op, BK>, dim3(1), dim3(P1_THREADS), 0, s, D, L, n, p0, cT, ldT, rP);
     else
-      fw_phase1<Op, BK><<<1, P1_THREADS, 0, s>>>(D, L, n, p0, cT, ldT);
+      launch_pdl(fw_phase1<Op, BK>, dim3(1), dim3(P1_THREADS), 0, s, D, L, n, p0, cT, ldT);
     if (launches) *launches += 1;
     if (tm) tm->after(0, s, w * w * w);
     if (q == 1) return;
@@ -2017,8 +2046,8 @@ static cudaError_t rounds_impl(void *Dv, Layout L, int64_t n, void *colTv, int64
       c_count = (int)((p0 + C2::COL_BM - 1) / C2::COL_BM);
     }
     if (r_count + c_count > 0) {
-      fw_phase2<Op, BK><<<r_count + c_count, C2::THREADS, C2::SMEM, s>>>(D, L, n, p0, p1, cT, ldT, r_count,
-                                                                        vec ? 1 : 0, r_first, sym ? 1 : 0, sp);
+      launch_pdl(fw_phase2<Op, BK>, dim3(r_count + c_count), dim3(C2::THREADS), (size_t)C2::SMEM, s, D, L, n, p0, p1, cT,
+                 ldT, r_count, vec ? 1 : 0, r_first, sym ? 1 : 0, sp);
       if (launches) *launches += 1;
     }
     if (sym && p0 > 0) {
@@ -2026,7 +2055,8 @@ static cudaError_t rounds_impl(void *Dv, Layout L, int64_t n, void *colTv, int64
       const int64_t xs = rP ? p0 : p0 - band_start;  // elements to visit per row
       const unsigned gx = (unsigned)std::min<int64_t>((xs + 255) / 256, 64);
       if (xs > 0) {
-        panel_finalize<Op><<<dim3(gx, BK), 256, 0, s>>>(D, L, n, p0, cT, ldT, rP, band_start);
+        launch_pdl(panel_finalize<Op>, dim3(gx, BK), dim3(256), 0, s, D, L, n, p0, (const uint32_t *)cT, ldT, rP,
+                   band_start);
         if (launches) *launches += 1;
       }
     }
@@ -2048,8 +2078,8 @@ static cudaError_t rounds_impl(void *Dv, Layout L, int64_t n, void *colTv, int64
       if (q == 1) break;
       if (tm) tm->before(2, s);
       if (tma && variant == 3)
-        fw_phase3_ws<Op, BK, kRedOp<Op>><<<grid_tma, P3W_THREADS, P3T<BK>::SMEM, s>>>(
-            mA[0], mB[0], mC, D, L, n, p0, p1, tiles_x, tiles_total, err, sym ? 1 : 0, tiles_y);
+        launch_pdl(fw_phase3_ws<Op, BK, kRedOp<Op>>, dim3(grid_tma), dim3(P3W_THREADS), (size_t)P3T<BK>::SMEM, s,
+                   mA[0], mB[0], mC, D, L, n, p0, p1, tiles_x, tiles_total, err, sym ? 1 : 0, tiles_y);
       else if (tma && variant == 2)
         fw_phase3_tma<Op, BK, 4><<<grid_tma, TileMap<128, 128, 4>::THREADS, P3T<BK>::SMEM, s>>>(
             mA[0], mB[0], mC, D, ld, n, p0, p1, tiles_x, tiles_total, err, sym ? 1 : 0, tiles_y);

@@ -8,6 +8,17 @@
 
 namespace apsp {
 
+// Programmatic dependent launch (the per-round kernels): a kernel launched
+// with the programmatic-serialization attribute may start while the previous
+// kernel on its stream is still running.  pdl_trigger lets the next kernel be
+// launched once every CTA of this one has executed it (so all of this grid's
+// CTAs are resident or done: the next grid can never take the SMs they need);
+// pdl_wait blocks until the previous kernel has completed and its memory
+// writes are visible.  Both are no-ops for a kernel launched without the
+// attribute.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
