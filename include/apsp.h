@@ -80,8 +80,8 @@ typedef struct {
   int queue_depth;       /* serving: pending requests before APSP_E_BUSY (default 4096) */
   int64_t memory_budget; /* serving: bytes of device memory for admitted requests (0 = free HBM - reserve) */
   int64_t spin_limit;    /* bounded device waits: iterations before APSP_E_TIMEOUT (0 = default) */
-  int phase3_variant;    /* Phase-3 kernel: 0 = tuned, else by n and dtype (5 for 5120 <= n < 24576,
-                            7168 <= n < 49152 for packed 16-bit; 4 otherwise), 1 = one
+  int phase3_variant;    /* Phase-3 kernel: 0 = tuned, else by n and dtype (5 for 6144 <= n < 24576,
+                            6144 <= n < 49152 for packed 16-bit; 4 otherwise), 1 = one
                             CTA per tile, 2 = persistent TMA kernel with 256 threads, 3 = persistent TMA
                             kernel with 512 threads, 4 = warp-specialized persistent kernel (TMA producer
                             warp; int32 results leave by a TMA min-reduction), one launch per round,

@@ -54,19 +54,18 @@ struct RoundConfig {
 bool single_launch(int dtype, const void *D, int64_t ld, int64_t n, const RoundConfig &cfg);
 // The default Phase-3 kernel for (n, dtype) when nothing was tuned: every round
 // in one launch for mid-size n, one launch per round below and above (timed per
-// n and dtype on GB300).  Below the lower cut a round is at most a few waves of
-// tiles and the per-round launches are cheaper than the single launch's item
-// scheduling; above the upper cut the per-round launches' fixed cost per round
-// is small against the single launch's cost per tile.  Measured (symmetric
-// mode, ms per solve, one launch per round / single launch): int32 n = 4096
-// 4.53 / 4.95, 5120 7.04 / 6.81, 8192 20.6 / 16.5, 16384 128.4 / 125.6, 32768
-// 954 / 975; packed 16-bit n = 6144 7.56 / 7.61, 7168 10.64 / 9.63, 65536 3922
-// / 3983 (its rounds have half the tiles); fp32 n = 4096 4.41 / 4.97, 5120
-// 6.87 / 6.75.
+// n and dtype on GB300, the per-round kernels with programmatic dependent
+// launch).  Below the lower cut a round is at most a few waves of tiles and the
+// per-round launches are cheaper than the single launch's item scheduling;
+// above the upper cut the per-round launches' fixed cost per round is small
+// against the single launch's cost per tile.  Measured (symmetric mode, ms per
+// solve, one launch per round / single launch): int32 n = 5120 6.52 / 6.89,
+// 6144 9.89 / 8.62, 16384 128.4 / 125.6, 32768 954 / 975; packed 16-bit
+// n = 5120 5.48 / 6.23, 6144 8.05 / 7.66, 65536 3922 / 3983 (its rounds have
+// half the tiles); fp32 n = 5120 6.39 / 6.82, 6144 9.60 / 8.55.
 inline int default_phase3(int64_t n, int dtype) {
-  const int64_t lo = dtype == 1 ? 7168 : 5120;
   const int64_t hi = dtype == 1 ? 49152 : 24576;
-  return n >= lo && n < hi ? 4 : 3;
+  return n >= 6144 && n < hi ? 4 : 3;
 }
 
 // flag |= 1 when D (n x n, leading dimension ld) is not symmetric.

@@ -64,7 +64,7 @@ def test_bounded_wait_reports_timeout_and_context_survives(H):
     W = er_dense(200, 3)
     D = H.solve_t("int32", dev(W))
     np.testing.assert_array_equal(D.cpu().numpy().astype(np.int64), oracle.fw(W.astype(np.int64)))
-    n = 5200  # every round in one launch by default from n = 5120
+    n = 6200  # every round in one launch by default from n = 6144
     s, d, w = gen.er_graph(n, 31, avg_degree=6.0)
     D = H.solve_t("int32", dev(gen.dense_matrix(n, s, d, w, dtype=np.int32))).cpu().numpy()
     rows = np.array([0, 1, 1550, 3099])
@@ -173,9 +173,9 @@ def test_serving_reports_input_errors_per_request(H):
 
 
 @pytest.mark.parametrize("dtype,n,p3", [
-    ("int32", 2048, 3), ("int32", 5119, 3), ("int32", 5120, 4), ("int32", 16384, 4), ("int32", 24575, 4),
-    ("int32", 24576, 3), ("int32", 65536, 3), ("fp32", 4096, 3), ("fp32", 16384, 4), ("fp32", 32768, 3),
-    ("u16", 7167, 3), ("u16", 7168, 4), ("u16", 32768, 4), ("u16", 49151, 4), ("u16", 49152, 3),
+    ("int32", 2048, 3), ("int32", 6143, 3), ("int32", 6144, 4), ("int32", 16384, 4), ("int32", 24575, 4),
+    ("int32", 24576, 3), ("int32", 65536, 3), ("fp32", 5120, 3), ("fp32", 16384, 4), ("fp32", 32768, 3),
+    ("u16", 6143, 3), ("u16", 6144, 4), ("u16", 32768, 4), ("u16", 49151, 4), ("u16", 49152, 3),
     ("u16", 262144, 3)])
 def test_default_phase3_kernel_by_n_and_dtype(lib, dtype, n, p3):
     """Untuned, the handle takes every round in one launch (kernel 4) for mid-size n and one launch per round
