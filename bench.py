@@ -312,7 +312,7 @@ def _replay_batched(torch, apsp, device, mats, arrival, **cfg):
                 pending.discard(j)
                 h.release(tickets[j])
             if not done and (i >= nreq or arrival[i] > now + 1e-4):
-                time.sleep(5e-5)
+                time.sleep(1e-5)
         return lat, time.perf_counter() - t_start
 
 

@@ -94,10 +94,12 @@ typedef struct {
                             (one stream synchronization per solve), 1 = the caller guarantees W is
                             symmetric, 2 = never.  Edge-list solves are symmetric by construction. */
   int64_t serving_large_n; /* serving: a request with n >= this runs alone in its own group on the per-round
-                              kernels; smaller ones share the batched persistent kernel (0 = default 1536) */
-  int serving_large_grid;  /* serving: CTAs of a large request's persistent Phase-3 kernel (0 = one per SM, one
-                              launch per round); a smaller grid lets several large requests run side by side on
-                              disjoint SMs, and then every round of a request runs in one launch */
+                              kernels; smaller ones share the batched persistent kernel (0 = default 1536),
+                              except one that finds the server idle, which also runs alone on the per-round
+                              kernels */
+  int serving_large_grid;  /* serving: CTAs of a large request's persistent Phase-3 kernel (0 = one per SM, and
+                              one launch per round); a smaller grid lets several large requests run side by side
+                              on disjoint SMs, each with its size's default round shape */
 } apsp_config;
 
 /* Fills *cfg with the defaults (library plumbing; no paper counterpart). */

@@ -61,6 +61,7 @@ struct Request {
   int64_t transient = 0;  // panel share (held until the group finishes)
   bool admitted = false;
   bool finished = false;
+  bool alone = false;     // runs in its own group on the per-round kernels
   apsp_status err = APSP_OK;
   void *D = nullptr;
   std::shared_ptr<Group> group;
@@ -1169,15 +1170,14 @@ int64_t large_n(const apsp_handle *h) { return h->cfg.serving_large_n > 0 ? h->c
 
 int64_t panel_bytes(int64_t n) { return 64 * apsp::batch_panel_ld(n) * 4 + 256; }
 
-// Round shape of a large request: with the whole GPU (serving_large_grid 0)
-// one launch per round, so that the batched groups on other streams keep
-// running between its rounds; with a capped grid every round in one launch
-// (the cap leaves SMs to the other groups).
+// Round shape of a large request: the size's own shape, but with the whole GPU
+// (serving_large_grid 0) one launch per round, so that the batched groups on
+// other streams keep running between its rounds; with a capped grid (the cap
+// leaves SMs to the other groups) the size's default.
 apsp::RoundConfig large_round_config(apsp_handle *h, int dtype, int64_t n) {
   apsp::RoundConfig rc = config_for(h, dtype, n);
   rc.grid_cap = h->cfg.serving_large_grid;
   if (rc.p3 == 4 && rc.grid_cap == 0) rc.p3 = 3;
-  if (rc.grid_cap > 0 && rc.bk == 64 && rc.p3 >= 3) rc.p3 = 4;
   return rc;
 }
 
@@ -1186,7 +1186,7 @@ apsp::RoundConfig large_round_config(apsp_handle *h, int dtype, int64_t n) {
 // APSP_AUTO the element panel and the packed 16-bit copy.
 int64_t large_extra_bytes(apsp_handle *h, const apsp_request &q) {
   const int64_t ldT = panel_ld(q.n);
-  const bool all = h->cfg.serving_large_grid > 0;
+  const bool all = large_round_config(h, q.dtype == APSP_AUTO ? APSP_U16 : APSP_I32, q.n).p3 == 4;
   int64_t b = (int64_t)apsp::panel_buffer_bytes(q.n, ldT, all);
   if (q.dtype == APSP_AUTO)
     b += 512 + (int64_t)apsp::row_panel_bytes(ldT, all) + q.n * round_up(q.n, 8) * 2;
@@ -1301,7 +1301,7 @@ apsp_status admit_group_steps(apsp_handle *h, const std::vector<Request *> &rs, 
     if (rn > 0 && apsp::launch_ingest(APSP_I32, rs[i]->D, rs[i]->D, rn, rn, g->status + i, s, &l) != cudaSuccess)
       return APSP_E_CUDA;
   }
-  if (rs.size() == 1 && rs[0]->req.n >= large_n(h)) {
+  if (rs.size() == 1 && (rs[0]->req.n >= large_n(h) || rs[0]->alone)) {
     // one large graph: per-round kernels on the group's stream; an undirected
     // (symmetric) matrix takes the symmetric mode, decided by a device check
     const int64_t rn = rs[0]->req.n;
@@ -1402,13 +1402,24 @@ void worker_loop(apsp_handle *h) {
     if (!h->queue.empty() && (int)h->groups.size() < kMaxGroupsInFlight) {
       std::vector<Request *> rs;
       int64_t add = 0;
+      // a request that finds the server idle (nothing in flight, nothing
+      // queued behind it) runs alone on the per-round kernels, like a large one:
+      // with nothing to share the GPU with, the batched kernel only adds its
+      // setup and its lower tile rate
+      const bool lone = h->groups.empty() && h->queue.size() == 1;
       while (!h->queue.empty() && (int)rs.size() < h->cfg.max_batch) {
         Request *r = h->reqs[h->queue.front()].get();
-        const bool large = r->req.n >= large_n(h);
+        const bool big = r->req.n >= large_n(h);
+        bool large = lone || big;
         if (large && !rs.empty()) break;  // a large request starts its own group
-        const int64_t b = r->bytes + panel_bytes(r->req.n) + (large ? large_extra_bytes(h, r->req) : 0);
+        int64_t b = r->bytes + panel_bytes(r->req.n) + (large ? large_extra_bytes(h, r->req) : 0);
+        if (large && !big && h->used + add + b > h->budget) {
+          large = false;  // no room for the per-round workspace: the batched kernel after all
+          b = r->bytes + panel_bytes(r->req.n);
+        }
         if (h->used + add + b > h->budget) break;  // wait for memory to free up
         h->queue.pop_front();
+        r->alone = large;
         r->transient = b - r->bytes;
         add += b;
         rs.push_back(r);

@@ -281,3 +281,24 @@ def test_serving_auto_requests_equal_int32_and_oracle(H):
         np.testing.assert_array_equal(out.cpu().numpy().astype(np.int64), oracle.dijkstra(n, s, d, w, np.arange(n)))
     with pytest.raises(Exception):
         H.submit(dev(cases[1][0]), dtype="fp32")
+
+
+def test_serving_lone_requests_run_alone_and_exact(lib):
+    """A request that finds the server idle runs alone on the per-round kernels (like a one-at-a-time solve): one
+    request at a time, small and directed ones included, each equal to the oracle."""
+    rng = np.random.default_rng(77)
+    with lib.Handle(device=0) as h:
+        for n, directed in ((90, False), (333, True), (700, False), (1100, True)):
+            m = 4 * n
+            s = rng.integers(0, n, m); d = rng.integers(0, n, m); keep = s != d
+            s, d = s[keep], d[keep]
+            w = rng.integers(1, 300, s.shape[0])
+            W = gen.dense_matrix(n, s, d, w, dtype=np.int32, directed=directed)
+            t = h.submit(dev(W) if n % 2 == 0 else torch.from_numpy(W))
+            assert h.wait(t, 60000) == 0
+            out = torch.empty((n, n), dtype=torch.int32, device="cuda")
+            h.fetch(t, out)
+            torch.cuda.synchronize()
+            assert h.release(t) == 0
+            np.testing.assert_array_equal(out.cpu().numpy().astype(np.int64),
+                                          oracle.dijkstra(n, s, d, w, np.arange(n), directed=directed))
