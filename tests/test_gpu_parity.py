@@ -715,3 +715,54 @@ def test_tri_storage_refuses_asymmetric_input(lib):
     with lib.Handle(device=0) as h:
         h.tri_from_dense("int32", dev(W))
         assert h.last_status() == lib.APSP_I32 + 1  # APSP_E_INVALID
+
+
+def test_tri_storage_round_width_32_profiled_and_real_fp32(lib):
+    """Upper-triangular storage with round width 32 and per-phase profiling on (int32, exact), and with real-valued
+    fp32 weights (within the tolerance, +inf set identical)."""
+    n = 700
+    s, d, w = er_edges(n, seed=70, deg=4.0, wmax=90)
+    with lib.Handle(device=0, block_k=32) as h:
+        h.profile(True)
+        T = h.tri_from_dense("int32", dev(gen.dense_matrix(n, s, d, w, dtype=np.int32)))
+        h.solve_tri("int32", T, n)
+        prof = h.profile_read()
+        h.profile(False)
+        assert h.last_status() == 0
+        assert prof[3][0] == (n + 31) // 32 and prof[3][2] > 0  # one Phase-3 launch per round
+        np.testing.assert_array_equal(lib.tri_to_dense("int32", T, n).cpu().numpy().astype(np.int64),
+                                      expect_fw(gen.dense_matrix(n, s, d, w, dtype=np.int32)))
+    rng = np.random.default_rng(71)
+    wf = (rng.random(s.shape[0]) * 10 + 0.01).astype(np.float32)
+    Wf = gen.dense_matrix(n, s, d, wf, dtype=np.float32)
+    E = oracle.fw(Wf.astype(np.float64))
+    with lib.Handle(device=0) as h:
+        T = h.tri_from_dense("fp32", dev(Wf))
+        h.solve_tri("fp32", T, n)
+        assert h.last_status() == 0
+        got = lib.tri_to_dense("fp32", T, n).cpu().numpy().astype(np.float64)
+    np.testing.assert_array_equal(np.isinf(got), np.isinf(E))
+    f = np.isfinite(E) & (E > 0)
+    assert (np.abs(got[f] - E[f]) <= REL_TOL * E[f]).all()
+
+
+def test_tri_storage_from_edges_duplicates_self_loops_and_bad_ids(lib):
+    """The edge scatter into upper-triangular storage keeps the smaller weight of a duplicated edge (either
+    orientation), ignores self loops, and reports a bad vertex id as APSP_E_INVALID."""
+    n = 300
+    s, d, w = er_edges(n, seed=72, deg=4.0, wmax=50)
+    s2 = np.concatenate([s, d[:50], np.arange(20)])          # the reversed duplicates and 20 self loops
+    d2 = np.concatenate([d, s[:50], np.arange(20)])
+    w2 = np.concatenate([w, np.maximum(1, w[:50] - 3), np.full(20, 7)])
+    E = expect_fw(gen.dense_matrix(n, s2, d2, w2, dtype=np.int32))
+    with lib.Handle(device=0) as h:
+        args = [torch.from_numpy(a.astype(np.int32)).cuda() for a in (s2, d2, w2)]
+        T = h.tri_from_edges("int32", *args, n)
+        h.solve_tri("int32", T, n)
+        assert h.last_status() == 0
+        np.testing.assert_array_equal(lib.tri_to_dense("int32", T, n).cpu().numpy().astype(np.int64), E)
+        bad = [torch.tensor([0, 5], dtype=torch.int32, device="cuda"), torch.tensor([1, n + 3], dtype=torch.int32,
+                                                                                    device="cuda"),
+               torch.tensor([4, 4], dtype=torch.int32, device="cuda")]
+        h.tri_from_edges("int32", *bad, n)
+        assert h.last_status() == 1  # APSP_E_INVALID
