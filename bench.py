@@ -591,7 +591,8 @@ def run_gpu(args):
            "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "int32", "data": "synthetic",
            "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT.get(args.workload, '')}", "n": n,
-                      "edges": int(g.src.shape[0]), "round_width": 64, "parallelism": f"replicas x{ws}",
+                      "edges": int(g.src.shape[0]), "round_width": h.tuned_config("int32", n)[0],
+                      "parallelism": f"replicas x{ws}",
                       "l2": "input matrix larger than L2 (%.2f GB), no flush needed" % (n * n * 4 / 1e9)},
            "roofline": roofline, "gpu_launches": int(launches), "clocks": clocks,
            "addmin_peak_live": live, "paper_context": PAPER_CONTEXT}
@@ -606,7 +607,7 @@ def run_gpu(args):
                              "u16x2 rounds, unpack (all inside the timed region)",
                              "phase3_achieved": a16, "phase3_peak": 2 * peak,
                              "phase3_frac": (a16 / (2 * peak)) if a16 else None, "gpu_launches": int(l16),
-                             "bytes_per_distance": 2}
+                             "round_width": h.tuned_config("u16", n)[0], "bytes_per_distance": 2}
 
     # ---- the same graph in upper-triangular storage (half the bytes): edge list -> storage -> rounds, fewer
     # repeats (each step rebuilds the matrix from the edge list, as the dense path's step copies W in)

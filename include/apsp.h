@@ -75,7 +75,8 @@ typedef struct apsp_handle apsp_handle;
 typedef struct {
   int device;            /* CUDA device ordinal (the handle makes it current in every call) */
   int dtype;             /* apsp_dtype used by apsp_solve (default APSP_I32) */
-  int block_k;           /* round width Bk (32 or 64); 0 = tuned (apsp_autotune) or 64 */
+  int block_k;           /* round width Bk (32, 64 or 128); 0 = tuned (apsp_autotune), else by n and dtype
+                            (128 for packed 16-bit from n = 49152 and fp32 from n = 24576, else 64) */
   int max_batch;         /* serving: graphs per persistent launch (default 64) */
   int queue_depth;       /* serving: pending requests before APSP_E_BUSY (default 4096) */
   int64_t memory_budget; /* serving: bytes of device memory for admitted requests (0 = free HBM - reserve) */
@@ -334,7 +335,8 @@ apsp_status apsp_cancel(apsp_handle *h, uint64_t ticket);
  * (or auto-tuned)", Sec. 5.2-5.4, Table 3).  For `dtype` and every n bucket
  * (powers of two from 128 up to n_max) this times the candidate round shapes
  * -- round width Bk in {32, 64} x Phase-3 variant (the persistent TMA kernels,
- * per round or all rounds in one launch, or one CTA per tile) -- on a synthetic matrix generated on the device (the
+ * per round or all rounds in one launch, or one CTA per tile), and Bk = 128
+ * with the per-round warp-specialized kernel or one CTA per tile -- on a synthetic matrix generated on the device (the
  * kernels do the same work for any graph of a given n), and keeps the
  * fastest for later solves on this handle.  cache_path (nullable): a JSON
  * file keyed by GPU name; entries for this GPU are loaded instead of timing

@@ -238,10 +238,11 @@ int64_t bucket_of(int64_t n) {
 }
 
 // Round shape for (dtype, n): a forced block_k, else the tuned bucket (the
-// largest tuned bucket for larger n), else Bk = 64 with the TMA Phase 3.
+// largest tuned bucket for larger n), else the defaults by n and dtype.
 apsp::RoundConfig config_for(apsp_handle *h, int dtype, int64_t n) {
   apsp::RoundConfig c;
   c.p3 = apsp::default_phase3(n, dtype);
+  c.bk = apsp::default_round_width(n, dtype);
   const int64_t b = bucket_of(n);
   auto it = h->tuned.find({dtype, b});
   if (it != h->tuned.end()) {
@@ -253,7 +254,7 @@ apsp::RoundConfig config_for(apsp_handle *h, int dtype, int64_t n) {
         break;
       }
   }
-  if (h->cfg.block_k == 32 || h->cfg.block_k == 64) c.bk = h->cfg.block_k;
+  if (h->cfg.block_k == 32 || h->cfg.block_k == 64 || h->cfg.block_k == 128) c.bk = h->cfg.block_k;
   if (h->cfg.phase3_variant >= 1 && h->cfg.phase3_variant <= 5) c.p3 = h->cfg.phase3_variant - 1;
   return c;
 }
@@ -409,7 +410,7 @@ apsp_status apsp_create(apsp_handle **out, const apsp_config *cfg) {
   apsp_config_default(&c);
   if (cfg) c = *cfg;
   if (c.dtype != APSP_AUTO && !valid_dtype(c.dtype)) return APSP_E_INVALID;
-  if (c.block_k != 0 && c.block_k != 32 && c.block_k != 64) return APSP_E_INVALID;
+  if (c.block_k != 0 && c.block_k != 32 && c.block_k != 64 && c.block_k != 128) return APSP_E_INVALID;
   if (c.phase3_variant < 0 || c.phase3_variant > 5) return APSP_E_INVALID;
   if (c.symmetric < 0 || c.symmetric > 2) return APSP_E_INVALID;
   if (c.serving_large_n < 0 || c.serving_large_grid < 0) return APSP_E_INVALID;
@@ -981,7 +982,7 @@ std::vector<TuneEntry> read_cache(const char *path) {
     e.bk = (int)json_num_field(obj, "bk", 64);
     e.tma = (int)json_num_field(obj, "tma", 1);
     e.ms = json_num_field(obj, "ms", 0);
-    if (!e.gpu.empty() && e.dtype >= 0 && e.n > 0 && (e.bk == 32 || e.bk == 64) && e.tma >= 0 && e.tma <= 4)
+    if (!e.gpu.empty() && e.dtype >= 0 && e.n > 0 && (e.bk == 32 || e.bk == 64 || e.bk == 128) && e.tma >= 0 && e.tma <= 4)
       out.push_back(e);
     p = b + 1;
   }
@@ -1044,8 +1045,9 @@ apsp_status apsp_autotune(apsp_handle *h, int dtype, int64_t n_max, const char *
     cudaEventCreate(&e1);
     double best = 1e30;
     apsp::RoundConfig best_c;
-    for (int bk : {32, 64})
+    for (int bk : {32, 64, 128})
       for (int var : {4, 3, 2, 1, 0}) {
+        if (bk == 128 && var != 3 && var != 0) continue;  // width 128: per-tile or warp-specialized, per round
         apsp::RoundConfig c;
         c.bk = bk;
         c.p3 = var;

@@ -51,6 +51,112 @@ __global__ void __launch_bounds__(P1_THREADS) fw_phase1(typename Op::elem *__res
   phase1_body<Op, BK, P1_THREADS, false>(D, L, n, p0, colT, ldT, s, threadIdx.x);
 }
 
+// Phase 1 of a 128-wide round: the pivot-block scheme of phase1_body
+// (fw_tasks.cuh) on a 32 x 32 grid of threads, each owning a 4 x 4 block of
+// D_kk in registers (1024 threads, at most 64 registers each).  Per pivot
+// block p (pivots 4p .. 4p+3) every thread closes the 4 x 4 corner K, then
+// for each of its rows r forms a' = a (x) K* from the row's pivot-column
+// values a (read from shared memory one row at a time, which keeps the
+// registers within the limit) and lowers its row by a' (x) b, b = the
+// pivot-row values of its columns.  Reading a later than phase1_body does is
+// covered by the same argument: a value written back meanwhile is a' itself,
+// and a' (x) K* = a' since K* is closed.  Outputs as phase1_body: D_kk, the
+// transposed panel rows in colT and, with rowP, the element panel.
+constexpr int P1W_THREADS = 1024;
+template <class Op>
+__device__ __forceinline__ void phase1_body_w128(typename Op::elem *__restrict__ D, Layout L, int64_t n, int64_t p0,
+                                                 uint32_t *__restrict__ colT, int64_t ldT, P1Smem<Op, 128> &sm,
+                                                 int tid, typename Op::elem *__restrict__ rowP) {
+  using S = typename Op::scalar;
+  constexpr int BK = 128, G = 32, PT = 4, NT = P1W_THREADS;
+  static_assert(G * PT == BK && G * G == NT, "phase 1 layout");
+  auto &s = sm.s;
+  const int by = tid / G, bx = tid % G;
+  const S INF = Op::to_s(Op::inf_elem());
+  for (int idx = tid; idx < BK * BK; idx += NT) {
+    const int64_t r = p0 + idx / BK, c = p0 + idx % BK;
+    s[idx / BK][idx % BK] = (r < n && c < n) ? Op::to_s(D[L.off(r, c)]) : INF;
+  }
+  __syncthreads();
+  S v[PT][PT];
+#pragma unroll
+  for (int r = 0; r < PT; ++r)
+#pragma unroll
+    for (int c = 0; c < PT; ++c) v[r][c] = s[by * PT + r][bx * PT + c];
+#pragma unroll 1
+  for (int p = 0; p < G; ++p) {
+    const int t0 = p * PT;
+    S K[PT][PT], b[PT][PT];
+#pragma unroll
+    for (int i = 0; i < PT; ++i)
+#pragma unroll
+      for (int j = 0; j < PT; ++j) {
+        K[i][j] = s[t0 + i][t0 + j];
+        b[i][j] = s[t0 + i][bx * PT + j];
+      }
+#pragma unroll
+    for (int m = 0; m < PT; ++m)
+#pragma unroll
+      for (int i = 0; i < PT; ++i)
+#pragma unroll
+        for (int j = 0; j < PT; ++j) K[i][j] = Op::s_addmin(K[i][m], K[m][j], K[i][j]);
+#pragma unroll
+    for (int r = 0; r < PT; ++r) {
+      S a[PT], a2[PT];
+#pragma unroll
+      for (int i = 0; i < PT; ++i) a[i] = s[by * PT + r][t0 + i];
+#pragma unroll
+      for (int j = 0; j < PT; ++j) {
+        S x = a[j];
+#pragma unroll
+        for (int i = 0; i < PT; ++i) x = Op::s_addmin(a[i], K[i][j], x);
+        a2[j] = x;
+      }
+#pragma unroll
+      for (int c = 0; c < PT; ++c)
+#pragma unroll
+        for (int j = 0; j < PT; ++j) v[r][c] = Op::s_addmin(a2[j], b[j][c], v[r][c]);
+    }
+    if (p + 1 < G && (by == p + 1 || bx == p + 1)) {
+#pragma unroll
+      for (int r = 0; r < PT; ++r)
+#pragma unroll
+        for (int c = 0; c < PT; ++c) s[by * PT + r][bx * PT + c] = v[r][c];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < PT; ++r)
+#pragma unroll
+    for (int c = 0; c < PT; ++c) s[by * PT + r][bx * PT + c] = v[r][c];
+  __syncthreads();
+  for (int idx = tid; idx < BK * BK; idx += NT) {
+    const int i = idx / BK, j = idx % BK;
+    const int64_t r = p0 + i, c = p0 + j;
+    if (r < n && c < n) D[L.off(r, c)] = Op::from_s(s[i][j]);
+  }
+  for (int idx = tid; idx < BK * BK; idx += NT) {
+    const int t = idx / BK, i = idx % BK;
+    colT[t * ldT + p0 + i] = Op::dup(Op::from_s(s[i][t]));
+  }
+  if (rowP) {
+    for (int idx = tid; idx < BK * BK; idx += NT) {
+      const int t = idx / BK, j = idx % BK;
+      rowP[t * ldT + p0 + j] = Op::from_s(s[t][j]);
+    }
+  }
+}
+
+template <class Op>
+__global__ void __launch_bounds__(P1W_THREADS) fw_phase1_w128(typename Op::elem *__restrict__ D, Layout L, int64_t n,
+                                                              int64_t p0, uint32_t *__restrict__ colT, int64_t ldT,
+                                                              typename Op::elem *rowP) {
+  extern __shared__ __align__(16) uint8_t p1w_raw[];
+  pdl_trigger();
+  pdl_wait();
+  phase1_body_w128<Op>(D, L, n, p0, colT, ldT, *reinterpret_cast<P1Smem<Op, 128> *>(p1w_raw), threadIdx.x, rowP);
+}
+
 // shared-memory loaders: load_As_colT, load_Bs_rows, load_As_transposed (fw_device.cuh)
 
 // ---------------------------------------------------------------- Phase 2
@@ -208,9 +314,15 @@ __global__ void __launch_bounds__(256, 2) fw_phase3(typename Op::elem *__restric
 constexpr int P3T_C_BYTES = 128 * 128 * 4;
 constexpr uint32_t P3T_WAIT_LIMIT = 1u << 26;
 constexpr uint32_t P3T_SLEEP_NS = 256;  // longest sleep of one wait try in the persistent kernels' producers
+// A stage holds KS k-steps of the A and B tiles: the whole round for round
+// widths up to 64, half of it for width 128 (whose tiles then take two stages
+// each and store their C block once per 128 k-steps).
 template <int BK>
 struct P3T {
-  static constexpr int STAGE_BYTES = 2 * BK * 128 * 4;  // A + B tiles
+  static constexpr int KS = BK < 64 ? BK : 64;
+  static constexpr int NSPLIT = BK / KS;  // stages per tile
+  static_assert(NSPLIT == 1 || NSPLIT == 2, "round width 32, 64 or 128");
+  static constexpr int STAGE_BYTES = 2 * KS * 128 * 4;  // A + B tiles
   static constexpr int SMEM = 2 * STAGE_BYTES + P3T_C_BYTES + 1024;
 };
 
@@ -429,12 +541,13 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
   constexpr int NCW = Map::THREADS / 32;  // consumer warps
   static_assert(Map::THREADS + 32 == P3W_THREADS, "one producer warp after the consumers");
   constexpr int STAGE = P3T<BK>::STAGE_BYTES;
+  constexpr int KS = P3T<BK>::KS, NSPLIT = P3T<BK>::NSPLIT;  // k-steps per stage, stages per tile
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_ab[2], empty_ab[2], full_c, cdone, cfree;
   __shared__ int abort_flag;
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   auto stA = [&](int s) { return reinterpret_cast<uint32_t *>(base + s * STAGE); };
-  auto stB = [&](int s) { return reinterpret_cast<uint32_t *>(base + s * STAGE) + BK * BM; };
+  auto stB = [&](int s) { return reinterpret_cast<uint32_t *>(base + s * STAGE) + KS * BM; };
   uint32_t *Cs = reinterpret_cast<uint32_t *>(base + 2 * STAGE);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -501,10 +614,11 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
     if (lane == 0) {
       int n_ab[2] = {0, 0}, n_c = 0;
       bool ok = true;
-      auto issue_ab = [&](int ty_, int tx_, int s) {
+      // k-steps [h * KS, (h + 1) * KS) of tile (ty_, tx_) into stage s
+      auto issue_ab = [&](int ty_, int tx_, int h, int s) {
         mbar_arrive_expect_tx(&full_ab[s], STAGE);
-        tma_load_2d(stA(s), &mapA, &full_ab[s], ty_ * BM, 0);
-        tma_load_2d(stB(s), &mapB, &full_ab[s], tx_ * BNW * Op::EPW, sym ? 0 : (int)p0);
+        tma_load_2d(stA(s), &mapA, &full_ab[s], ty_ * BM, h * KS);
+        tma_load_2d(stB(s), &mapB, &full_ab[s], tx_ * BNW * Op::EPW, (sym ? 0 : (int)p0) + h * KS);
         if (s == 0) ++n_ab[0];
         else ++n_ab[1];
       };
@@ -515,25 +629,37 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
         tma_load_2d(Cs, &mapC, &full_c, x, y);
         ++n_c;
       };
-      int aty = ty0, atx = tx0;  // next A/B tile to load
+      // the item stream: (tile, k-part h) in tile order, item j in stage j & 1
+      const int n_items = (t_end - t_begin) * NSPLIT;
+      int aty = ty0, atx = tx0, ah = 0;  // next item to load
+      auto next_item = [&]() {
+        if (++ah == NSPLIT) {
+          ah = 0;
+          step(aty, atx);
+        }
+      };
       int cty = ty0, ctx = tx0;  // tile whose result is written next
-      issue_ab(aty, atx, 0);
-      step(aty, atx);
-      if (t_begin + 1 < t_end) {
-        issue_ab(aty, atx, 1);
-        step(aty, atx);
+      issue_ab(aty, atx, ah, 0);
+      next_item();
+      if (n_items > 1) {
+        issue_ab(aty, atx, ah, 1);
+        next_item();
       }
       if (!RED) issue_c(cty, ctx);
       for (int t = t_begin; t < t_end; ++t) {
-        const int i = t - t_begin, s = i & 1;
-        if (!mbar_wait_sleep_bounded(&empty_ab[s], (uint32_t)(i >> 1) & 1u, P3T_WAIT_LIMIT, P3T_SLEEP_NS)) {
-          ok = false;
-          break;
+        const int i = t - t_begin;
+        for (int h = 0; h < NSPLIT; ++h) {
+          const int j = i * NSPLIT + h, s = j & 1;
+          if (!mbar_wait_sleep_bounded(&empty_ab[s], (uint32_t)(j >> 1) & 1u, P3T_WAIT_LIMIT, P3T_SLEEP_NS)) {
+            ok = false;
+            break;
+          }
+          if (j + 2 < n_items) {
+            issue_ab(aty, atx, ah, s);
+            next_item();
+          }
         }
-        if (t + 2 < t_end) {
-          issue_ab(aty, atx, s);
-          step(aty, atx);
-        }
+        if (!ok) break;
         if (!mbar_wait_sleep_bounded(&cdone, (uint32_t)i & 1u, P3T_WAIT_LIMIT, P3T_SLEEP_NS)) {
           ok = false;
           break;
@@ -570,19 +696,25 @@ __global__ void __launch_bounds__(P3W_THREADS, 1)
     int cty = ty0, ctx = tx0;
     uint32_t acc[8][TN];
     for (int t = t_begin; t < t_end; ++t) {
-      const int i = t - t_begin, s = i & 1;
+      const int i = t - t_begin;
 #pragma unroll
       for (int r = 0; r < 8; ++r)
 #pragma unroll
         for (int c = 0; c < TN; ++c) acc[r][c] = Op::INF_WORD;
-      bool bad = !mbar_wait_bounded(&full_ab[s], (uint32_t)(i >> 1) & 1u, P3T_WAIT_LIMIT);
+      bool bad = false;
+#pragma unroll 1
+      for (int h = 0; h < NSPLIT; ++h) {  // the tile's k-parts, one stage each (one copy of the k-loop)
+        const int j = i * NSPLIT + h, s = j & 1;
+        bad = !mbar_wait_bounded(&full_ab[s], (uint32_t)(j >> 1) & 1u, P3T_WAIT_LIMIT);
+        if (__any_sync(0xffffffffu, bad)) break;
+        tile_minplus<Op, BM, BNW, KS, TN>(stA(s), stB(s), acc, ty, tx);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty_ab[s]);
+      }
       if (__any_sync(0xffffffffu, bad)) {
         if (lane == 0) abort_flag = 1;
         break;
       }
-      tile_minplus<Op, BM, BNW, BK, TN>(stA(s), stB(s), acc, ty, tx);
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty_ab[s]);
       const int64_t r0 = (int64_t)cty * BM, c0 = (int64_t)ctx * BNW * Op::EPW;
       if (RED) {
         // the previous tile's reduction has finished reading the C buffer
@@ -1934,6 +2066,10 @@ static cudaError_t rounds_impl(void *Dv, Layout L, int64_t n, void *colTv, int64
   // kernel 4 (every round in one launch) when its conditions hold, else 3
   bool la_on = kLookaheadWidth<BK> && use_tma && vec && variant == 4 && q > 1 && !tri;
   if (variant == 4) variant = 3;
+  // round width 128 runs the per-tile kernel or the warp-specialized one (its
+  // tiles take two 64-step stages); the other TMA kernels hold a whole round
+  // per stage, which does not fit
+  if (BK > 64 && (variant == 1 || variant == 2)) variant = 3;
   // upper-triangular storage: symmetric mode on the warp-specialized Phase 3,
   // one launch per round
   if (tri && (!sym || !vec || variant != 3)) return cudaErrorNotSupported;
@@ -1958,9 +2094,15 @@ static cudaError_t rounds_impl(void *Dv, Layout L, int64_t n, void *colTv, int64
   using C2 = P2Cfg<Op, BK>;
   using C3 = P3Cfg<Op>;
   constexpr int SMEM3 = (BK * C3::BM + BK * C3::BNW) * 4;
+  constexpr int KS = P3T<BK>::KS;  // k-steps per stage of the TMA Phase-3 kernels (box height of the A/B maps)
   // the attributes are per device, so they are set on every call (a cheap host call)
   cudaError_t e = cudaFuncSetAttribute(fw_phase2<Op, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, C2::SMEM);
   if (e != cudaSuccess) return e;
+  if constexpr (BK > 64) {
+    e = cudaFuncSetAttribute(fw_phase1_w128<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(P1Smem<Op, 128>));
+    if (e != cudaSuccess) return e;
+  }
   e = cudaFuncSetAttribute(fw_phase3<Op, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM3);
   if (e != cudaSuccess) return e;
   // persistent TMA Phase 3 when D is 16-byte addressable (otherwise the
@@ -1975,13 +2117,13 @@ static cudaError_t rounds_impl(void *Dv, Layout L, int64_t n, void *colTv, int64
                                                         : CU_TENSOR_MAP_DATA_TYPE_INT32;
     for (int b = 0; b < (la_on ? 2 : 1) && tma; ++b)
       tma = make_map(&mA[b], CU_TENSOR_MAP_DATA_TYPE_UINT32, colTb[b], (uint64_t)ldT, (uint64_t)BK,
-                     (uint64_t)ldT * 4, 128, BK) &&
+                     (uint64_t)ldT * 4, 128, KS) &&
             (sym ? make_map(&mB[b], dt, symB_of(b), (uint64_t)ldT, (uint64_t)BK, (uint64_t)ldT * sizeof(E),
-                            128 * Op::EPW, BK)
-                 : make_map(&mB[b], dt, D, (uint64_t)n, (uint64_t)n, (uint64_t)ld * sizeof(E), 128 * Op::EPW, BK));
+                            128 * Op::EPW, KS)
+                 : make_map(&mB[b], dt, D, (uint64_t)n, (uint64_t)n, (uint64_t)ld * sizeof(E), 128 * Op::EPW, KS));
     for (int b = 0; b < 2 && dev_sym && tma; ++b)
       tma = make_map(&mBs[b], dt, symB_any(b), (uint64_t)ldT, (uint64_t)BK, (uint64_t)ldT * sizeof(E), 128 * Op::EPW,
-                     BK);
+                     KS);
     // int32 and fp32 (TMA min-reduction epilogue of variant 3): x extent
     // red_cols(n), and an int32 map (fp32 bits of non-negative values order
     // like int32); upper-triangular storage: the whole rectangle
@@ -1994,10 +2136,13 @@ static cudaError_t rounds_impl(void *Dv, Layout L, int64_t n, void *colTv, int64
     err = tma ? (wait_err ? wait_err : error_word()) : nullptr;
     tma = tma && err != nullptr;
     if (tma) {
-      e = cudaFuncSetAttribute(fw_phase3_tma<Op, BK, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, P3T<BK>::SMEM);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fw_phase3_tma<Op, BK, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      if constexpr (BK <= 64) {
+        e = cudaFuncSetAttribute(fw_phase3_tma<Op, BK, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  P3T<BK>::SMEM);
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(fw_phase3_tma<Op, BK, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   P3T<BK>::SMEM);
+      }
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(fw_phase3_ws<Op, BK, kRedOp<Op>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  P3T<BK>::SMEM);
@@ -2030,7 +2175,10 @@ static cudaError_t rounds_impl(void *Dv, Layout L, int64_t n, void *colTv, int64
     span(k, p0, p1);
     const double w = (double)(p1 - p0), rest = (double)(n - (p1 - p0));
     if (tm) tm->before(0, s);
-    if (sym && rP)
+    if constexpr (BK > 64)
+      launch_pdl(fw_phase1_w128<Op>, dim3(1), dim3(P1W_THREADS), sizeof(P1Smem<Op, 128>), s, D, L, n, p0, cT, ldT,
+                 sym ? rP : nullptr);
+    else if (sym && rP)
       launch_pdl(fw_phase1_sym<Op, BK>, dim3(1), dim3(P1_THREADS), 0, s, D, L, n, p0, cT, ldT, rP);
     else
       launch_pdl(fw_phase1<Op, BK>, dim3(1), dim3(P1_THREADS), 0, s, D, L, n, p0, cT, ldT);
@@ -2080,13 +2228,16 @@ static cudaError_t rounds_impl(void *Dv, Layout L, int64_t n, void *colTv, int64
       if (tma && variant == 3)
         launch_pdl(fw_phase3_ws<Op, BK, kRedOp<Op>>, dim3(grid_tma), dim3(P3W_THREADS), (size_t)P3T<BK>::SMEM, s,
                    mA[0], mB[0], mC, D, L, n, p0, p1, tiles_x, tiles_total, err, sym ? 1 : 0, tiles_y);
-      else if (tma && variant == 2)
-        fw_phase3_tma<Op, BK, 4><<<grid_tma, TileMap<128, 128, 4>::THREADS, P3T<BK>::SMEM, s>>>(
-            mA[0], mB[0], mC, D, ld, n, p0, p1, tiles_x, tiles_total, err, sym ? 1 : 0, tiles_y);
-      else if (tma)
-        fw_phase3_tma<Op, BK, 8><<<grid_tma, TileMap<128, 128, 8>::THREADS, P3T<BK>::SMEM, s>>>(
-            mA[0], mB[0], mC, D, ld, n, p0, p1, tiles_x, tiles_total, err, sym ? 1 : 0, tiles_y);
-      else
+      else if constexpr (BK <= 64) {
+        if (tma && variant == 2)
+          fw_phase3_tma<Op, BK, 4><<<grid_tma, TileMap<128, 128, 4>::THREADS, P3T<BK>::SMEM, s>>>(
+              mA[0], mB[0], mC, D, ld, n, p0, p1, tiles_x, tiles_total, err, sym ? 1 : 0, tiles_y);
+        else if (tma)
+          fw_phase3_tma<Op, BK, 8><<<grid_tma, TileMap<128, 128, 8>::THREADS, P3T<BK>::SMEM, s>>>(
+              mA[0], mB[0], mC, D, ld, n, p0, p1, tiles_x, tiles_total, err, sym ? 1 : 0, tiles_y);
+        else
+          fw_phase3<Op, BK><<<g3, C3::THREADS, SMEM3, s>>>(D, ld, n, p0, p1, colT, ldT, vec ? 1 : 0, symB_of(0));
+      } else
         fw_phase3<Op, BK><<<g3, C3::THREADS, SMEM3, s>>>(D, ld, n, p0, p1, colT, ldT, vec ? 1 : 0, symB_of(0));
       if (launches) *launches += 1;
       if (tm) tm->after(2, s, p3_work(k));
@@ -2178,6 +2329,9 @@ static cudaError_t rounds_bk(const RoundConfig &cfg, void *D, Layout L, int64_t 
   if (cfg.bk == 64)
     return rounds_impl<Op, 64>(D, L, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err, cfg.sym, cfg.rowP,
                                cfg.sym_flag, cfg.gate, cfg.dep_spins, cfg.grid_cap);
+  if (cfg.bk == 128)
+    return rounds_impl<Op, 128>(D, L, n, colT, ldT, vec, cfg.p3, s, launches, tm, wait_err, cfg.sym, cfg.rowP,
+                                cfg.sym_flag, cfg.gate, cfg.dep_spins, cfg.grid_cap);
   return cudaErrorInvalidValue;
 }
 

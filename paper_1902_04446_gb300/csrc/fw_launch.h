@@ -20,7 +20,7 @@ struct PhaseTimer {
   virtual ~PhaseTimer() {}
 };
 
-// Tunable shape of the rounds: round width Bk (32 or 64) and the Phase-3
+// Tunable shape of the rounds: round width Bk (32, 64 or 128) and the Phase-3
 // kernel: 0 = one CTA per tile, 1 = persistent TMA kernel with 256 threads
 // (8 x 8 words each), 2 = persistent TMA kernel with 512 threads (8 x 4 words
 // each), 3 = warp-specialized persistent kernel (8 consumer warps with 8 x 8
@@ -30,6 +30,8 @@ struct PhaseTimer {
 // (fw_solve_ws; round width 64, needs the double panel buffer of
 // panel_buffer_bytes(n, ldT, true); otherwise it falls back to 3).  The TMA
 // kernels need a 16-byte addressable matrix and fall back to 0 otherwise.
+// Round width 128 runs kernels 0 and 3 (1 and 2 run as 3): kernel 3 then
+// takes each tile's 128 k-steps as two 64-step stages.
 // sym: symmetric mode for undirected (symmetric) inputs -- Phase 3 updates
 // only the tiles that touch the upper triangle, both of its operands come from
 // one symmetric panel, and a final pass mirrors the upper triangle into the
@@ -67,10 +69,21 @@ inline int default_phase3(int64_t n, int dtype) {
   const int64_t hi = dtype == 1 ? 49152 : 24576;
   return n >= 6144 && n < hi ? 4 : 3;
 }
+// The default round width for (n, dtype): 128 where large n runs one launch
+// per round in packed 16-bit or fp32 (each tile then takes 128 k-steps in two
+// stages and stores its C block half as often), else 64.  Measured (symmetric
+// mode, ms per solve, width 64 / 128): fp32 n = 65536 7177 / 6967, packed
+// 16-bit n = 65536 3931 / 3910, n = 32768 528 / 519; int32 n = 65536 7486 /
+// 7550 (its k-loop runs slower in the two-stage kernel than the epilogue
+// saves), and every element type at small n, where the 128-wide Phase 1 on
+// one SM is on the critical path (int32 n = 4096 4.07 / 5.24).
+inline int default_round_width(int64_t n, int dtype) {
+  return dtype != 0 && default_phase3(n, dtype) == 3 && n >= 6144 ? 128 : 64;
+}
 
 // flag |= 1 when D (n x n, leading dimension ld) is not symmetric.
 cudaError_t launch_symmetry_check(int dtype, const void *D, int64_t n, int64_t ld, int *flag, cudaStream_t s);
-constexpr int64_t kMaxRoundWidth = 64;  // panel buffers are sized for this
+constexpr int64_t kMaxRoundWidth = 128;  // panel buffers are sized for this (the widest round)
 
 // Bytes of the colT panel buffer launch_rounds needs for n (ldT = its row
 // pitch in words): one kMaxRoundWidth x ldT panel of 32-bit words, or for

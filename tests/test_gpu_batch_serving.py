@@ -179,9 +179,11 @@ def test_serving_reports_input_errors_per_request(H):
     ("u16", 262144, 3)])
 def test_default_phase3_kernel_by_n_and_dtype(lib, dtype, n, p3):
     """Untuned, the handle takes every round in one launch (kernel 4) for mid-size n and one launch per round
-    (kernel 3) below and above; packed 16-bit, with half the tiles per round, keeps the single launch longer."""
+    (kernel 3) below and above; packed 16-bit, with half the tiles per round, keeps the single launch longer.
+    Large n in packed 16-bit and fp32 runs 128-wide rounds, everything else 64-wide."""
+    bk = 128 if dtype != "int32" and p3 == 3 and n >= 6144 else 64
     with lib.Handle(device=0) as h:
-        assert h.tuned_config(dtype, n) == (64, p3)
+        assert h.tuned_config(dtype, n) == (bk, p3)
 
 
 def test_autotune_cache_and_bit_exact_with_every_shape(lib, tmp_path):
@@ -189,7 +191,8 @@ def test_autotune_cache_and_bit_exact_with_every_shape(lib, tmp_path):
     with lib.Handle(device=0) as h:
         table = h.autotune("int32", 512, cache)
         assert set(table) == {128, 256, 512}
-        assert all(bk in (32, 64) and p3 in (0, 1, 2, 3, 4) for bk, p3 in table.values())
+        assert all(bk in (32, 64, 128) and p3 in (0, 1, 2, 3, 4) for bk, p3 in table.values())
+        assert all(p3 in (0, 3) for bk, p3 in table.values() if bk == 128)
     import json
     entries = json.load(open(cache))["entries"]
     assert {e["n"] for e in entries} == {128, 256, 512} and all(e["ms"] > 0 for e in entries)
@@ -198,7 +201,7 @@ def test_autotune_cache_and_bit_exact_with_every_shape(lib, tmp_path):
     # every round shape gives the same exact answer
     W = er_dense(300, 77)
     E = oracle.fw(W.astype(np.int64))
-    for bk in (32, 64):
+    for bk in (32, 64, 128):
         with lib.Handle(device=0, block_k=bk) as hb:
             assert hb.tuned_config("int32", 300)[0] == bk
             for dt, Wx in (("int32", W), ("u16", None)):

@@ -414,7 +414,7 @@ def test_fp32_negative_zero_weights_are_canonical(H):
 
 
 # ------------------------------------------------------------------ every round shape
-@pytest.mark.parametrize("block_k", [32, 64])
+@pytest.mark.parametrize("block_k", [32, 64, 128])
 @pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("dt", ["int32", "u16", "fp32"])
 def test_every_round_shape_matches_oracle(lib, block_k, variant, dt):
@@ -433,7 +433,7 @@ def test_every_round_shape_matches_oracle(lib, block_k, variant, dt):
         np.testing.assert_array_equal(D, E)
 
 
-@pytest.mark.parametrize("block_k", [32, 64])
+@pytest.mark.parametrize("block_k", [32, 64, 128])
 @pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("dt", ["int32", "u16", "fp32"])
 def test_directed_every_phase3_kernel(lib, block_k, variant, dt):
@@ -562,7 +562,7 @@ def test_symmetric_mode_matches_oracle(lib, symmetric, variant, dt, n):
         np.testing.assert_array_equal(D, E)
 
 
-@pytest.mark.parametrize("block_k", [32, 64])
+@pytest.mark.parametrize("block_k", [32, 64, 128])
 def test_symmetric_mode_block_k_and_ld(lib, block_k):
     n, ld = 333, 340
     s, d, w = er_edges(n, seed=block_k, deg=3.0, wmax=500)
@@ -766,3 +766,47 @@ def test_tri_storage_from_edges_duplicates_self_loops_and_bad_ids(lib):
                torch.tensor([4, 4], dtype=torch.int32, device="cuda")]
         h.tri_from_edges("int32", *bad, n)
         assert h.last_status() == 1  # APSP_E_INVALID
+
+
+# ------------------------------------------------------------------ round width 128
+def _as_i64(dt, D):
+    if dt == "u16":
+        return oracle.unpack_u16(D.view(np.uint16)).astype(np.int64)
+    if dt == "fp32":
+        return np.where(np.isinf(D), INF, D.astype(np.float64)).astype(np.int64)  # small integers: exact
+    return D.astype(np.int64)
+
+
+def _dense_as(dt, n, s, d, w, directed):
+    npdt, inf = {"int32": (np.int32, INF), "u16": (np.int16, 0x7FFF), "fp32": (np.float32, np.inf)}[dt]
+    return gen.dense_matrix(n, s, d, w, dtype=npdt, inf=inf, directed=directed)
+
+
+@pytest.mark.parametrize("dt", ["int32", "u16", "fp32"])
+@pytest.mark.parametrize("variant", [1, 4])  # the per-tile kernel; the warp-specialized one (two stages per tile)
+def test_round_width_128_ragged_sizes_both_modes(lib, dt, variant):
+    """Round width 128: sizes whose last round ends inside the first or the second 64-step stage of a tile (or
+    fills it), undirected (symmetric mode) and directed (general mode) inputs, against the oracle."""
+    with lib.Handle(device=0, block_k=128, phase3_variant=variant) as h:
+        assert h.tuned_config(dt, 300)[0] == 128
+        for n in (1, 2, 63, 64, 65, 127, 128, 129, 191, 192, 193, 256, 300, 555):
+            for directed in (False, True):
+                s, d, w = er_edges(n, seed=n + 7 + directed, deg=3.0, wmax=50, directed=directed)
+                W = _dense_as(dt, n, s, d, w, directed)
+                E = expect_fw(_dense_as("int32", n, s, d, w, directed))
+                got = _as_i64(dt, h.solve_t(dt, dev(W)).cpu().numpy())
+                np.testing.assert_array_equal(got, E, err_msg=f"n={n} directed={directed}")
+
+
+@pytest.mark.parametrize("dt", ["int32", "u16", "fp32"])
+def test_round_width_128_upper_triangular_storage(lib, dt):
+    """Upper-triangular storage solved with round width 128, unpacked and compared with the oracle, for sizes
+    around the super-tile and round boundaries."""
+    with lib.Handle(device=0, block_k=128) as h:
+        for n in (1, 65, 129, 255, 257, 300, 700):
+            s, d, w = er_edges(n, seed=3 * n + 1, deg=3.0, wmax=60)
+            T = h.tri_from_dense(dt, dev(_dense_as(dt, n, s, d, w, False)))
+            h.solve_tri(dt, T, n)
+            assert h.last_status() == 0
+            got = _as_i64(dt, lib.tri_to_dense(dt, T, n).cpu().numpy())
+            np.testing.assert_array_equal(got, expect_fw(_dense_as("int32", n, s, d, w, False)), err_msg=f"n={n}")
