@@ -491,6 +491,9 @@ __global__ void __launch_bounds__(TileMap<128, 128, TN>::THREADS, 1)
 //     at the end; interior tiles go back through
 //     the C buffer and a TMA store, edge tiles (panel rows or columns, ragged
 //     edge) by masked stores that leave the panels untouched.
+// Round width 128 (P3T<128>::NSPLIT = 2): each tile takes two 64-step stages
+// in a row -- the producer streams (tile, k-half) items, item j in stage
+// j & 1 -- and the consumers run the epilogue once per tile, after both.
 // Symmetric mode and the tile order are as in fw_phase3_tma.  Every wait is
 // bounded; a CTA that gives up waits (bounded) for its copies in flight and
 // ORs 4 into *err.
