@@ -852,7 +852,7 @@ def run_round_shapes(args):
              4: "warp-specialized, one launch per round", 5: "warp-specialized, every round in one launch"}
     epw = 2 if args.dtype == "u16" else 1
     peak = ADDMIN_LANES_PER_CLK_PER_SM * torch.cuda.get_device_properties(0).multi_processor_count * 2070.0 / 1e3
-    shapes = [(bk, v) for bk in (32, 64) for v in (1, 2, 3, 4, 5)]
+    shapes = [(bk, v) for bk in (32, 64) for v in (1, 2, 3, 4, 5)] + [(128, 1), (128, 4)]
     if args.shapes:
         shapes = [tuple(int(x) for x in sv.split("x")) for sv in args.shapes.split(",")]
     for bk, v in shapes:
@@ -889,7 +889,8 @@ def main(argv=None):
     ap.add_argument("--dtype", default="int32", choices=["int32", "u16", "fp32"],
                     help="--round-shapes: the element type solved (u16 from the int32 matrix, INF -> 0x7FFF)")
     ap.add_argument("--shapes", default="",
-                    help="--round-shapes: comma-separated BKxVARIANT list (e.g. 64x4,64x5); default all ten")
+                    help="--round-shapes: comma-separated BKxVARIANT list (e.g. 64x4,64x5); default all twelve (width "
+                         "128 runs variants 1 and 4)")
     ap.add_argument("--er-n", type=int, default=0,
                     help="--round-shapes: an Erdos-Renyi graph of this n (average degree 16 plus a spanning path, "
                          "seed n, weights U{1..1000}) instead of --workload")
