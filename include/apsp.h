@@ -87,7 +87,8 @@ typedef struct {
                             kernel with 512 threads, 4 = warp-specialized persistent kernel (TMA producer
                             warp; int32 results leave by a TMA min-reduction), one launch per round,
                             5 = the same kernel running every round in one launch with each round's
-                            Phase 1 and Phase 2 as tasks inside it (round width 64) */
+                            Phase 1 and Phase 2 as tasks inside it (round width 64).  At round width 128
+                            variants 2, 3 and 5 run as 4, whose tiles then take two 64-step stages */
   int symmetric;         /* symmetric mode for undirected graphs (Sec. 3: A_ij = A_ji; the paper keeps
                             only the upper triangle): Phase 3 updates only the tiles touching the upper
                             triangle and the lower triangle is mirrored at the end -- same result, about
